@@ -1,0 +1,298 @@
+"""Benchmark of the stochastic-Galerkin slab operator apply (sg_apply).
+
+One step = one application y = A^(n) x of the SG slab operator
+(eq. local_rhs_tensor) to one slab vector, on the 2D 64x64 Q2, dG(1),
+M=4 / P=3 (35 chaos modes) workload: 16,641 nodes x 2 time nodes x 35 modes =
+1,164,870 unknowns.  Metric: GDoF*modes/s = unknowns x applies / s / 1e9.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one process per GPU; every rank applies the
+operator to its own replica of the workload (the apply has no exchange step
+on one node), value = all ranks' unknowns / max-over-ranks time ("weak").
+The reference arm times the CPU oracle (oracle/, FP64 numpy/scipy) on the
+host cores, rank 0 only.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SG operator applies"
+UNIT = "GDoF*modes/s"
+# FP64 FMA peak: 152 SMs x 2 FP64 FMA lanes per clock x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# algorithmic work of the sum-factorised apply per unknown (FP64 flop) and
+# the algorithmic HBM bytes per unknown (read x, write y once)
+FLOP_PER_UNKNOWN = 166.0
+BYTES_PER_UNKNOWN = 16.0
+L2_BYTES = 135_528_448
+
+
+def workload():
+    from paper_2605_21046_gb300 import inputs
+    return inputs.config_2d_q2_64()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_apply_rate(spec, budget_s=15.0, min_reps=1):
+    """Times the oracle's Kronecker-sum apply (set-up excluded) for about
+    budget_s seconds; returns (unknowns/s, reps, wall, cores used)."""
+    import numpy as np
+    from oracle import operator
+    from paper_2605_21046_gb300 import inputs
+    p = operator.SGProblem(spec)
+    x = inputs.random_vector(spec)
+    p.apply(x)  # warm
+    reps, t0, c0 = 0, time.perf_counter(), time.process_time()
+    while True:
+        p.apply(x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el > budget_s:
+            break
+        if el > budget_s and reps >= 1:
+            break
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    n = inputs.n_unknowns(spec)
+    return n * reps / wall, reps, wall, max(1, round(cpu / wall))
+
+
+def run_reference(args, world, rank):
+    spec = workload()
+    from paper_2605_21046_gb300 import inputs
+    if rank != 0:
+        return
+    per_step = []
+    cores = 1
+    for s in range(args.warmup + args.steps):
+        rate, reps, wall, cores = oracle_apply_rate(spec, budget_s=0.0, min_reps=1)
+        if s >= args.warmup:
+            per_step.append(wall / reps)
+    n = inputs.n_unknowns(spec)
+    t = sum(per_step)
+    value = n * len(per_step) / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec["name"], "unknowns": n, "mesh": "64x64 Q2",
+                                            "time": "dG(1)", "M": 4, "P": 3, "chaos_modes": 35},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(per_step)} full oracle applies of the {n}-unknown workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2605_21046_gb300 as sg
+    from paper_2605_21046_gb300 import build, inputs
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    spec = workload()
+    ctx = sg.sg_setup_spec(spec)
+    n = ctx.info["n_unknowns"]
+    # rotating x/y pairs whose total exceeds L2, so no step reads another's cache
+    vec_bytes = 8 * n
+    R = max(2, math.ceil(2.2 * L2_BYTES / (2 * vec_bytes)))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(inputs.SEED_X + rank)
+    X = [torch.rand(n, dtype=torch.float64, device=dev, generator=gen) * 2 - 1 for _ in range(R)]
+    Y = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(R)]
+    stream = torch.cuda.current_stream(dev)
+    for s in range(args.warmup):
+        sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for s in range(args.steps):
+            ev[s][0].record(stream)
+            sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
+            ev[s][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    clocks = clk.summary()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    t_launch = statistics.mean(launch_ms) / 1e3
+    value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
+    assert torch.isfinite(Y[0]).all()
+
+    # end to end through the host-buffer entry point: pinned x in, y out
+    xh = X[0].cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(3):
+        sg.sg_apply_host(ctx, 0, xh, yh)
+    k_e2e = max(3, min(args.steps, 200))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        sg.sg_apply_host(ctx, 0, xh, yh)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = world * n * k_e2e / e2e_s / 1e9
+
+    pk = peaks()
+    achieved_tf = FLOP_PER_UNKNOWN * n / t_launch / 1e12
+    hbm_gbs = BYTES_PER_UNKNOWN * n / t_launch / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, reps, wall, cores = oracle_apply_rate(spec, budget_s=args.cpu_seconds)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{reps} full oracle applies of the {n}-unknown workload in {wall:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "unknowns": n, "mesh": "64x64 Q2 unit square",
+                       "time": "dG(1)", "M": 4, "P": 3, "chaos_modes": 35,
+                       "l2": f"{R} rotating x/y pairs, {2 * R * vec_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2",
+                       "parallelism": f"replicas x{world}",
+                       "tile": list(ctx.info["tile"]), "threads": ctx.info["threads"]},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes},
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "sg_apply (init + tile kernel, per-launch CUDA events)",
+                         "hbm": {"achieved": hbm_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                                 "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0)}},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.destroy()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

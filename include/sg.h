@@ -1,0 +1,178 @@
+/*
+ * sg.h - C ABI of the GB300 stochastic-Galerkin slab-operator library (libsg).
+ *
+ * The library applies the coupled stochastic-Galerkin (SG) space-time slab
+ * operator of the random heat equation (Problem "tensor-product slab system",
+ * eq. local_rhs_tensor of the paper):
+ *
+ *     A^(n) = M_xi (x) A_t (x) M_x  +  sum_{mu in M_a} G_mu (x) B_t (x) K_mu
+ *
+ * with Q_k finite elements in space (Sec. 3.1), dG(r) in time with the right
+ * Gauss-Radau nodal basis (Sec. 3.2, eqs. At, Bt), a total-degree Hermite chaos
+ * Lambda_p in M standard Gaussian variables (Sec. 3.3), M_xi = I and the
+ * triple-product matrices G_mu (eq. triple_stoch), and a coefficient given as
+ * a finite chaos expansion a = sum_mu a_mu(x) Psi_mu(xi) (eq. coeff_expansion).
+ * The operator is never assembled (the matrix-free remark after eq.
+ * local_rhs_tensor): only its action is computed, by sum-factorised CUDA
+ * kernels for sm_103a.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Vector layout.  A slab vector holds N = N_xi * N_t * N_x doubles with index
+ *     (alpha * N_t + i) * N_x + m,
+ * alpha the chaos index in the order returned by sg_get_multi_indices
+ * (ascending total degree; inside a degree alpha_1 descending, then alpha_2,
+ * ...), i = 0..r the time node (right Radau nodes ascending), m the spatial
+ * node, lexicographic with x fastest over all (k*cells_d + 1) nodes per
+ * direction, boundary nodes included.
+ *
+ * Dirichlet rows.  V_h is a subspace of H^1_0 (Sec. 3.1).  Boundary nodes are
+ * stored; every product reads them as 0 and the operator's boundary rows are
+ * the identity: y_b = x_b.
+ *
+ * Ownership.  The caller owns every vector it passes (device or host memory
+ * as stated per call); the library never frees them and keeps no pointer to
+ * them after a call returns.  The context owns all tables and workspaces it
+ * allocates; sg_destroy releases them.
+ *
+ * Streams and errors.  Device calls are stream ordered and asynchronous: the
+ * status reports argument validation and launch errors only.  A returned
+ * error leaves the context usable.  sg_last_error() gives a one-line message
+ * for the most recent failing call on the calling thread.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque context: one discretised problem resident on the current device. */
+typedef struct sg_ctx sg_ctx;
+
+/* A cudaStream_t (the same type); NULL means the legacy default stream. */
+typedef struct CUstream_st* sg_stream;
+
+typedef enum {
+  SG_OK = 0,
+  SG_ERR_ARG = 1,          /* invalid argument (null, size, alias, range)   */
+  SG_ERR_CUDA = 2,         /* a CUDA runtime call failed                    */
+  SG_ERR_OOM = 3,          /* device or host allocation failed              */
+  SG_ERR_UNSUPPORTED = 4,  /* valid but not built (degree, dimension, size) */
+  SG_ERR_NOT_CONVERGED = 5,
+  SG_ERR_NONFINITE = 6,
+  SG_ERR_TIMEOUT = 7
+} sg_status;
+
+/* Spatial factor kinds of a separable coefficient piece (see sg_coeff). */
+enum { SG_F_ONE = 0, SG_F_SIN = 1, SG_F_POW = 2 };
+
+/* Arithmetic of the operator kernels. */
+enum { SG_PREC_FP64 = 0 };
+
+/* Uniform Cartesian mesh of [lo, hi] (dim = 2 or 3; entries beyond dim are
+ * ignored).  cells[d] >= 1 cells in direction d. */
+typedef struct {
+  int dim;
+  int cells[3];
+  double lo[3];
+  double hi[3];
+} sg_mesh;
+
+/* Coefficient expansion a(x, xi) = sum_mu a_mu(x) Psi_mu(xi)
+ * (eq. coeff_expansion) given as n_pieces separable pieces; piece p adds
+ *     amp[p] * s_p(cell) * prod_d f(kind[p][d], k[p][d], x_d)
+ * to a_{mu_p}(x), with f(SG_F_ONE) = 1, f(SG_F_SIN, k, s) = sin(k pi s),
+ * f(SG_F_POW, k, s) = s^k of the physical coordinate s, and s_p(cell) = 1
+ * unless cell_scale[p] is given (one value per cell, cells lexicographic with
+ * x fastest).  The distinct mu form the active set M_a, in order of first
+ * appearance.  All arrays are host memory, read during sg_setup only.
+ *   mu           n_pieces x M chaos multi-indices (row major)
+ *   amp          n_pieces amplitudes
+ *   factor_kind  n_pieces x 3 kinds (entries beyond dim ignored)
+ *   factor_k     n_pieces x 3 integer parameters
+ *   cell_scale   NULL, or n_pieces pointers each NULL or n_cells doubles */
+typedef struct {
+  int n_pieces;
+  const int* mu;
+  const double* amp;
+  const int* factor_kind;
+  const int* factor_k;
+  const double* const* cell_scale;
+} sg_coeff;
+
+/* Sizes of a set-up problem. */
+typedef struct {
+  int dim, fe_degree, time_degree, M, chaos_order;
+  int n_xi;        /* N_xi = binom(M + p, p)            */
+  int n_t;         /* N_t = r + 1                       */
+  int n_terms;     /* |M_a|                             */
+  int g_nnz;       /* nonzeros of sum_mu |G_mu| pattern */
+  int n_slabs;
+  int64_t n_x;     /* spatial nodes, boundary included  */
+  int64_t n_cells;
+  int64_t n_unknowns; /* N_xi * N_t * N_x per slab      */
+  double tau;      /* slab length T / n_slabs           */
+  int tile[3];     /* cells per CTA tile of sg_apply    */
+  int threads;     /* threads per CTA of sg_apply       */
+  int smem_bytes;  /* dynamic shared memory per CTA     */
+} sg_info;
+
+/* sg_setup - discretise one problem and make it resident on the current
+ * CUDA device (Sec. 3: Q_k in space, dG(r) in time, Lambda_p chaos; Sec. 3.5:
+ * time matrices eqs. At/Bt/Ct, G_mu eq. triple_stoch and its factorisation
+ * remark, coefficient modes eq. coeff_expansion).
+ *   mesh         uniform Cartesian mesh (host)
+ *   fe_degree    k = 1, 2 or 3 (3D: 1 or 2)
+ *   time_degree  r = 0..3 (N_t = r + 1)
+ *   n_slabs, T   uniform slabs of length tau = T / n_slabs (tau > 0)
+ *   M, chaos_order  M >= 1 Gaussian variables, total degree p >= 0
+ *   coef         coefficient expansion (host), see sg_coeff
+ *   precision    SG_PREC_FP64
+ *   out          receives the new context; untouched on error
+ * Errors: SG_ERR_ARG for invalid sizes or pointers, SG_ERR_UNSUPPORTED for
+ * degrees or sizes no kernel is built for, SG_ERR_OOM, SG_ERR_CUDA. */
+sg_status sg_setup(const sg_mesh* mesh, int fe_degree, int time_degree, int n_slabs,
+                   double T, int M, int chaos_order, const sg_coeff* coef, int precision,
+                   sg_ctx** out);
+
+/* sg_apply - y = A^(n) x on slab n (eq. local_rhs_tensor), or y = A^(n)^T x
+ * when transpose != 0 (A_t replaced by A_t^T; G_mu, B_t, K_mu are symmetric).
+ * The slab operator is the same on every slab of a uniform partition; slab is
+ * validated (0 <= slab < n_slabs).
+ *   x, y    DEVICE pointers to n_unknowns doubles in the layout above,
+ *           8-byte aligned, not overlapping (x == y is SG_ERR_ARG)
+ *   stream  stream the kernels are launched on
+ * Asynchronous: y is complete when the stream reaches this point. */
+sg_status sg_apply(sg_ctx* ctx, int slab, const double* x, double* y, int transpose,
+                   sg_stream stream);
+
+/* sg_apply_host - as sg_apply with HOST vectors: copies x to a device
+ * workspace owned by the context (allocated on the first call), applies, and
+ * copies y back.  Synchronous: returns when y_host is written.  Pinned host
+ * memory gives full copy bandwidth; pageable memory works. */
+sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
+                        int transpose);
+
+/* sg_get_info - sizes and launch shape of a context (host struct out). */
+sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);
+
+/* sg_get_multi_indices - the chaos index set Lambda_p (Sec. 3.3) in the
+ * library's order: out receives n_xi x M ints (host, row major). */
+sg_status sg_get_multi_indices(const sg_ctx* ctx, int* out);
+
+/* sg_destroy - release a context and everything it owns (NULL is a no-op).
+ * Synchronises the device work of the context first. */
+void sg_destroy(sg_ctx* ctx);
+
+/* Static strings, never freed by the caller. */
+const char* sg_status_string(sg_status s);
+const char* sg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

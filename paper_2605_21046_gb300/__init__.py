@@ -1,0 +1,206 @@
+"""GB300-native stochastic-Galerkin slab operator for the random heat equation.
+
+Python binding of the C-ABI library libsg (include/sg.h).  The functions keep
+the C names; they only marshal arguments (torch CUDA tensors for device
+vectors, numpy arrays for host vectors) and raise ``SGError`` on a non-zero
+status.  Every step of the operator runs in the library's CUDA kernels; there
+is no CPU fallback: without libsg.so every call raises.
+
+    ctx = sg_setup(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef)
+    sg_apply(ctx, slab, x, y)            # y = A^(n) x on the current stream
+    sg_destroy(ctx)
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+
+__all__ = ["SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+           "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
+
+_KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
+
+
+class SGError(RuntimeError):
+    def __init__(self, status, where):
+        lib = _abi.load()
+        super().__init__(f"{where}: {lib.sg_status_string(status).decode()} "
+                         f"({lib.sg_last_error().decode()})")
+        self.status = status
+
+
+def _check(status, where):
+    if status != _abi.SG_OK:
+        raise SGError(status, where)
+
+
+class SGContext:
+    """Owns one sg_ctx; ``info`` holds its sizes."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+        self.info = sg_get_info(self)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("context destroyed")
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.info["n_xi"], self.info["n_t"], self.info["n_x"])
+
+    def apply(self, x, y=None, slab=0, transpose=False, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        sg_apply(self, slab, x, y, transpose, stream)
+        return y
+
+    def destroy(self):
+        if self._h:
+            _abi.load().sg_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def mesh_spec(dim, cells, lo, hi):
+    m = _abi.sg_mesh()
+    m.dim = dim
+    for d in range(3):
+        m.cells[d] = int(cells[d]) if d < dim else 1
+        m.lo[d] = float(lo[d]) if d < dim else 0.0
+        m.hi[d] = float(hi[d]) if d < dim else 1.0
+    return m
+
+
+def _coeff_struct(pieces, M, dim):
+    n = len(pieces)
+    mu = np.zeros((n, M), dtype=np.int32)
+    amp = np.zeros(n, dtype=np.float64)
+    kind = np.zeros((n, 3), dtype=np.int32)
+    kk = np.zeros((n, 3), dtype=np.int32)
+    scales = (C.POINTER(C.c_double) * n)()
+    keep = [mu, amp, kind, kk, scales]
+    any_scale = False
+    for i, p in enumerate(pieces):
+        mu[i] = np.asarray(p["mu"], dtype=np.int32)
+        amp[i] = float(p["amp"])
+        for d in range(min(dim, 3, len(p["factors"]))):
+            kd, kv = p["factors"][d]
+            kind[i, d] = _KIND[kd]
+            kk[i, d] = int(kv)
+        cs = p.get("cell_scale")
+        if cs is not None:
+            arr = np.ascontiguousarray(cs, dtype=np.float64)
+            keep.append(arr)
+            scales[i] = arr.ctypes.data_as(C.POINTER(C.c_double))
+            any_scale = True
+    s = _abi.sg_coeff()
+    s.n_pieces = n
+    s.mu = mu.ctypes.data_as(C.POINTER(C.c_int))
+    s.amp = amp.ctypes.data_as(C.POINTER(C.c_double))
+    s.factor_kind = kind.ctypes.data_as(C.POINTER(C.c_int))
+    s.factor_k = kk.ctypes.data_as(C.POINTER(C.c_int))
+    s.cell_scale = C.cast(scales, C.POINTER(C.POINTER(C.c_double))) if any_scale else None
+    return s, keep
+
+
+def sg_setup(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef, precision=0):
+    """sg_setup of include/sg.h.  ``mesh`` is an sg_mesh or a dict with
+    dim/cells/lo/hi; ``coef`` a list of separable pieces
+    {"mu", "amp", "factors": [(kind, k) per direction], "cell_scale"}."""
+    lib = _abi.load()
+    if isinstance(mesh, dict):
+        mesh = mesh_spec(mesh["dim"], mesh["cells"], mesh["lo"], mesh["hi"])
+    cs, keep = _coeff_struct(coef, M, mesh.dim)
+    h = C.c_void_p()
+    _check(lib.sg_setup(C.byref(mesh), fe_degree, time_degree, n_slabs, float(T), M, chaos_order,
+                        C.byref(cs), precision, C.byref(h)), "sg_setup")
+    del keep
+    return SGContext(h.value)
+
+
+def sg_setup_spec(spec):
+    """sg_setup from a problem spec dict (the format of ``inputs``)."""
+    return sg_setup(dict(dim=spec["dim"], cells=spec["cells"], lo=spec["lo"], hi=spec["hi"]),
+                    spec["k"], spec["r"], spec["n_slabs"], spec["T"], spec["M"], spec["P"],
+                    spec["coef"])
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def sg_apply(ctx, slab, x, y, transpose=False, stream=None):
+    """y = A^(n) x (or A^T x) for torch float64 CUDA tensors of n_unknowns
+    elements, launched on ``stream`` (default: torch's current stream)."""
+    lib = _abi.load()
+    n = ctx.info["n_unknowns"]
+    for t in (x, y):
+        if not (t.is_cuda and t.dtype.itemsize == 8 and str(t.dtype) == "torch.float64"):
+            raise TypeError("sg_apply wants float64 CUDA tensors")
+        if t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"sg_apply wants contiguous tensors of {n} elements")
+    _check(lib.sg_apply(ctx.handle, int(slab), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                        int(bool(transpose)), C.c_void_p(_stream_handle(stream))), "sg_apply")
+    return y
+
+
+def sg_apply_host(ctx, slab, x, y=None, transpose=False):
+    """Host-buffer variant: numpy float64 (or pinned torch CPU tensors) in,
+    result written to ``y`` (allocated if None); synchronous."""
+    lib = _abi.load()
+    n = ctx.info["n_unknowns"]
+
+    def ptr(a):
+        if hasattr(a, "data_ptr"):
+            if a.numel() != n or not a.is_contiguous() or a.is_cuda:
+                raise ValueError("host tensor of n_unknowns contiguous elements expected")
+            return a.data_ptr()
+        if a.dtype != np.float64 or a.size != n or not a.flags.c_contiguous:
+            raise ValueError("float64 contiguous host array of n_unknowns elements expected")
+        return a.ctypes.data
+    if y is None:
+        y = np.empty(n, dtype=np.float64)
+    _check(lib.sg_apply_host(ctx.handle, int(slab), C.c_void_p(ptr(x)), C.c_void_p(ptr(y)),
+                             int(bool(transpose))), "sg_apply_host")
+    return y
+
+
+def sg_get_info(ctx):
+    lib = _abi.load()
+    info = _abi.sg_info()
+    _check(lib.sg_get_info(ctx.handle, C.byref(info)), "sg_get_info")
+    out = {name: getattr(info, name) for name, _ in _abi.sg_info._fields_}
+    out["tile"] = tuple(info.tile)
+    return out
+
+
+def sg_get_multi_indices(ctx):
+    lib = _abi.load()
+    n, M = ctx.info["n_xi"], ctx.info["M"]
+    out = np.zeros((n, M), dtype=np.int32)
+    _check(lib.sg_get_multi_indices(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_int))),
+           "sg_get_multi_indices")
+    return out
+
+
+def sg_destroy(ctx):
+    ctx.destroy()
+
+
+def sg_status_string(status):
+    return _abi.load().sg_status_string(status).decode()

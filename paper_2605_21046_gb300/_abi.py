@@ -1,0 +1,68 @@
+"""ctypes declarations of the C ABI in include/sg.h (argument marshalling only)."""
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsg.so")
+
+SG_OK, SG_ERR_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+SG_ERR_NOT_CONVERGED, SG_ERR_NONFINITE, SG_ERR_TIMEOUT = 5, 6, 7
+SG_F_ONE, SG_F_SIN, SG_F_POW = 0, 1, 2
+SG_PREC_FP64 = 0
+
+# every symbol include/sg.h declares
+EXPORTED = ["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
+            "sg_destroy", "sg_status_string", "sg_last_error"]
+
+
+class sg_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("cells", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3)]
+
+
+class sg_coeff(C.Structure):
+    _fields_ = [("n_pieces", C.c_int), ("mu", C.POINTER(C.c_int)), ("amp", C.POINTER(C.c_double)),
+                ("factor_kind", C.POINTER(C.c_int)), ("factor_k", C.POINTER(C.c_int)),
+                ("cell_scale", C.POINTER(C.POINTER(C.c_double)))]
+
+
+class sg_info(C.Structure):
+    _fields_ = [("dim", C.c_int), ("fe_degree", C.c_int), ("time_degree", C.c_int), ("M", C.c_int),
+                ("chaos_order", C.c_int), ("n_xi", C.c_int), ("n_t", C.c_int), ("n_terms", C.c_int),
+                ("g_nnz", C.c_int), ("n_slabs", C.c_int), ("n_x", C.c_int64), ("n_cells", C.c_int64),
+                ("n_unknowns", C.c_int64), ("tau", C.c_double), ("tile", C.c_int * 3),
+                ("threads", C.c_int), ("smem_bytes", C.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load libsg.so once; raises if it has not been built (there is no
+    fallback implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsg.so is not built ({LIB_PATH}); run paper_2605_21046_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    lib.sg_setup.argtypes = [C.POINTER(sg_mesh), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(sg_coeff), C.c_int, C.POINTER(vp)]
+    lib.sg_setup.restype = C.c_int
+    lib.sg_apply.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
+    lib.sg_apply.restype = C.c_int
+    lib.sg_apply_host.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+    lib.sg_apply_host.restype = C.c_int
+    lib.sg_get_info.argtypes = [vp, C.POINTER(sg_info)]
+    lib.sg_get_info.restype = C.c_int
+    lib.sg_get_multi_indices.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.sg_get_multi_indices.restype = C.c_int
+    lib.sg_destroy.argtypes = [vp]
+    lib.sg_destroy.restype = None
+    lib.sg_status_string.argtypes = [C.c_int]
+    lib.sg_status_string.restype = C.c_char_p
+    lib.sg_last_error.argtypes = []
+    lib.sg_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib

@@ -1,0 +1,169 @@
+"""Parity of sg_apply (CUDA, through the C ABI) with the oracle's Kronecker-sum
+apply of eq. local_rhs_tensor, element by element on seeded inputs.
+
+Tolerance: the FP64 apply must match to 1e-12 relative, measured as
+max |y_gpu - y_oracle| / max |y_oracle|."""
+import numpy as np
+import pytest
+
+import paper_2605_21046_gb300 as sg
+from paper_2605_21046_gb300 import inputs as I
+from oracle import operator
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def gpu_apply(torch, spec, x, transpose=False, ctx=None):
+    own = ctx is None
+    ctx = ctx or sg.sg_setup_spec(spec)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    sg.sg_apply(ctx, 0, xd, yd, transpose)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    if own:
+        ctx.destroy()
+    return y
+
+
+def small(dim, cells, k, r, M, P, coef=None, lo=None, hi=None):
+    if coef is None:
+        freqs = [tuple(((m + d) % 3) + 1 for d in range(dim)) for m in range(M)]
+        coef = I.linear_sine_coef(M, dim, 0.08, freqs)
+    return dict(name="t", dim=dim, cells=cells, lo=lo or (0.0,) * dim, hi=hi or (1.0,) * dim, k=k, r=r,
+                n_slabs=3, T=0.9, M=M, P=P, coef=coef)
+
+
+FULL_CASES = {
+    "config-2d-q1-8x8": I.config_small_2d_q1(),
+    "config-2d-q2-64x64": I.config_2d_q2_64(),
+    "ragged-2d-q2-13x7": small(2, (13, 7), 2, 1, 2, 3),
+    "ragged-2d-q1-9x11-r0": small(2, (9, 11), 1, 0, 3, 2),
+    "2d-q3-dg3-6x5": small(2, (6, 5), 3, 3, 2, 2, lo=(-1.0, -1.0)),
+    "2d-q2-dg2-P0": small(2, (7, 6), 2, 2, 2, 0),
+    "2d-q2-M1P5": small(2, (5, 9), 2, 1, 1, 5),
+    "3d-q1-5x4x3": small(3, (5, 4, 3), 1, 1, 2, 2),
+    "3d-q2-4x3x5": small(3, (4, 3, 5), 2, 1, 3, 2, hi=(1.0, 0.6, 1.3)),
+    "3d-q2-r0-3x3x3": small(3, (3, 3, 3), 2, 0, 2, 1),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL_CASES))
+def test_apply_matches_oracle_full(cuda, name):
+    spec = FULL_CASES[name]
+    p = operator.SGProblem(spec)
+    x = I.random_vector(spec, seed=hash(name) % 2**32)
+    for tr in (False, True):
+        want = p.apply(x, transpose=tr).reshape(-1)
+        got = gpu_apply(cuda, spec, x, transpose=tr)
+        assert np.all(np.isfinite(got))
+        assert _rel(got, want) < TOL, (name, tr, _rel(got, want))
+
+
+def test_paper_squared_coefficient(cuda):
+    # the paper's benchmark coefficient d_min + (xi1 x1^2 + xi2 x1 x2 + xi3 x2^2 + xi4)^2 in the
+    # Hermite basis: 11 modes of even degree, Q3 / dG(3) on (-1, 1)^2
+    from math import sqrt
+    g = [[("pow", 2), ("one", 0)], [("pow", 1), ("pow", 1)], [("one", 0), ("pow", 2)], [("one", 0), ("one", 0)]]
+    def mul(f1, f2):
+        return [(("pow", (f1[d][1] if f1[d][0] == "pow" else 0) + (f2[d][1] if f2[d][0] == "pow" else 0)))
+                for d in range(2)]
+    M = 4
+    pieces = [dict(mu=(0,) * M, amp=0.2, factors=[("one", 0)] * 2)]
+    for m in range(M):
+        pieces.append(dict(mu=(0,) * M, amp=1.0, factors=mul(g[m], g[m])))
+        pieces.append(dict(mu=tuple(2 * (i == m) for i in range(M)), amp=sqrt(2.0), factors=mul(g[m], g[m])))
+    for m in range(M):
+        for n in range(m + 1, M):
+            pieces.append(dict(mu=tuple(int(i in (m, n)) for i in range(M)), amp=2.0, factors=mul(g[m], g[n])))
+    spec = dict(name="paper", dim=2, cells=(6, 6), lo=(-1.0, -1.0), hi=(1.0, 1.0), k=3, r=3, n_slabs=16, T=1.0,
+                M=M, P=2, coef=pieces)
+    p = operator.SGProblem(spec)
+    assert len(p.mus) == 11
+    x = I.random_vector(spec, seed=5)
+    assert _rel(gpu_apply(cuda, spec, x), p.apply(x).reshape(-1)) < TOL
+
+
+@pytest.mark.parametrize("maker", [I.config_3d_q2_32, I.config_2d_q2_128])
+def test_apply_full_size_sampled(cuda, maker):
+    spec = maker()
+    ctx = sg.sg_setup_spec(spec)
+    x = I.random_vector(spec)
+    y = gpu_apply(cuda, spec, x, ctx=ctx).reshape(ctx.shape)
+    ctx.destroy()
+    p = operator.SGProblem(spec, assemble_space=False)
+    rng = np.random.default_rng(17)
+    outs = [(int(rng.integers(p.n_xi)), int(rng.integers(p.n_t)), int(rng.integers(p.n_x))) for _ in range(60)]
+    outs += [(p.n_xi - 1, 1, p.n_x // 2), (0, 0, p.n_x - 1), (0, 0, 0)]
+    want = p.apply_rows(x, outs)
+    got = np.array([y[a, i, m] for a, i, m in outs])
+    scale = np.abs(want).max()
+    assert np.abs(got - want).max() / scale < TOL
+    assert np.all(np.isfinite(y))
+
+
+def test_multi_index_order_matches_oracle(cuda):
+    from oracle import hermite
+    for spec in (I.config_small_2d_q1(), small(2, (3, 3), 1, 1, 4, 4), small(3, (2, 2, 2), 1, 1, 3, 3)):
+        ctx = sg.sg_setup_spec(spec)
+        assert np.array_equal(sg.sg_get_multi_indices(ctx), hermite.multi_indices(spec["M"], spec["P"]))
+        ctx.destroy()
+
+
+def test_host_entry_point_matches(cuda):
+    spec = I.config_2d_q2_64()
+    ctx = sg.sg_setup_spec(spec)
+    x = I.random_vector(spec, seed=3)
+    y_dev = gpu_apply(cuda, spec, x, ctx=ctx)
+    y_host = sg.sg_apply_host(ctx, 0, x)
+    pinned = cuda.from_numpy(x).pin_memory()
+    y_pin = cuda.empty_like(pinned).pin_memory()
+    sg.sg_apply_host(ctx, 1, pinned, y_pin, transpose=False)
+    ctx.destroy()
+    assert _rel(y_host, y_dev) < 1e-15
+    assert _rel(y_pin.numpy(), y_dev) < 1e-15
+
+
+def test_all_dirichlet_mesh_is_identity(cuda):
+    spec = small(2, (1, 1), 1, 1, 2, 2)
+    x = I.random_vector(spec, seed=9)
+    assert np.array_equal(gpu_apply(cuda, spec, x), x)
+
+
+def test_repeat_is_stable(cuda):
+    spec = I.config_2d_q2_64()
+    ctx = sg.sg_setup_spec(spec)
+    x = I.random_vector(spec, seed=4)
+    a = gpu_apply(cuda, spec, x, ctx=ctx)
+    b = gpu_apply(cuda, spec, x, ctx=ctx)
+    ctx.destroy()
+    assert _rel(a, b) < 1e-15
+
+
+def test_errors_are_reported_not_faulted(cuda):
+    torch = cuda
+    spec = I.config_small_2d_q1()
+    ctx = sg.sg_setup_spec(spec)
+    x = torch.from_numpy(I.random_vector(spec)).cuda()
+    with pytest.raises(sg.SGError):
+        sg.sg_apply(ctx, 0, x, x)                            # in place
+    with pytest.raises(sg.SGError):
+        sg.sg_apply(ctx, 10, x, torch.empty_like(x))         # slab out of range
+    with pytest.raises(ValueError):
+        sg.sg_apply(ctx, 0, x[:-1], torch.empty_like(x[:-1]))
+    # a host pointer straight through the C ABI is rejected before launch
+    import ctypes as C
+    from paper_2605_21046_gb300 import _abi
+    host = np.zeros(ctx.info["n_unknowns"])
+    st = _abi.load().sg_apply(ctx.handle, 0, C.c_void_p(host.ctypes.data), C.c_void_p(x.data_ptr()), 0, None)
+    assert st == _abi.SG_ERR_ARG
+    # the context is still usable
+    y = torch.empty_like(x)
+    sg.sg_apply(ctx, 0, x, y)
+    torch.cuda.synchronize()
+    ctx.destroy()

@@ -37,7 +37,7 @@ BYTES_PER_UNKNOWN = 16.0
 L2_BYTES = 135_528_448
 # dram__bytes_read.sum + dram__bytes_write.sum of one tile-kernel launch on this
 # workload (ncu capture summarised in profiles/); None once the kernel changes
-NCU_TRAFFIC_BYTES = 19.42e6 + 0.08e6
+NCU_TRAFFIC_BYTES = None
 
 
 def workload():
@@ -66,6 +66,8 @@ class ClockSampler:
         self.path = None
 
     def __enter__(self):
+        if self.gpu < 0:
+            return self
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -194,6 +196,33 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_clocks, local):
+    """Device time of `steps` applies over rotating buffers; returns
+    (elapsed_ms max over ranks, mean per-launch seconds, clocks)."""
+    R = len(X)
+    for s in range(warmup):
+        sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(local if sample_clocks else -1) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for s in range(steps):
+            ev[s][0].record(stream)
+            sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
+            ev[s][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    clocks = clk.summary() if sample_clocks else None
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
+    t_launch = statistics.mean(a.elapsed_time(b) for a, b in ev) / 1e3
+    return elapsed_ms, t_launch, clocks
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2605_21046_gb300 as sg
@@ -202,7 +231,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     spec = workload()
-    ctx = sg.sg_setup_spec(spec)
+    ctx = sg.sg_setup_spec(spec, sg.SG_PREC_FP64)
     n = ctx.info["n_unknowns"]
     # rotating x/y pairs whose total exceeds L2, so no step reads another's cache
     vec_bytes = 8 * n
@@ -212,30 +241,26 @@ def run_ours(args, world, rank, local):
     X = [torch.rand(n, dtype=torch.float64, device=dev, generator=gen) * 2 - 1 for _ in range(R)]
     Y = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(R)]
     stream = torch.cuda.current_stream(dev)
-    for s in range(args.warmup):
-        sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
-    torch.cuda.synchronize(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        barrier(world)
-        torch.cuda.synchronize(dev)
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for s in range(args.steps):
-            ev[s][0].record(stream)
-            sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
-            ev[s][1].record(stream)
-        t_end.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(world)
-    clocks = clk.summary()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
-    elapsed_ms = max_over_ranks(elapsed_ms, world)
-    t_launch = statistics.mean(launch_ms) / 1e3
+    elapsed_ms, t_launch, clocks = time_applies(sg, torch, ctx, X, Y, args.steps, args.warmup, stream,
+                                                world, True, local)
     value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
     assert torch.isfinite(Y[0]).all()
+    y64 = Y[0].clone()
+
+    # double-word variant (same tolerance), reported beside the FP64 headline
+    dw = None
+    if not args.no_dw:
+        ctx_dw = sg.sg_setup_spec(spec, sg.SG_PREC_DW)
+        e_dw, t_dw, _ = time_applies(sg, torch, ctx_dw, X, Y, args.steps, args.warmup, stream, world, False, local)
+        sg.sg_apply(ctx_dw, 0, X[0], Y[0], False, stream)
+        torch.cuda.synchronize()
+        err = float((Y[0] - y64).abs().max() / y64.abs().max())
+        v_dw = world * n * args.steps / (e_dw / 1e3) / 1e9
+        dw = {"value": v_dw, "unit": UNIT, "ms_per_step": e_dw / args.steps, "dtype": "f32x2 double-word",
+              "speedup_vs_fp64": v_dw / value, "max_rel_diff_vs_fp64": err,
+              "fp64_equivalent_tflops": FLOP_PER_UNKNOWN * n / t_dw / 1e12,
+              "gpu_launches": 2 * args.steps}
+        ctx_dw.destroy()
 
     # end to end through the host-buffer entry point: pinned x in, y out
     xh = X[0].cpu().pin_memory()
@@ -267,16 +292,18 @@ def run_ours(args, world, rank, local):
                        "time": "dG(1)", "M": 4, "P": 3, "chaos_modes": 35,
                        "l2": f"{R} rotating x/y pairs, {2 * R * vec_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2",
                        "parallelism": f"replicas x{world}",
-                       "tile": list(ctx.info["tile"]), "threads": ctx.info["threads"]},
+                       "chunk_cells": ctx.info["chunk"], "grid": ctx.info["grid"],
+                       "threads": ctx.info["threads"]},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC_BYTES,
-                         "kernel": "sg_apply (init + tile kernel, per-launch CUDA events)",
+                         "kernel": "sg_apply (init + chunk kernel, per-launch CUDA events)",
                          "hbm": {"achieved": hbm_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                                  "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0)}},
             "cpu_baseline": cpu,
+            "variants": {"dw": dw},
         }
         print(json.dumps(line), flush=True)
     ctx.destroy()
@@ -290,6 +317,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dw", action="store_true", help="skip the double-word variant")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_init()

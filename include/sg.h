@@ -69,8 +69,15 @@ typedef enum {
 /* Spatial factor kinds of a separable coefficient piece (see sg_coeff). */
 enum { SG_F_ONE = 0, SG_F_SIN = 1, SG_F_POW = 2 };
 
-/* Arithmetic of the operator kernels. */
-enum { SG_PREC_FP64 = 0 };
+/* Arithmetic of the operator kernels.
+ *   SG_PREC_FP64  native IEEE double (the FP64 pipe).
+ *   SG_PREC_DW    double-word arithmetic: every value is an unevaluated sum of
+ *                 two floats, computed on the FP32 pipe with error-free
+ *                 transformations (exact FMA product errors, TwoSum); about 48
+ *                 significant bits.  Inputs and outputs stay double.  Inputs
+ *                 with magnitude below 2^-74 keep only 24 significant bits.
+ *                 Meets the 1e-12 relative apply tolerance of the FP64 path. */
+enum { SG_PREC_FP64 = 0, SG_PREC_DW = 1 };
 
 /* Uniform Cartesian mesh of [lo, hi] (dim = 2 or 3; entries beyond dim are
  * ignored).  cells[d] >= 1 cells in direction d. */
@@ -106,6 +113,7 @@ typedef struct {
 /* Sizes of a set-up problem. */
 typedef struct {
   int dim, fe_degree, time_degree, M, chaos_order;
+  int precision;   /* SG_PREC_*                         */
   int n_xi;        /* N_xi = binom(M + p, p)            */
   int n_t;         /* N_t = r + 1                       */
   int n_terms;     /* |M_a|                             */
@@ -115,7 +123,8 @@ typedef struct {
   int64_t n_cells;
   int64_t n_unknowns; /* N_xi * N_t * N_x per slab      */
   double tau;      /* slab length T / n_slabs           */
-  int tile[3];     /* cells per CTA tile of sg_apply    */
+  int chunk;       /* cells per shared-memory chunk of sg_apply */
+  int grid;        /* persistent CTAs of sg_apply       */
   int threads;     /* threads per CTA of sg_apply       */
   int smem_bytes;  /* dynamic shared memory per CTA     */
 } sg_info;
@@ -130,7 +139,7 @@ typedef struct {
  *   n_slabs, T   uniform slabs of length tau = T / n_slabs (tau > 0)
  *   M, chaos_order  M >= 1 Gaussian variables, total degree p >= 0
  *   coef         coefficient expansion (host), see sg_coeff
- *   precision    SG_PREC_FP64
+ *   precision    SG_PREC_FP64 or SG_PREC_DW
  *   out          receives the new context; untouched on error
  * Errors: SG_ERR_ARG for invalid sizes or pointers, SG_ERR_UNSUPPORTED for
  * degrees or sizes no kernel is built for, SG_ERR_OOM, SG_ERR_CUDA. */

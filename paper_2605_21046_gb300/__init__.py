@@ -16,7 +16,9 @@ import numpy as np
 
 from . import _abi
 
-__all__ = ["SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+SG_PREC_FP64, SG_PREC_DW = _abi.SG_PREC_FP64, _abi.SG_PREC_DW
+
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -128,11 +130,11 @@ def sg_setup(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef, pre
     return SGContext(h.value)
 
 
-def sg_setup_spec(spec):
+def sg_setup_spec(spec, precision=0):
     """sg_setup from a problem spec dict (the format of ``inputs``)."""
     return sg_setup(dict(dim=spec["dim"], cells=spec["cells"], lo=spec["lo"], hi=spec["hi"]),
                     spec["k"], spec["r"], spec["n_slabs"], spec["T"], spec["M"], spec["P"],
-                    spec["coef"])
+                    spec["coef"], precision)
 
 
 def _stream_handle(stream):
@@ -184,9 +186,7 @@ def sg_get_info(ctx):
     lib = _abi.load()
     info = _abi.sg_info()
     _check(lib.sg_get_info(ctx.handle, C.byref(info)), "sg_get_info")
-    out = {name: getattr(info, name) for name, _ in _abi.sg_info._fields_}
-    out["tile"] = tuple(info.tile)
-    return out
+    return {name: getattr(info, name) for name, _ in _abi.sg_info._fields_}
 
 
 def sg_get_multi_indices(ctx):

@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(PKG, "libsg.so")
 SG_OK, SG_ERR_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 SG_ERR_NOT_CONVERGED, SG_ERR_NONFINITE, SG_ERR_TIMEOUT = 5, 6, 7
 SG_F_ONE, SG_F_SIN, SG_F_POW = 0, 1, 2
-SG_PREC_FP64 = 0
+SG_PREC_FP64, SG_PREC_DW = 0, 1
 
 # every symbol include/sg.h declares
 EXPORTED = ["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
@@ -28,10 +28,10 @@ class sg_coeff(C.Structure):
 
 class sg_info(C.Structure):
     _fields_ = [("dim", C.c_int), ("fe_degree", C.c_int), ("time_degree", C.c_int), ("M", C.c_int),
-                ("chaos_order", C.c_int), ("n_xi", C.c_int), ("n_t", C.c_int), ("n_terms", C.c_int),
+                ("chaos_order", C.c_int), ("precision", C.c_int), ("n_xi", C.c_int), ("n_t", C.c_int), ("n_terms", C.c_int),
                 ("g_nnz", C.c_int), ("n_slabs", C.c_int), ("n_x", C.c_int64), ("n_cells", C.c_int64),
-                ("n_unknowns", C.c_int64), ("tau", C.c_double), ("tile", C.c_int * 3),
-                ("threads", C.c_int), ("smem_bytes", C.c_int)]
+                ("n_unknowns", C.c_int64), ("tau", C.c_double), ("chunk", C.c_int),
+                ("grid", C.c_int), ("threads", C.c_int), ("smem_bytes", C.c_int)]
 
 
 _lib = None

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_api.cu"]
+SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_apply_f64.cu", "sg_apply_dw.cu", "sg_api.cu"]
 
 
 def _nvcc():

@@ -37,6 +37,7 @@ void free_ctx_device(sg_ctx* c) {
   cudaFree(c->d_gcol);
   cudaFree(c->d_gterm);
   cudaFree(c->d_gval);
+  cudaFree(c->d_perm);
   cudaFree(c->d_xbuf);
   cudaFree(c->d_ybuf);
   if (c->host_stream) cudaStreamDestroy(c->host_stream);
@@ -52,30 +53,29 @@ void fill_params(const sg_ctx* c, const double* x, double* y, int transpose, sg:
   p.g_col = c->d_gcol;
   p.g_term = c->d_gterm;
   p.g_val = c->d_gval;
+  p.perm = c->d_perm;
   p.n_x = hp.n_x;
+  p.n_cells = hp.n_cells;
   for (int d = 0; d < 3; ++d) {
     p.nn[d] = hp.nn[d];
     p.cells[d] = hp.cells[d];
-    p.tile[d] = c->ls.tile[d];
-    p.ntiles[d] = (hp.cells[d] + c->ls.tile[d] - 1) / c->ls.tile[d];
+    p.ratio[d] = d < hp.dim ? (hp.h[0] * hp.h[0]) / (hp.h[d] * hp.h[d]) : 1.0;
+    if (d < hp.dim && p.ratio[d] != 1.0) p.aniso = 1;
   }
+  p.chunk = c->ls.chunk;
   p.n_xi = hp.n_xi;
   p.n_terms = hp.n_terms;
   p.nnz = (int)hp.g.col.size();
   const int nq = hp.k + 1;
-  for (int q = 0; q < nq; ++q)
-    for (int n = 0; n < nq; ++n) {
-      p.S[q][n] = hp.S[q * nq + n];
-      for (int d = 0; d < 3; ++d) p.D[d][q][n] = hp.Dhat[q * nq + n] / hp.h[d];
-    }
   const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
   double detJ = 1.0;
   for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];
+  double wJ[sg::kMaxQD];
   for (int qd = 0; qd < nqd; ++qd) {
     int qi[3] = {qd % nq, (qd / nq) % nq, qd / (nq * nq)};
     double w = detJ;
     for (int d = 0; d < hp.dim; ++d) w *= hp.wq[qi[d]];
-    p.wJ[qd] = w;
+    wJ[qd] = w;
   }
   const int nt = hp.n_t;
   for (int i = 0; i < nt; ++i) {
@@ -83,7 +83,7 @@ void fill_params(const sg_ctx* c, const double* x, double* y, int transpose, sg:
     p.tb[i] = tb;
     for (int j = 0; j < nt; ++j) {
       const double a = transpose ? hp.A_hat[j * nt + i] : hp.A_hat[i * nt + j];
-      p.Am[i][j] = a / tb;
+      for (int qd = 0; qd < nqd; ++qd) p.amq[(qd * nt + i) * nt + j] = wJ[qd] * (a / tb);
     }
   }
 }
@@ -111,23 +111,26 @@ const char* sg_last_error(void) { return g_last_error.c_str(); }
 sg_status sg_setup(const sg_mesh* mesh, int fe_degree, int time_degree, int n_slabs, double T,
                    int M, int chaos_order, const sg_coeff* coef, int precision, sg_ctx** out) {
   if (!out) return fail(SG_ERR_ARG, "sg_setup: out is NULL");
-  if (precision != SG_PREC_FP64) return fail(SG_ERR_UNSUPPORTED, "sg_setup: precision not built");
+  if (precision != SG_PREC_FP64 && precision != SG_PREC_DW)
+    return fail(SG_ERR_UNSUPPORTED, "sg_setup: precision not built");
   sg_ctx* c = new (std::nothrow) sg_ctx();
   if (!c) return fail(SG_ERR_OOM, "sg_setup: host allocation failed");
   std::string msg;
   sg_status st = sg::build_host_problem(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order,
                                         coef, c->hp, msg);
   if (st != SG_OK) { delete c; return fail(st, "sg_setup: " + msg); }
+  c->hp.precision = precision;
   cudaGetDevice(&c->device);
   st = sg::plan_apply(c->hp, c->ls, msg);
   if (st != SG_OK) { delete c; return fail(st, "sg_setup: " + msg); }
-  cudaError_t e = sg::prepare_apply_kernel(c->hp.dim, c->hp.k, c->hp.n_t, c->ls.smem);
+  cudaError_t e = sg::prepare_apply_kernel(precision, c->hp.dim, c->hp.k, c->hp.n_t, c->ls.smem);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "sg_setup: kernel attributes"); }
   if ((e = upload(&c->d_ctab, c->hp.ctab)) != cudaSuccess ||
       (e = upload(&c->d_grow, c->hp.g.row)) != cudaSuccess ||
       (e = upload(&c->d_gcol, c->hp.g.col)) != cudaSuccess ||
       (e = upload(&c->d_gterm, c->hp.g.term)) != cudaSuccess ||
-      (e = upload(&c->d_gval, c->hp.g.val)) != cudaSuccess) {
+      (e = upload(&c->d_gval, c->hp.g.val)) != cudaSuccess ||
+      (e = upload(&c->d_perm, c->hp.perm)) != cudaSuccess) {
     free_ctx_device(c);
     delete c;
     return cuda_fail(e, "sg_setup: upload of tables");
@@ -206,6 +209,7 @@ sg_status sg_get_info(const sg_ctx* ctx, sg_info* out) {
   out->time_degree = hp.r;
   out->M = hp.M;
   out->chaos_order = hp.p;
+  out->precision = hp.precision;
   out->n_xi = hp.n_xi;
   out->n_t = hp.n_t;
   out->n_terms = hp.n_terms;
@@ -215,7 +219,8 @@ sg_status sg_get_info(const sg_ctx* ctx, sg_info* out) {
   out->n_cells = hp.n_cells;
   out->n_unknowns = (int64_t)hp.n_xi * hp.n_t * hp.n_x;
   out->tau = hp.tau;
-  for (int d = 0; d < 3; ++d) out->tile[d] = ctx->ls.tile[d];
+  out->chunk = ctx->ls.chunk;
+  out->grid = ctx->ls.grid;
   out->threads = ctx->ls.threads;
   out->smem_bytes = (int)ctx->ls.smem;
   return SG_OK;

@@ -1,0 +1,351 @@
+// The SG slab-operator apply kernel, generic over the arithmetic policy
+// (sg_arith.h).  See sg_apply.cu for the design; this header holds the device
+// code that both precisions instantiate.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sg_arith.h"
+#include "sg_internal.h"
+#include "sg_shape_tables.h"
+
+namespace sg {
+
+template <int DIM, int K>
+struct Shape {
+  static constexpr int N = K + 1;                       // nodes = Gauss points per direction
+  static constexpr int NKD = DIM == 2 ? N * N : N * N * N;
+  static constexpr int NQD = NKD;
+  static constexpr int NC = 1 + DIM;                    // value + gradient per point
+};
+
+template <int K>
+__device__ __forceinline__ constexpr Cf cS(int a, int b) {
+  return {RefShape<K>::S(a, b), RefShape<K>::Sh(a, b), RefShape<K>::Sl(a, b)};
+}
+template <int K>
+__device__ __forceinline__ constexpr Cf cD(int a, int b) {
+  return {RefShape<K>::D(a, b), RefShape<K>::Dh(a, b), RefShape<K>::Dl(a, b)};
+}
+
+// sum_j c(j) x(j) over J compile-time terms; exact zeros are skipped, a lone
+// +-1 term is an exact copy, every other result is normalised once.
+template <class A, int J, class CF, class XF>
+__device__ __forceinline__ typename A::T cdot(CF cf, XF xf) {
+  typename A::T s = A::zero();
+  int nt = 0;
+  bool unit = true;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const Cf c = cf(j);
+    if (c.c == 0.0) continue;
+    if (nt == 0) s = A::cmul(c, xf(j));
+    else A::cfma(c, xf(j), s);
+    ++nt;
+    if (!(c.c == 1.0 || c.c == -1.0)) unit = false;
+  }
+  if (nt == 1 && unit) return s;
+  return A::fin(s);
+}
+
+// --------------------------------------------------------------- phase 1
+// Nodal values u (lexicographic, x fastest) -> values and reference gradients
+// at the tensor Gauss points, written to q[comp * NQD + point].
+template <class A, int DIM, int K>
+__device__ __forceinline__ void forward_cell(const typename A::T* u, typename A::T* q) {
+  using T = typename A::T;
+  using Sh = Shape<DIM, K>;
+  constexpr int N = Sh::N;
+  constexpr Cf one = {1.0, 1.0f, 0.0f};
+  (void)one;
+  if constexpr (DIM == 2) {
+    T t[N][N];   // [ny][qx]
+#pragma unroll
+    for (int ny = 0; ny < N; ++ny)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx)
+        t[ny][qx] = cdot<A, N>([&](int j) { return cS<K>(qx, j); }, [&](int j) { return u[ny * N + j]; });
+    T v[N][N];   // [qy][qx]
+#pragma unroll
+    for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx) {
+        v[qy][qx] = cdot<A, N>([&](int j) { return cS<K>(qy, j); }, [&](int j) { return t[j][qx]; });
+        q[qy * N + qx] = v[qy][qx];
+      }
+#pragma unroll
+    for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx) {
+        q[Sh::NQD + qy * N + qx] = cdot<A, N>([&](int r) { return cD<K>(qx, r); }, [&](int r) { return v[qy][r]; });
+        q[2 * Sh::NQD + qy * N + qx] = cdot<A, N>([&](int r) { return cD<K>(qy, r); }, [&](int r) { return v[r][qx]; });
+      }
+  } else {
+    T t1[N][N][N];  // [nz][ny][qx]
+#pragma unroll
+    for (int nz = 0; nz < N; ++nz)
+#pragma unroll
+      for (int ny = 0; ny < N; ++ny)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx)
+          t1[nz][ny][qx] = cdot<A, N>([&](int j) { return cS<K>(qx, j); },
+                                      [&](int j) { return u[(nz * N + ny) * N + j]; });
+    T t2[N][N][N];  // [nz][qy][qx]
+#pragma unroll
+    for (int nz = 0; nz < N; ++nz)
+#pragma unroll
+      for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx)
+          t2[nz][qy][qx] = cdot<A, N>([&](int j) { return cS<K>(qy, j); }, [&](int j) { return t1[nz][j][qx]; });
+    T v[N][N][N];   // [qz][qy][qx]
+#pragma unroll
+    for (int qz = 0; qz < N; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx) {
+          v[qz][qy][qx] = cdot<A, N>([&](int j) { return cS<K>(qz, j); }, [&](int j) { return t2[j][qy][qx]; });
+          q[(qz * N + qy) * N + qx] = v[qz][qy][qx];
+        }
+#pragma unroll
+    for (int qz = 0; qz < N; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx) {
+          const int o = (qz * N + qy) * N + qx;
+          q[Sh::NQD + o] = cdot<A, N>([&](int r) { return cD<K>(qx, r); }, [&](int r) { return v[qz][qy][r]; });
+          q[2 * Sh::NQD + o] = cdot<A, N>([&](int r) { return cD<K>(qy, r); }, [&](int r) { return v[qz][r][qx]; });
+          q[3 * Sh::NQD + o] = cdot<A, N>([&](int r) { return cD<K>(qz, r); }, [&](int r) { return v[r][qy][qx]; });
+        }
+  }
+}
+
+// --------------------------------------------------------------- phase 3
+// Point values (q[0..NQD)) and reference-gradient coefficients
+// (q[NQD*(1+d) ...]) -> nodal contributions, written over q[0..NKD).  All
+// reads of q happen before the first write.
+template <class A, int DIM, int K>
+__device__ __forceinline__ void backward_cell(typename A::T* q) {
+  using T = typename A::T;
+  using Sh = Shape<DIM, K>;
+  constexpr int N = Sh::N;
+  constexpr Cf one = {1.0, 1.0f, 0.0f};
+  if constexpr (DIM == 2) {
+    T r[N][N];   // [qy][qx] combined point residual
+#pragma unroll
+    for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx)
+        r[qy][qx] = cdot<A, 2 * N + 1>(
+            [&](int j) { return j == 0 ? one : (j <= N ? cD<K>(j - 1, qx) : cD<K>(j - 1 - N, qy)); },
+            [&](int j) {
+              return j == 0 ? q[qy * N + qx]
+                            : (j <= N ? q[Sh::NQD + qy * N + (j - 1)] : q[2 * Sh::NQD + (j - 1 - N) * N + qx]);
+            });
+    T t[N][N];   // [ny][qx]
+#pragma unroll
+    for (int ny = 0; ny < N; ++ny)
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx)
+        t[ny][qx] = cdot<A, N>([&](int j) { return cS<K>(j, ny); }, [&](int j) { return r[j][qx]; });
+#pragma unroll
+    for (int ny = 0; ny < N; ++ny)
+#pragma unroll
+      for (int nx = 0; nx < N; ++nx)
+        q[ny * N + nx] = cdot<A, N>([&](int j) { return cS<K>(j, nx); }, [&](int j) { return t[ny][j]; });
+  } else {
+    T r[N][N][N];
+#pragma unroll
+    for (int qz = 0; qz < N; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx)
+          r[qz][qy][qx] = cdot<A, 3 * N + 1>(
+              [&](int j) {
+                return j == 0 ? one
+                              : (j <= N ? cD<K>(j - 1, qx) : (j <= 2 * N ? cD<K>(j - 1 - N, qy) : cD<K>(j - 1 - 2 * N, qz)));
+              },
+              [&](int j) {
+                return j == 0 ? q[(qz * N + qy) * N + qx]
+                              : (j <= N ? q[Sh::NQD + (qz * N + qy) * N + (j - 1)]
+                                        : (j <= 2 * N ? q[2 * Sh::NQD + (qz * N + (j - 1 - N)) * N + qx]
+                                                      : q[3 * Sh::NQD + ((j - 1 - 2 * N) * N + qy) * N + qx]));
+              });
+    T t1[N][N][N];  // [nz][qy][qx]
+#pragma unroll
+    for (int nz = 0; nz < N; ++nz)
+#pragma unroll
+      for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx)
+          t1[nz][qy][qx] = cdot<A, N>([&](int j) { return cS<K>(j, nz); }, [&](int j) { return r[j][qy][qx]; });
+    T t2[N][N][N];  // [nz][ny][qx]
+#pragma unroll
+    for (int nz = 0; nz < N; ++nz)
+#pragma unroll
+      for (int ny = 0; ny < N; ++ny)
+#pragma unroll
+        for (int qx = 0; qx < N; ++qx)
+          t2[nz][ny][qx] = cdot<A, N>([&](int j) { return cS<K>(j, ny); }, [&](int j) { return t1[nz][j][qx]; });
+#pragma unroll
+    for (int nz = 0; nz < N; ++nz)
+#pragma unroll
+      for (int ny = 0; ny < N; ++ny)
+#pragma unroll
+        for (int nx = 0; nx < N; ++nx)
+          q[(nz * N + ny) * N + nx] = cdot<A, N>([&](int j) { return cS<K>(j, nx); }, [&](int j) { return t2[nz][ny][j]; });
+  }
+}
+
+// The persistent chunk kernel (design notes in sg_apply.cu).
+template <class A, int DIM, int K, int NT>
+__global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p) {
+  using T = typename A::T;
+  using Sh = Shape<DIM, K>;
+  constexpr int NQD = Sh::NQD, NKD = Sh::NKD, NC = Sh::NC, N = Sh::N;
+  constexpr int SLOT = NC * NQD;                 // values per (cell, vector)
+  static_assert(sizeof(T) == 8, "8-byte value type expected");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int n_xi = p.n_xi, V = n_xi * NT, C = p.chunk;
+
+  T* Qs = reinterpret_cast<T*>(smem_raw);                       // [C][V][NC][NQD]
+  T* Cs = Qs + (size_t)C * V * SLOT;                            // [C][term][NQD]
+  T* Gv = Cs + (size_t)C * p.n_terms * NQD;                     // [nnz]
+  T* Amq = Gv + p.nnz;                                          // [NQD][NT][NT]
+  T* Tb = Amq + NQD * NT * NT;                                  // [NT]
+  T* Rt = Tb + NT;                                              // [3] (h_0/h_d)^2
+  int* Gr = reinterpret_cast<int*>(Rt + 3);                     // [n_xi+1]
+  int* Gc = Gr + n_xi + 1;                                      // [nnz]
+  int* Gt = Gc + p.nnz;                                         // [nnz]
+  int* Pm = Gt + p.nnz;                                         // [n_xi]
+
+  for (int e = tid; e < p.nnz; e += nthr) {
+    Gv[e] = A::in(p.g_val[e]);
+    Gc[e] = p.g_col[e];
+    Gt[e] = p.g_term[e];
+  }
+  for (int e = tid; e <= n_xi; e += nthr) Gr[e] = p.g_row[e];
+  for (int e = tid; e < n_xi; e += nthr) Pm[e] = p.perm[e];
+  for (int e = tid; e < NQD * NT * NT; e += nthr) Amq[e] = A::in(p.amq[e]);
+  if (tid < NT) Tb[tid] = A::in(p.tb[tid]);
+  if (tid < 3) Rt[tid] = A::in(p.ratio[tid]);
+
+  const long long c_begin = (long long)blockIdx.x * p.n_cells / gridDim.x;
+  const long long c_end = (long long)(blockIdx.x + 1) * p.n_cells / gridDim.x;
+  const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
+
+  for (long long c0 = c_begin; c0 < c_end; c0 += C) {
+    const int nc = (int)min((long long)C, c_end - c0);
+    __syncthreads();   // previous chunk done with Qs / Cs; tables visible
+    // ---------------------------------------------------------- phase 0
+    {
+      const int per_cell = p.n_terms * NQD;
+      for (int idx = tid; idx < nc * per_cell; idx += nthr) Cs[idx] = A::in(p.ctab[c0 * per_cell + idx]);
+    }
+    for (int idx = tid; idx < nc * V * NKD; idx += nthr) {
+      const int a = idx % NKD;
+      const int cv = idx / NKD;
+      const int v = cv % V, c = cv / V;
+      const long long gc = c0 + c;
+      const int cx = (int)(gc % p.cells[0]);
+      const int cy = (int)((gc / p.cells[0]) % p.cells[1]);
+      const int cz = (int)(gc / ((long long)p.cells[0] * p.cells[1]));
+      const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
+      bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+      if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
+      T val = A::zero();
+      if (interior) val = A::in(p.x[(long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx]);
+      Qs[(size_t)cv * SLOT + a] = val;
+    }
+    __syncthreads();
+    // ---------------------------------------------------------- phase 1
+    for (int it = tid; it < nc * V; it += nthr) {
+      T* q = Qs + (size_t)it * SLOT;
+      T u[NKD];
+#pragma unroll
+      for (int a = 0; a < NKD; ++a) u[a] = q[a];
+      forward_cell<A, DIM, K>(u, q);
+    }
+    __syncthreads();
+    // ---------------------------------------------------------- phase 2
+    {
+      const int gpr = nthr / n_xi;               // (cell, point) groups per round
+      const int gl = tid / n_xi;
+      const int a = Pm[tid - gl * n_xi];
+      const int ngroups = nc * NQD;
+      for (int g0 = 0; g0 < ngroups; g0 += gpr) {
+        const int g = g0 + gl;
+        const bool act = gl < gpr && g < ngroups;
+        const int c = act ? g / NQD : 0;
+        const int q = act ? g - c * NQD : 0;
+        T out[NT][NC];
+        if (act) {
+          const T* base = Qs + (size_t)c * V * SLOT + q;
+          T uv[NT];
+#pragma unroll
+          for (int j = 0; j < NT; ++j) uv[j] = base[(size_t)(a * NT + j) * SLOT];
+          const T* am = Amq + q * NT * NT;
+#pragma unroll
+          for (int i = 0; i < NT; ++i) {
+            T s = A::mul(am[i * NT], uv[0]);
+#pragma unroll
+            for (int j = 1; j < NT; ++j) A::fma(am[i * NT + j], uv[j], s);
+            out[i][0] = A::fin(s);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) out[i][1 + d] = A::zero();
+          }
+          const T* cq = Cs + (size_t)c * p.n_terms * NQD + q;
+          const int e_end = Gr[a + 1];
+          for (int e = Gr[a]; e < e_end; ++e) {
+            const T w = A::fin(A::mul(Gv[e], cq[Gt[e] * NQD]));
+            const T* gb = base + (size_t)(Gc[e] * NT) * SLOT;
+#pragma unroll
+            for (int i = 0; i < NT; ++i)
+#pragma unroll
+              for (int d = 0; d < DIM; ++d) A::fma(w, gb[(size_t)i * SLOT + (1 + d) * NQD], out[i][1 + d]);
+          }
+#pragma unroll
+          for (int i = 0; i < NT; ++i)
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              if (p.aniso && d > 0) out[i][1 + d] = A::mul(A::fin(out[i][1 + d]), Rt[d]);
+              out[i][1 + d] = A::fin(out[i][1 + d]);
+            }
+        }
+        __syncthreads();
+        if (act) {
+          T* base = Qs + (size_t)c * V * SLOT + q;
+#pragma unroll
+          for (int i = 0; i < NT; ++i)
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) base[(size_t)(a * NT + i) * SLOT + cc * NQD] = out[i][cc];
+        }
+        __syncthreads();
+      }
+    }
+    // ---------------------------------------------------------- phase 3
+    for (int it = tid; it < nc * V; it += nthr) backward_cell<A, DIM, K>(Qs + (size_t)it * SLOT);
+    __syncthreads();
+    // ---------------------------------------------------------- phase 4
+    for (int idx = tid; idx < nc * V * NKD; idx += nthr) {
+      const int a = idx % NKD;
+      const int cv = idx / NKD;
+      const int v = cv % V, c = cv / V;
+      const long long gc = c0 + c;
+      const int cx = (int)(gc % p.cells[0]);
+      const int cy = (int)((gc / p.cells[0]) % p.cells[1]);
+      const int cz = (int)(gc / ((long long)p.cells[0] * p.cells[1]));
+      const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
+      bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+      if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
+      if (interior)
+        A::add_out(p.y + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx,
+                   A::mul(Tb[v % NT], Qs[(size_t)cv * SLOT + a]));
+    }
+  }
+}
+
+}  // namespace sg

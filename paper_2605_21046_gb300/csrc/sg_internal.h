@@ -15,6 +15,7 @@ constexpr int kMaxK = 3;          // largest spatial degree built
 constexpr int kMaxNQ = kMaxK + 1; // Gauss points per direction
 constexpr int kMaxNT = 4;         // largest number of time nodes (dG(3))
 constexpr int kMaxQD = 64;        // largest tensor Gauss rule per cell (4^3)
+constexpr int kMaxAmq = 256;      // largest (points x time nodes^2) coupling table
 
 // ---------------------------------------------------------------- host maths
 // One-dimensional rules and bases on the reference interval [0, 1].
@@ -42,6 +43,7 @@ struct GTable {
 };
 
 struct HostProblem {
+  int precision = SG_PREC_FP64;
   int dim = 2, k = 1, r = 1, M = 1, p = 0, n_slabs = 1;
   double T = 1.0, tau = 1.0;
   int cells[3] = {1, 1, 1}, nn[3] = {1, 1, 1};
@@ -54,7 +56,8 @@ struct HostProblem {
   std::vector<double> A_hat, B_hat;     // (r+1)^2 each
   std::vector<double> S, Dhat;          // [q][n] interpolation, [q][p] collocation derivative
   std::vector<double> wq;               // 1D Gauss weights
-  std::vector<double> ctab;             // [cell][term][qd]: w_q |J| a_mu(x_q)
+  std::vector<double> ctab;             // [cell][term][qd]: w_q |J| a_mu(x_q) / h_0^2
+  std::vector<int> perm;                // chaos rows sorted by their number of G entries
 };
 
 // Builds every host table of a problem.  Returns SG_OK or an error with msg.
@@ -66,41 +69,40 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
 struct ApplyParams {
   const double* x;
   double* y;
-  const double* ctab;     // [n_cells][n_terms][NQD]
+  const double* ctab;     // [n_cells][n_terms][NQD], w_q |J| a_mu(x_q) / h_0^2
   const int* g_row;       // [n_xi + 1]
   const int* g_col;       // [nnz]
   const int* g_term;      // [nnz]
   const double* g_val;    // [nnz]
+  const int* perm;        // [n_xi] chaos rows sorted by row length
   long long n_x;
+  long long n_cells;
   int nn[3];              // nodes per direction
   int cells[3];
-  int tile[3];            // cells per tile per direction
-  int ntiles[3];
+  int chunk;              // cells per shared-memory chunk
   int n_xi, n_terms, nnz;
-  double S[kMaxNQ][kMaxNQ];        // S[q][n] = l_n(x_q), GLL basis at Gauss points
-  double D[3][kMaxNQ][kMaxNQ];     // D[d][q][p] = l^G_p'(x_q) / h_d
-  double wJ[kMaxQD];               // w_q |J| per tensor Gauss point
-  double Am[kMaxNT][kMaxNT];       // A_t[i][j] / (tau Bhat_ii) (A_t^T for the transpose)
-  double tb[kMaxNT];               // tau Bhat_ii
+  int aniso;              // 1 if the cell is not a cube / square
+  double ratio[3];        // (h_0 / h_d)^2
+  double amq[kMaxAmq];    // [q][i][j] w_q |J| A_t[i][j] / (tau Bhat_ii) (A_t^T for the transpose)
+  double tb[kMaxNT];      // tau Bhat_ii
 };
 
 struct LaunchShape {
-  int tile[3];
+  int chunk;              // cells per chunk
   int threads;
   size_t smem;
-  int grid;
+  int grid;               // persistent CTAs
 };
 
 // Chooses a tile shape and thread count for the apply kernel of a problem.
 sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg);
-// Size of the dynamic shared memory the apply kernel needs for a tile.
-size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz,
-                        const int tile[3]);
+// Size of the dynamic shared memory the apply kernel needs for a chunk of cells.
+size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk);
 // Launches y = A x (init kernel + tile kernel) on a stream.
 cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const ApplyParams& prm,
                          cudaStream_t stream);
-// One-time per-process kernel attribute set-up (max dynamic shared memory).
-cudaError_t prepare_apply_kernel(int dim, int k, int n_t, size_t smem);
+// Kernel attribute set-up (max dynamic shared memory).
+cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t smem);
 
 }  // namespace sg
 
@@ -113,6 +115,7 @@ struct sg_ctx {
   int* d_gcol = nullptr;
   int* d_gterm = nullptr;
   double* d_gval = nullptr;
+  int* d_perm = nullptr;
   double* d_xbuf = nullptr;   // workspaces of sg_apply_host (lazy)
   double* d_ybuf = nullptr;
   cudaStream_t host_stream = nullptr;

@@ -259,6 +259,12 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
         msg = "time mass matrix is not diagonal";
         return SG_ERR_UNSUPPORTED;
       }
+  // chaos rows ordered by their number of coupling entries (warp uniformity)
+  hp.perm.resize(hp.n_xi);
+  for (int a = 0; a < hp.n_xi; ++a) hp.perm[a] = a;
+  std::stable_sort(hp.perm.begin(), hp.perm.end(), [&](int a, int b) {
+    return hp.g.row[a + 1] - hp.g.row[a] > hp.g.row[b + 1] - hp.g.row[b];
+  });
   // 1D spatial bases at the (k+1)-point Gauss rule
   const int nq = k + 1;
   Rule1D g = gauss_legendre(nq);
@@ -296,7 +302,7 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
         for (int d = 0; d < hp.dim; ++d)
           v *= factor_value(coef->factor_kind[pc * 3 + d], coef->factor_k[pc * 3 + d], xq[d]);
         if (coef->cell_scale && coef->cell_scale[pc]) v *= coef->cell_scale[pc][c];
-        hp.ctab[((size_t)c * hp.n_terms + piece_term[pc]) * nqd + qd] += w * v;
+        hp.ctab[((size_t)c * hp.n_terms + piece_term[pc]) * nqd + qd] += w * v / (hp.h[0] * hp.h[0]);
       }
     }
   }

@@ -76,8 +76,10 @@ enum { SG_F_ONE = 0, SG_F_SIN = 1, SG_F_POW = 2 };
  *                 transformations (exact FMA product errors, TwoSum); about 48
  *                 significant bits.  Inputs and outputs stay double.  Inputs
  *                 with magnitude below 2^-74 keep only 24 significant bits.
- *                 Meets the 1e-12 relative apply tolerance of the FP64 path. */
-enum { SG_PREC_FP64 = 0, SG_PREC_DW = 1 };
+ *                 Meets the 1e-12 relative apply tolerance of the FP64 path.
+ *   SG_PREC_FP32  native single precision; accepted by sg_mg_setup only (the
+ *                 multigrid preconditioner inside the FP64 outer FGMRES). */
+enum { SG_PREC_FP64 = 0, SG_PREC_DW = 1, SG_PREC_FP32 = 2 };
 
 /* Uniform Cartesian mesh of [lo, hi] (dim = 2 or 3; entries beyond dim are
  * ignored).  cells[d] >= 1 cells in direction d. */
@@ -129,6 +131,18 @@ typedef struct {
   int smem_bytes;  /* dynamic shared memory per CTA     */
 } sg_info;
 
+/* Statistics of one sg_solve_slab call (host struct out). */
+typedef struct {
+  int iterations;       /* FGMRES iterations (Arnoldi steps)                 */
+  int restarts;         /* completed FGMRES cycles                           */
+  int vmult_calls;      /* applications of A^(n)                             */
+  int prec_calls;       /* V-cycles                                          */
+  int converged;        /* 1 if rel_residual <= rtol                          */
+  double rel_residual;  /* ||rhs - A x|| / ||rhs|| of the returned x, FP64     */
+  double solve_ms;      /* wall time of the call                              */
+  double mg_setup_ms;   /* wall time of the last sg_mg_setup                  */
+} sg_solve_stats;
+
 /* sg_setup - discretise one problem and make it resident on the current
  * CUDA device (Sec. 3: Q_k in space, dG(r) in time, Lambda_p chaos; Sec. 3.5:
  * time matrices eqs. At/Bt/Ct, G_mu eq. triple_stoch and its factorisation
@@ -164,6 +178,47 @@ sg_status sg_apply(sg_ctx* ctx, int slab, const double* x, double* y, int transp
  * memory gives full copy bandwidth; pageable memory works. */
 sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
                         int transpose);
+
+/* sg_mg_setup - build the block-Jacobi geometric-multigrid preconditioner
+ * (the matrix-free remark after eq. local_rhs_tensor: every chaos mode alpha
+ * is preconditioned by one V-cycle of its diagonal block
+ * A_alpha = A_t (x) M_x + sum_mu [G_mu]_{alpha alpha} B_t (x) K_mu with a
+ * space-time Vanka smoother).  Levels halve the cells per direction while all
+ * counts are even and > 2; the coarsest block is inverted densely (at most
+ * 2048 interior unknowns per mode, else SG_ERR_UNSUPPORTED).  Vanka patches
+ * are one cell's interior nodes x all time nodes, inverted exactly.
+ *   mg_precision  SG_PREC_FP64 or SG_PREC_FP32 (vectors, patch inverses,
+ *                 transfers and coarse solve; the outer solver stays FP64)
+ *   nu            smoothing steps before and after the coarse correction (>= 1)
+ *   omega         Vanka damping (0 < omega <= 1)
+ * Allocates device memory owned by the context (replaces an earlier set-up).
+ * Synchronous. */
+sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega);
+
+/* sg_vcycle - z = P^{-1} r: one V-cycle per chaos mode, all modes and time
+ * nodes at once (block-Jacobi in alpha).  r, z: DEVICE slab vectors (layout
+ * above), not overlapping.  Needs sg_mg_setup.  Stream ordered, async.  The
+ * first call records the V-cycle into a CUDA graph (make it outside any
+ * stream capture of the caller). */
+sg_status sg_vcycle(sg_ctx* ctx, const double* r, double* z, sg_stream stream);
+
+/* sg_solve_slab - solve A^(n) x = rhs (eq. local_tensor_system with the
+ * right-hand side already formed) by restarted flexible GMRES(restart) in
+ * FP64, right-preconditioned by sg_vcycle; Arnoldi by classical Gram-Schmidt
+ * with one reorthogonalisation.
+ *   rhs     DEVICE slab vector
+ *   x       DEVICE slab vector: initial guess in, solution out
+ *   rtol    stop when ||rhs - A x|| / ||rhs|| <= rtol (true residual, FP64)
+ *   max_it  iteration limit (SG_ERR_NOT_CONVERGED when reached; x holds the
+ *           last iterate and st the statistics)
+ *   restart Krylov basis size (1..200)
+ *   st      statistics out (may be NULL)
+ * Needs sg_mg_setup.  Allocates a Krylov workspace of (2 restart + 3) slab
+ * vectors on first use (kept by the context).  Synchronous: returns when x is
+ * written; launches go to `stream`.  SG_ERR_NONFINITE if a residual norm is
+ * not finite. */
+sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, double rtol, int max_it,
+                        int restart, sg_solve_stats* st, sg_stream stream);
 
 /* sg_get_info - sizes and launch shape of a context (host struct out). */
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);

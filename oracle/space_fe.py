@@ -119,6 +119,16 @@ class Mesh:
             mask |= (ijk[:, d] == 0) | (ijk[:, d] == self.nn[d] - 1)
         return mask
 
+    def node_coords(self):
+        """(n_nodes, dim) physical coordinates of all nodes."""
+        fe_nodes = gll_nodes_01(self.k)
+        ijk = self.node_coords_idx(np.arange(self.n_nodes))
+        out = np.zeros((self.n_nodes, self.dim))
+        for d in range(self.dim):
+            cell = np.minimum(ijk[:, d] // self.k, self.cells[d] - 1)
+            out[:, d] = self.lo[d] + (cell + fe_nodes[ijk[:, d] - cell * self.k]) * self.h[d]
+        return out
+
     def cells_of_node(self, node):
         """Lexicographic indices of the cells that contain a node."""
         ijk = self.node_coords_idx([node])[0]

@@ -16,9 +16,9 @@ import numpy as np
 
 from . import _abi
 
-SG_PREC_FP64, SG_PREC_DW = _abi.SG_PREC_FP64, _abi.SG_PREC_DW
+SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = _abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -180,6 +180,43 @@ def sg_apply_host(ctx, slab, x, y=None, transpose=False):
     _check(lib.sg_apply_host(ctx.handle, int(slab), C.c_void_p(ptr(x)), C.c_void_p(ptr(y)),
                              int(bool(transpose))), "sg_apply_host")
     return y
+
+
+def _check_vec(ctx, *ts):
+    n = ctx.info["n_unknowns"]
+    for t in ts:
+        if not (t.is_cuda and str(t.dtype) == "torch.float64"):
+            raise TypeError("float64 CUDA tensors expected")
+        if t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"contiguous tensors of {n} elements expected")
+
+
+def sg_mg_setup(ctx, mg_precision=SG_PREC_FP64, nu=2, omega=0.7):
+    """Build the block-Jacobi multigrid preconditioner (sg_mg_setup)."""
+    _check(_abi.load().sg_mg_setup(ctx.handle, int(mg_precision), int(nu), float(omega)), "sg_mg_setup")
+
+
+def sg_vcycle(ctx, r, z, stream=None):
+    """z = P^{-1} r (one V-cycle per chaos mode) on ``stream``."""
+    _check_vec(ctx, r, z)
+    _check(_abi.load().sg_vcycle(ctx.handle, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()),
+                                 C.c_void_p(_stream_handle(stream))), "sg_vcycle")
+    return z
+
+
+def sg_solve_slab(ctx, slab, rhs, x, rtol=1e-8, max_it=500, restart=30, stream=None, check=True):
+    """FGMRES solve of A^(n) x = rhs; x holds the initial guess.  Returns the
+    statistics dict; raises SGError on failure when ``check``."""
+    _check_vec(ctx, rhs, x)
+    st = _abi.sg_solve_stats()
+    status = _abi.load().sg_solve_slab(ctx.handle, int(slab), C.c_void_p(rhs.data_ptr()),
+                                       C.c_void_p(x.data_ptr()), float(rtol), int(max_it), int(restart),
+                                       C.byref(st), C.c_void_p(_stream_handle(stream)))
+    out = {name: getattr(st, name) for name, _ in _abi.sg_solve_stats._fields_}
+    out["status"] = status
+    if check:
+        _check(status, "sg_solve_slab")
+    return out
 
 
 def sg_get_info(ctx):

@@ -8,11 +8,12 @@ LIB_PATH = os.path.join(PKG, "libsg.so")
 SG_OK, SG_ERR_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 SG_ERR_NOT_CONVERGED, SG_ERR_NONFINITE, SG_ERR_TIMEOUT = 5, 6, 7
 SG_F_ONE, SG_F_SIN, SG_F_POW = 0, 1, 2
-SG_PREC_FP64, SG_PREC_DW = 0, 1
+SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = 0, 1, 2
 
 # every symbol include/sg.h declares
-EXPORTED = ["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
-            "sg_destroy", "sg_status_string", "sg_last_error"]
+EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
+                   "sg_destroy", "sg_status_string", "sg_last_error", "sg_mg_setup", "sg_vcycle",
+                   "sg_solve_slab"])
 
 
 class sg_mesh(C.Structure):
@@ -32,6 +33,12 @@ class sg_info(C.Structure):
                 ("g_nnz", C.c_int), ("n_slabs", C.c_int), ("n_x", C.c_int64), ("n_cells", C.c_int64),
                 ("n_unknowns", C.c_int64), ("tau", C.c_double), ("chunk", C.c_int),
                 ("grid", C.c_int), ("threads", C.c_int), ("smem_bytes", C.c_int)]
+
+
+class sg_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("vmult_calls", C.c_int),
+                ("prec_calls", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
+                ("solve_ms", C.c_double), ("mg_setup_ms", C.c_double)]
 
 
 _lib = None
@@ -58,6 +65,13 @@ def load():
     lib.sg_get_info.restype = C.c_int
     lib.sg_get_multi_indices.argtypes = [vp, C.POINTER(C.c_int)]
     lib.sg_get_multi_indices.restype = C.c_int
+    lib.sg_mg_setup.argtypes = [vp, C.c_int, C.c_int, C.c_double]
+    lib.sg_mg_setup.restype = C.c_int
+    lib.sg_vcycle.argtypes = [vp, vp, vp, vp]
+    lib.sg_vcycle.restype = C.c_int
+    lib.sg_solve_slab.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int,
+                                  C.POINTER(sg_solve_stats), vp]
+    lib.sg_solve_slab.restype = C.c_int
     lib.sg_destroy.argtypes = [vp]
     lib.sg_destroy.restype = None
     lib.sg_status_string.argtypes = [C.c_int]

@@ -14,7 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_apply_f64.cu", "sg_apply_dw.cu", "sg_api.cu"]
+SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_apply_f64.cu", "sg_apply_dw.cu", "sg_apply_f32.cu", "sg_mg.cu",
+           "sg_krylov.cu", "sg_api.cu"]
 
 
 def _nvcc():
@@ -31,6 +32,8 @@ def _compile(src, verbose):
            "-I", os.path.join(PKG, "..", "include"), "-c", os.path.join(CSRC, src), "-o", out]
     if src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
+    if src == "sg_mg.cu":
+        cmd[1:1] = ["-Xcompiler", "-fopenmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -54,7 +57,7 @@ def build(verbose=False, force=False):
             if log:
                 sys.stderr.write(log)
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *objs]
+    cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -40,52 +40,33 @@ void free_ctx_device(sg_ctx* c) {
   cudaFree(c->d_perm);
   cudaFree(c->d_xbuf);
   cudaFree(c->d_ybuf);
+  cudaFree(c->d_krylov);
   if (c->host_stream) cudaStreamDestroy(c->host_stream);
+  if (c->mg) {
+    sg::mg_free(*c->mg);
+    delete c->mg;
+    c->mg = nullptr;
+  }
 }
 
-void fill_params(const sg_ctx* c, const double* x, double* y, int transpose, sg::ApplyParams& p) {
-  const sg::HostProblem& hp = c->hp;
-  std::memset(&p, 0, sizeof(p));
-  p.x = x;
-  p.y = y;
-  p.ctab = c->d_ctab;
-  p.g_row = c->d_grow;
-  p.g_col = c->d_gcol;
-  p.g_term = c->d_gterm;
-  p.g_val = c->d_gval;
-  p.perm = c->d_perm;
-  p.n_x = hp.n_x;
-  p.n_cells = hp.n_cells;
-  for (int d = 0; d < 3; ++d) {
-    p.nn[d] = hp.nn[d];
-    p.cells[d] = hp.cells[d];
-    p.ratio[d] = d < hp.dim ? (hp.h[0] * hp.h[0]) / (hp.h[d] * hp.h[d]) : 1.0;
-    if (d < hp.dim && p.ratio[d] != 1.0) p.aniso = 1;
+cudaError_t apply_device(sg_ctx* c, const double* x, double* y, cudaStream_t s) {
+  sg::ApplyParams p;
+  sg::fill_apply_params(c->hp, c->ls, c->d_ctab, c->d_grow, c->d_gcol, c->d_gterm, c->d_gval, c->d_perm, x, y, 0, p);
+  return sg::launch_apply(c->hp, c->ls, p, s);
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
-  p.chunk = c->ls.chunk;
-  p.n_xi = hp.n_xi;
-  p.n_terms = hp.n_terms;
-  p.nnz = (int)hp.g.col.size();
-  const int nq = hp.k + 1;
-  const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
-  double detJ = 1.0;
-  for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];
-  double wJ[sg::kMaxQD];
-  for (int qd = 0; qd < nqd; ++qd) {
-    int qi[3] = {qd % nq, (qd / nq) % nq, qd / (nq * nq)};
-    double w = detJ;
-    for (int d = 0; d < hp.dim; ++d) w *= hp.wq[qi[d]];
-    wJ[qd] = w;
-  }
-  const int nt = hp.n_t;
-  for (int i = 0; i < nt; ++i) {
-    const double tb = hp.tau * hp.B_hat[i * nt + i];
-    p.tb[i] = tb;
-    for (int j = 0; j < nt; ++j) {
-      const double a = transpose ? hp.A_hat[j * nt + i] : hp.A_hat[i * nt + j];
-      for (int qd = 0; qd < nqd; ++qd) p.amq[(qd * nt + i) * nt + j] = wJ[qd] * (a / tb);
-    }
-  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void fill_params(const sg_ctx* c, const void* x, void* y, int transpose, sg::ApplyParams& p) {
+  sg::fill_apply_params(c->hp, c->ls, c->d_ctab, c->d_grow, c->d_gcol, c->d_gterm, c->d_gval, c->d_perm, x, y,
+                        transpose, p);
 }
 
 }  // namespace
@@ -197,6 +178,59 @@ sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_h
   if (e != cudaSuccess) return cuda_fail(e, "sg_apply_host: copy out");
   e = cudaStreamSynchronize(ctx->host_stream);
   if (e != cudaSuccess) return cuda_fail(e, "sg_apply_host: synchronize");
+  return SG_OK;
+}
+
+sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_mg_setup: ctx is NULL");
+  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32)
+    return fail(SG_ERR_UNSUPPORTED, "sg_mg_setup: precision must be SG_PREC_FP64 or SG_PREC_FP32");
+  if (nu < 1 || nu > 16 || !(omega > 0.0 && omega <= 1.0)) return fail(SG_ERR_ARG, "sg_mg_setup: nu or omega out of range");
+  cudaDeviceSynchronize();
+  if (ctx->mg) {
+    sg::mg_free(*ctx->mg);
+    delete ctx->mg;
+    ctx->mg = nullptr;
+  }
+  sg::MG* mg = new (std::nothrow) sg::MG();
+  if (!mg) return fail(SG_ERR_OOM, "sg_mg_setup: host allocation failed");
+  std::string msg;
+  sg_status st = sg::mg_build(ctx->hp, mg_precision, nu, omega, *mg, msg);
+  if (st != SG_OK) {
+    sg::mg_free(*mg);
+    delete mg;
+    return fail(st, "sg_mg_setup: " + msg);
+  }
+  ctx->mg = mg;
+  return SG_OK;
+}
+
+sg_status sg_vcycle(sg_ctx* ctx, const double* r, double* z, sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_vcycle: ctx is NULL");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_vcycle: call sg_mg_setup first");
+  if (!r || !z) return fail(SG_ERR_ARG, "sg_vcycle: null vector");
+  const long long n = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
+  if (r < z + n && z < r + n) return fail(SG_ERR_ARG, "sg_vcycle: r and z overlap");
+  if (!is_device_ptr(r) || !is_device_ptr(z)) return fail(SG_ERR_ARG, "sg_vcycle: vectors must be device memory");
+  cudaError_t e = sg::mg_apply(*ctx->mg, r, z, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "sg_vcycle");
+  return SG_OK;
+}
+
+sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, double rtol, int max_it,
+                        int restart, sg_solve_stats* st, sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_solve_slab: ctx is NULL");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_solve_slab: call sg_mg_setup first");
+  if (slab < 0 || slab >= ctx->hp.n_slabs) return fail(SG_ERR_ARG, "sg_solve_slab: slab out of range");
+  if (!rhs || !x) return fail(SG_ERR_ARG, "sg_solve_slab: null vector");
+  if (!(rtol > 0.0) || max_it < 1 || restart < 1 || restart > 200) return fail(SG_ERR_ARG, "sg_solve_slab: rtol, max_it or restart out of range");
+  const long long n = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
+  if (rhs < x + n && x < rhs + n) return fail(SG_ERR_ARG, "sg_solve_slab: rhs and x overlap");
+  if (!is_device_ptr(rhs) || !is_device_ptr(x)) return fail(SG_ERR_ARG, "sg_solve_slab: vectors must be device memory");
+  std::string msg;
+  sg_status s = sg::fgmres(ctx, rhs, x, rtol, max_it, restart, st, reinterpret_cast<cudaStream_t>(stream), msg,
+                           &apply_device);
+  if (s != SG_OK) return fail(s, "sg_solve_slab: " + msg);
   return SG_OK;
 }
 

@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "sg_internal.h"
 #include "sg_shape_tables.h"
@@ -48,9 +49,11 @@ namespace sg {
 
 void* select_kernel_f64(int dim, int k, int n_t);
 void* select_kernel_dw(int dim, int k, int n_t);
+void* select_kernel_f32(int dim, int k, int n_t);
 
 // y = (x on Dirichlet nodes, 0 elsewhere).
-__global__ void sg_init_y_kernel(const double* __restrict__ x, double* __restrict__ y,
+template <typename IO>
+__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* __restrict__ y,
                                  long long n_total, long long n_x, int nnx, int nny, int nnz,
                                  int dim) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
@@ -61,11 +64,12 @@ __global__ void sg_init_y_kernel(const double* __restrict__ x, double* __restric
     int iz = (int)(m / ((long long)nnx * nny));
     bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    y[idx] = bd ? x[idx] : 0.0;
+    y[idx] = bd ? x[idx] : IO(0);
   }
 }
 
-size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk) {
+size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk,
+                        int value_bytes) {
   const size_t nqd = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
   const size_t V = (size_t)n_xi * n_t;
   size_t vals = (size_t)chunk * V * (1 + dim) * nqd      // Qs
@@ -74,7 +78,7 @@ size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz,
                 + nqd * n_t * n_t                        // Amq
                 + n_t + 3;                               // Tb, Rt
   size_t ints = (n_xi + 1) + 2 * (size_t)nnz + n_xi;     // Gr, Gc, Gt, Pm
-  return vals * 8 + ints * sizeof(int);
+  return ((vals * value_bytes + 7) / 8) * 8 + ints * sizeof(int);
 }
 
 template <int K>
@@ -90,13 +94,23 @@ static double max_table_gap(const HostProblem& hp) {
 }
 
 static void* select_kernel(int precision, int dim, int k, int n_t) {
-  return precision == SG_PREC_DW ? select_kernel_dw(dim, k, n_t) : select_kernel_f64(dim, k, n_t);
+  if (precision == SG_PREC_DW) return select_kernel_dw(dim, k, n_t);
+  if (precision == kPrecF32) return select_kernel_f32(dim, k, n_t);
+  return select_kernel_f64(dim, k, n_t);
 }
 
+// The dynamic shared-memory limit is a property of the kernel function, shared
+// by every context and multigrid level that launches it: it is always set to
+// the device's opt-in maximum, so a later set-up can never shrink the limit
+// below what an earlier one launches with.
 cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t smem) {
   void* f = select_kernel(precision, dim, k, n_t);
   if (!f) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if ((size_t)optin < smem) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
@@ -122,18 +136,19 @@ sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
   if (smem_optin <= 0) smem_optin = 227 * 1024;
   if (n_sm <= 0) n_sm = 1;
   const int nnz = (int)hp.g.col.size();
+  const int vb = hp.precision == kPrecF32 ? 4 : 8;
   const long long cells_per_sm = (hp.n_cells + n_sm - 1) / n_sm;
   // Largest chunk that lets two CTAs share an SM; one CTA per SM otherwise.
   const size_t budget2 = (size_t)smem_optin / 2 - 1024;
   const size_t budget1 = (size_t)smem_optin - 1024;
   int chunk = 0;
   for (int c = 1; c <= 64; ++c) {
-    if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c) > budget2) break;
+    if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c, vb) > budget2) break;
     chunk = c;
   }
   if (chunk == 0) {
     for (int c = 1; c <= 64; ++c) {
-      if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c) > budget1) break;
+      if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c, vb) > budget1) break;
       chunk = c;
     }
   }
@@ -143,13 +158,13 @@ sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
   }
   chunk = (int)std::min<long long>(chunk, std::max<long long>(1, (cells_per_sm + 1) / 2));
   ls.chunk = chunk;
-  ls.smem = apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, chunk);
+  ls.smem = apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, chunk, vb);
   // threads: phase 2 runs whole (cell, point) groups of n_xi threads
   int groups = std::max(1, 256 / hp.n_xi);
   int thr = ((groups * hp.n_xi + 31) / 32) * 32;
   if (thr < 128) thr = std::min(512, ((128 / hp.n_xi) * hp.n_xi + 31) / 32 * 32);
   ls.threads = std::min(thr, 512);
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls.smem);
+  cudaError_t e = prepare_apply_kernel(hp.precision, hp.dim, hp.k, hp.n_t, ls.smem);
   int per_sm = 1;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, ls.threads, ls.smem);
   if (e != cudaSuccess || per_sm < 1) { cudaGetLastError(); per_sm = 1; }
@@ -159,13 +174,63 @@ sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
   return SG_OK;
 }
 
+void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void* ctab,
+                       const int* grow, const int* gcol, const int* gterm, const double* gval,
+                       const int* perm, const void* x, void* y, int transpose, ApplyParams& p) {
+  std::memset(&p, 0, sizeof(p));
+  p.x = x;
+  p.y = y;
+  p.ctab = static_cast<const double*>(ctab);
+  p.g_row = grow;
+  p.g_col = gcol;
+  p.g_term = gterm;
+  p.g_val = gval;
+  p.perm = perm;
+  p.n_x = hp.n_x;
+  p.n_cells = hp.n_cells;
+  for (int d = 0; d < 3; ++d) {
+    p.nn[d] = hp.nn[d];
+    p.cells[d] = hp.cells[d];
+    p.ratio[d] = d < hp.dim ? (hp.h[0] * hp.h[0]) / (hp.h[d] * hp.h[d]) : 1.0;
+    if (d < hp.dim && p.ratio[d] != 1.0) p.aniso = 1;
+  }
+  p.chunk = ls.chunk;
+  p.n_xi = hp.n_xi;
+  p.n_terms = hp.n_terms;
+  p.nnz = (int)hp.g.col.size();
+  const int nq = hp.k + 1;
+  const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
+  double detJ = 1.0;
+  for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];
+  double wJ[kMaxQD];
+  for (int qd = 0; qd < nqd; ++qd) {
+    int qi[3] = {qd % nq, (qd / nq) % nq, qd / (nq * nq)};
+    double w = detJ;
+    for (int d = 0; d < hp.dim; ++d) w *= hp.wq[qi[d]];
+    wJ[qd] = w;
+  }
+  const int nt = hp.n_t;
+  for (int i = 0; i < nt; ++i) {
+    const double tb = hp.tau * hp.B_hat[i * nt + i];
+    p.tb[i] = tb;
+    for (int j = 0; j < nt; ++j) {
+      const double a = transpose ? hp.A_hat[j * nt + i] : hp.A_hat[i * nt + j];
+      for (int qd = 0; qd < nqd; ++qd) p.amq[(qd * nt + i) * nt + j] = wJ[qd] * (a / tb);
+    }
+  }
+}
+
 cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const ApplyParams& prm,
                          cudaStream_t stream) {
   const long long n_total = (long long)hp.n_xi * hp.n_t * hp.n_x;
   int ib = 256;
   long long ig = std::min<long long>((n_total + ib - 1) / ib, 152LL * 16);
-  sg_init_y_kernel<<<(int)ig, ib, 0, stream>>>(prm.x, prm.y, n_total, hp.n_x, hp.nn[0], hp.nn[1],
-                                              hp.nn[2], hp.dim);
+  if (hp.precision == kPrecF32)
+    sg_init_y_kernel<float><<<(int)ig, ib, 0, stream>>>(static_cast<const float*>(prm.x), static_cast<float*>(prm.y),
+                                                        n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+  else
+    sg_init_y_kernel<double><<<(int)ig, ib, 0, stream>>>(static_cast<const double*>(prm.x), static_cast<double*>(prm.y),
+                                                         n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<ApplyParams*>(&prm)};

@@ -206,12 +206,15 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
   using Sh = Shape<DIM, K>;
   constexpr int NQD = Sh::NQD, NKD = Sh::NKD, NC = Sh::NC, N = Sh::N;
   constexpr int SLOT = NC * NQD;                 // values per (cell, vector)
-  static_assert(sizeof(T) == 8, "8-byte value type expected");
+  using IO = typename A::IO;
+  const IO* __restrict__ xin = reinterpret_cast<const IO*>(p.x);
+  IO* __restrict__ yout = reinterpret_cast<IO*>(p.y);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int n_xi = p.n_xi, V = n_xi * NT, C = p.chunk;
 
   T* Qs = reinterpret_cast<T*>(smem_raw);                       // [C][V][NC][NQD]
+  // the 8-byte tables follow the value arrays at an 8-byte boundary
   T* Cs = Qs + (size_t)C * V * SLOT;                            // [C][term][NQD]
   T* Gv = Cs + (size_t)C * p.n_terms * NQD;                     // [nnz]
   T* Amq = Gv + p.nnz;                                          // [NQD][NT][NT]
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
       T val = A::zero();
-      if (interior) val = A::in(p.x[(long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx]);
+      if (interior) val = A::in(xin[(long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx]);
       Qs[(size_t)cv * SLOT + a] = val;
     }
     __syncthreads();
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
       if (interior)
-        A::add_out(p.y + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx,
+        A::add_out(yout + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx,
                    A::mul(Tb[v % NT], Qs[(size_t)cv * SLOT + a]));
     }
   }

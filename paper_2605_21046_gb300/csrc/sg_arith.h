@@ -31,6 +31,7 @@ struct Cf {
 
 struct F64 {
   using T = double;
+  using IO = double;
   static constexpr bool kDW = false;
   __device__ __forceinline__ static T in(double x) { return x; }
   __device__ __forceinline__ static T zero() { return 0.0; }
@@ -49,6 +50,7 @@ struct __align__(8) dw {
 
 struct DW {
   using T = dw;
+  using IO = double;
   static constexpr bool kDW = true;
 
   __device__ __forceinline__ static void two_sum(float a, float b, float& s, float& e) {
@@ -143,6 +145,24 @@ struct DW {
     atomicAdd(y, widen(v.h));
     if (v.l != 0.0f) atomicAdd(y, widen(v.l));
   }
+};
+
+// Native single precision (the FP32 pipe); used by the multigrid
+// preconditioner, whose vectors are float.
+struct F32 {
+  using T = float;
+  using IO = float;
+  static constexpr bool kDW = false;
+  __device__ __forceinline__ static T in(double x) { return (float)x; }
+  __device__ __forceinline__ static T in(float x) { return x; }
+  __device__ __forceinline__ static T zero() { return 0.0f; }
+  __device__ __forceinline__ static T cmul(Cf c, T x) { return c.h * x; }
+  __device__ __forceinline__ static void cfma(Cf c, T x, T& acc) { acc = fmaf(c.h, x, acc); }
+  __device__ __forceinline__ static T mul(T a, T b) { return a * b; }
+  __device__ __forceinline__ static void fma(T a, T b, T& acc) { acc = fmaf(a, b, acc); }
+  __device__ __forceinline__ static T add(T a, T b) { return a + b; }
+  __device__ __forceinline__ static T fin(T a) { return a; }
+  __device__ __forceinline__ static void add_out(float* y, T v) { atomicAdd(y, v); }
 };
 
 }  // namespace sg

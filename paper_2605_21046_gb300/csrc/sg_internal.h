@@ -42,6 +42,15 @@ struct GTable {
   std::vector<double> val;
 };
 
+// One separable coefficient piece (see sg_coeff), kept so that coarse
+// multigrid levels can re-evaluate the coefficient on their own meshes.
+struct Piece {
+  std::vector<int> mu;
+  double amp = 0.0;
+  int kind[3] = {0, 0, 0}, k[3] = {0, 0, 0};
+  std::vector<double> scale;           // per cell, empty = 1
+};
+
 struct HostProblem {
   int precision = SG_PREC_FP64;
   int dim = 2, k = 1, r = 1, M = 1, p = 0, n_slabs = 1;
@@ -55,6 +64,9 @@ struct HostProblem {
   GTable g;
   std::vector<double> A_hat, B_hat;     // (r+1)^2 each
   std::vector<double> S, Dhat;          // [q][n] interpolation, [q][p] collocation derivative
+  std::vector<double> dS;               // [q][n] derivative of the nodal basis at the Gauss points
+  std::vector<Piece> pieces;            // the coefficient as given
+  std::vector<int> piece_term;          // active term of every piece
   std::vector<double> wq;               // 1D Gauss weights
   std::vector<double> ctab;             // [cell][term][qd]: w_q |J| a_mu(x_q) / h_0^2
   std::vector<int> perm;                // chaos rows sorted by their number of G entries
@@ -64,11 +76,15 @@ struct HostProblem {
 sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, double T,
                              int M, int p, const sg_coeff* coef, HostProblem& hp,
                              std::string& msg);
+// The same from stored pieces (used for the coarse multigrid levels).
+sg_status build_host_problem_pieces(const sg_mesh* mesh, int k, int r, int n_slabs, double T,
+                                    int M, int p, const std::vector<Piece>& pieces,
+                                    HostProblem& hp, std::string& msg);
 
 // ---------------------------------------------------------------- kernels
 struct ApplyParams {
-  const double* x;
-  double* y;
+  const void* x;          // double (FP64, DW) or float (F32) vectors
+  void* y;
   const double* ctab;     // [n_cells][n_terms][NQD], w_q |J| a_mu(x_q) / h_0^2
   const int* g_row;       // [n_xi + 1]
   const int* g_col;       // [nnz]
@@ -96,15 +112,78 @@ struct LaunchShape {
 
 // Chooses a tile shape and thread count for the apply kernel of a problem.
 sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg);
-// Size of the dynamic shared memory the apply kernel needs for a chunk of cells.
-size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk);
-// Launches y = A x (init kernel + tile kernel) on a stream.
+// Size of the dynamic shared memory the apply kernel needs for a chunk of cells
+// (value_bytes = 8 for FP64 / DW, 4 for FP32).
+size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk,
+                        int value_bytes = 8);
+// Fills the kernel parameter block of an apply (device table pointers given).
+void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void* ctab,
+                       const int* grow, const int* gcol, const int* gterm, const double* gval,
+                       const int* perm, const void* x, void* y, int transpose, ApplyParams& p);
+// Launches y = A x (init kernel + chunk kernel) on a stream.
 cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const ApplyParams& prm,
                          cudaStream_t stream);
 // Kernel attribute set-up (max dynamic shared memory).
 cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t smem);
 
+// Precision of the apply kernels used inside the multigrid preconditioner.
+constexpr int kPrecF32 = SG_PREC_FP32;
+
+// ---------------------------------------------------------------- multigrid
+struct MGLevel {
+  HostProblem hp;            // level discretisation; hp.g holds the diagonal (block-Jacobi) coupling
+  LaunchShape ls;
+  bool coarsest = false;
+  int np = 0;                // padded patch size N_t * (k+1)^d
+  int n_int = 0;             // coarsest level: interior dofs per vector (N_t * interior nodes)
+  void* d_ctab = nullptr;    // device tables of the level apply (value type of the MG precision
+  int* d_grow = nullptr;     //  only for the vectors; tables stay double)
+  int* d_gcol = nullptr;
+  int* d_gterm = nullptr;
+  double* d_gval = nullptr;
+  int* d_perm = nullptr;
+  void* d_inv = nullptr;     // [class][cell][np][np] patch inverses, or coarsest [class][n_int][n_int]
+  int* d_inner = nullptr;    // coarsest: dof offset (i * n_x + node) of every interior dof
+  void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
+  void* d_b = nullptr;
+  void* d_r = nullptr;
+  // transfer from the next coarser level: per direction d, fine node index i ->
+  // coarse cell pc[i] and the (k+1) weights pw[i][.]; restriction lists per
+  // coarse node j: rptr[j]..rptr[j+1] entries (fine index, weight)
+  int* d_pc[3] = {nullptr, nullptr, nullptr};
+  void* d_pw[3] = {nullptr, nullptr, nullptr};      // weights in the MG precision
+  int* d_rptr[3] = {nullptr, nullptr, nullptr};
+  int* d_ridx[3] = {nullptr, nullptr, nullptr};
+  void* d_rw[3] = {nullptr, nullptr, nullptr};
+};
+
+struct MG {
+  int precision = SG_PREC_FP64;   // SG_PREC_FP64 or kPrecF32
+  int nu = 2;
+  double omega = 0.7;
+  int n_classes = 0;
+  std::vector<int> cls;           // diagonal class of every chaos row
+  int* d_cls = nullptr;
+  std::vector<MGLevel> lv;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double setup_ms = 0.0;
+};
+
+sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg);
+size_t krylov_bytes(long long N, int m);
+void mg_free(MG& mg);
+// z = P^{-1} r for one slab vector (double in, double out) on a stream.
+cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream);
+
 }  // namespace sg
+
+namespace sg {
+sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
+                 cudaStream_t s, std::string& msg,
+                 cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t));
+}
 
 struct sg_ctx {
   sg::HostProblem hp;
@@ -119,4 +198,8 @@ struct sg_ctx {
   double* d_xbuf = nullptr;   // workspaces of sg_apply_host (lazy)
   double* d_ybuf = nullptr;
   cudaStream_t host_stream = nullptr;
+  sg::MG* mg = nullptr;       // multigrid preconditioner (sg_mg_setup)
+  double* d_krylov = nullptr; // FGMRES workspace (lazy): V, Z, w, r and partial sums
+  size_t krylov_bytes = 0;
+  int krylov_restart = 0;
 };

@@ -1,0 +1,823 @@
+// Block-Jacobi geometric-multigrid preconditioner of the SG slab system
+// (paper, Sec. 3.5, remark on the algebraic solver): every chaos mode alpha is
+// preconditioned by one V-cycle of its diagonal block
+//     A_alpha = A_t (x) M_x + sum_mu [G_mu]_{alpha alpha} B_t (x) K_mu,
+// with a space-time Vanka patch smoother.  All N_xi * N_t vectors go through
+// the V-cycle together: the level operator is the apply kernel with the
+// diagonal coupling table, so one launch smooths every mode.
+//
+// Levels halve the cells per direction while every count is even and > 2;
+// coefficients are re-evaluated on every level (a per-cell scale is averaged
+// over the children).  Smoother: additive Vanka, one patch per cell = its
+// interior nodes x all time nodes, patch matrix = principal submatrix of the
+// level block operator (summed from the element matrices of the neighbouring
+// cells), exact dense inverse, damping omega, corrections divided by the
+// number of patches that hold the node; nu pre- and nu post-smoothing steps.
+// Transfer: canonical Q_k interpolation P (tensor product of 1D tables,
+// Dirichlet rows and columns removed), restriction P^T.  Coarsest level:
+// dense inverse of the interior block.  Dirichlet rows are the identity on
+// every level.  The whole V-cycle is captured once into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void* ctab,
+                       const int* grow, const int* gcol, const int* gterm, const double* gval,
+                       const int* perm, const void* x, void* y, int transpose, ApplyParams& p);
+cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t smem);
+
+namespace {
+
+// ------------------------------------------------------------------ kernels
+template <typename T>
+__global__ void mg_init_x(const T* __restrict__ b, T* __restrict__ x, long long n_total, long long n_x,
+                          int nnx, int nny, int nnz, int dim) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long m = idx % n_x;
+    const int ix = (int)(m % nnx), iy = (int)((m / nnx) % nny), iz = (int)(m / ((long long)nnx * nny));
+    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
+    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
+    x[idx] = bd ? b[idx] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void mg_sub(const T* __restrict__ b, T* __restrict__ r, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = b[i] - r[i];
+}
+
+template <typename S, typename D>
+__global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (D)a[i];
+}
+
+// Additive Vanka step: x += omega / mult * inv(patch) * r_patch for every
+// (cell, alpha).  One warp per (cell, 32 consecutive alpha): lanes share the
+// cell, so the patch inverse of a diagonal class is a broadcast load.
+template <typename T, int DIM, int K, int NT>
+__global__ void mg_vanka(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv,
+                         const int* __restrict__ cls, int n_xi, long long n_x, long long n_cells,
+                         int cells0, int cells1, int nnx, int nny, int nnz, T omega) {
+  constexpr int N = K + 1;
+  constexpr int NKD = DIM == 2 ? N * N : N * N * N;
+  constexpr int NP = NT * NKD;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int chunks = (n_xi + 31) / 32;
+  const long long cell = warp / chunks;
+  if (cell >= n_cells) return;
+  const int alpha = (int)(warp % chunks) * 32 + lane;
+  if (alpha >= n_xi) return;
+  const int cx = (int)(cell % cells0), cy = (int)((cell / cells0) % cells1), cz = (int)(cell / ((long long)cells0 * cells1));
+  long long node[NKD];
+  bool inner[NKD];
+  T rp[NP];
+#pragma unroll
+  for (int a = 0; a < NKD; ++a) {
+    const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
+    bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+    if (DIM == 3) in = in && gz > 0 && gz < nnz - 1;
+    inner[a] = in;
+    node[a] = ((long long)gz * nny + gy) * nnx + gx;
+#pragma unroll
+    for (int i = 0; i < NT; ++i) rp[i * NKD + a] = in ? r[(long long)(alpha * NT + i) * n_x + node[a]] : T(0);
+  }
+  const T* M = inv + ((long long)cls[alpha] * n_cells + cell) * NP * NP;
+#pragma unroll
+  for (int i = 0; i < NT; ++i)
+#pragma unroll
+    for (int a = 0; a < NKD; ++a) {
+      if (!inner[a]) continue;
+      const T* row = M + (i * NKD + a) * NP;
+      T z = T(0);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) z += row[q] * rp[q];
+      const long long g = node[a];
+      const int gx = (int)(g % nnx), gy = (int)((g / nnx) % nny), gz = (int)(g / ((long long)nnx * nny));
+      int mult = (gx % K == 0 ? 2 : 1) * (gy % K == 0 ? 2 : 1);
+      if (DIM == 3) mult *= (gz % K == 0 ? 2 : 1);
+      atomicAdd(x + (long long)(alpha * NT + i) * n_x + g, omega * z / T(mult));
+    }
+}
+
+// x_fine += P e_coarse: gather over the (k+1)^d nodes of the coarse cell that
+// holds the fine node (tensor product of the 1D interpolation tables).
+template <typename T, int DIM, int K>
+__global__ void mg_prolong_add(const T* __restrict__ ec, T* __restrict__ xf, int V, int nfx, int nfy, int nfz,
+                               int ncx, int ncy, int ncz, const int* __restrict__ pcx, const T* __restrict__ pwx,
+                               const int* __restrict__ pcy, const T* __restrict__ pwy,
+                               const int* __restrict__ pcz, const T* __restrict__ pwz) {
+  constexpr int N = K + 1;
+  const long long nf = (long long)nfx * nfy * nfz, nc = (long long)ncx * ncy * ncz;
+  const long long total = nf * V;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(idx / nf);
+    const long long f = idx - (long long)v * nf;
+    const int ix = (int)(f % nfx), iy = (int)((f / nfx) % nfy), iz = (int)(f / ((long long)nfx * nfy));
+    const T* e = ec + (long long)v * nc;
+    T s = T(0);
+    for (int c = 0; c < (DIM == 3 ? N : 1); ++c) {
+      const T wz = DIM == 3 ? pwz[iz * N + c] : T(1);
+      if (wz == T(0)) continue;
+      const long long jz = DIM == 3 ? (long long)(pcz[iz] * K + c) : 0;
+      for (int b = 0; b < N; ++b) {
+        const T wy = pwy[iy * N + b];
+        if (wy == T(0)) continue;
+        const long long jy = pcy[iy] * K + b;
+        for (int a = 0; a < N; ++a) {
+          const T wx = pwx[ix * N + a];
+          if (wx == T(0)) continue;
+          s += wz * wy * wx * e[(jz * ncy + jy) * ncx + pcx[ix] * K + a];
+        }
+      }
+    }
+    xf[idx] += s;
+  }
+}
+
+// b_coarse = P^T r_fine: gather over the fine nodes in the support of each
+// coarse node (tensor product of the 1D transposed tables).
+template <typename T, int DIM>
+__global__ void mg_restrict(const T* __restrict__ rf, T* __restrict__ bc, int V, int nfx, int nfy, int nfz,
+                            int ncx, int ncy, int ncz, const int* __restrict__ ptrx, const int* __restrict__ idxx,
+                            const T* __restrict__ wx, const int* __restrict__ ptry, const int* __restrict__ idxy,
+                            const T* __restrict__ wy, const int* __restrict__ ptrz, const int* __restrict__ idxz,
+                            const T* __restrict__ wz) {
+  const long long nf = (long long)nfx * nfy * nfz, nc = (long long)ncx * ncy * ncz;
+  const long long total = nc * V;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(idx / nc);
+    const long long j = idx - (long long)v * nc;
+    const int jx = (int)(j % ncx), jy = (int)((j / ncx) % ncy), jz = (int)(j / ((long long)ncx * ncy));
+    const T* r = rf + (long long)v * nf;
+    T s = T(0);
+    const int z0 = DIM == 3 ? ptrz[jz] : 0, z1 = DIM == 3 ? ptrz[jz + 1] : 1;
+    for (int tz = z0; tz < z1; ++tz) {
+      const T w3 = DIM == 3 ? wz[tz] : T(1);
+      const long long iz = DIM == 3 ? idxz[tz] : 0;
+      for (int ty = ptry[jy]; ty < ptry[jy + 1]; ++ty) {
+        const T w2 = w3 * wy[ty];
+        const long long row = (iz * nfy + idxy[ty]) * nfx;
+        for (int tx = ptrx[jx]; tx < ptrx[jx + 1]; ++tx) s += w2 * wx[tx] * r[row + idxx[tx]];
+      }
+    }
+    bc[idx] = s;
+  }
+}
+
+// Coarsest level: x[inner] = inv(C_class) b[inner] for every chaos mode
+// (one CTA per mode; the right-hand side is staged in shared memory).
+template <typename T>
+__global__ void mg_coarse(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv,
+                          const int* __restrict__ cls, const long long* __restrict__ inner, int n_int,
+                          int n_t, long long n_x) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* bs = reinterpret_cast<T*>(sm);
+  const int alpha = blockIdx.x;
+  const long long base = (long long)alpha * n_t * n_x;
+  for (int i = threadIdx.x; i < n_int; i += blockDim.x) bs[i] = b[base + inner[i]];
+  __syncthreads();
+  const T* M = inv + (long long)cls[alpha] * n_int * n_int;
+  for (int i = threadIdx.x; i < n_int; i += blockDim.x) {
+    T s = T(0);
+    const T* row = M + (long long)i * n_int;
+    for (int q = 0; q < n_int; ++q) s += row[q] * bs[q];
+    x[base + inner[i]] = s;
+  }
+}
+
+// ------------------------------------------------------------------ host set-up
+
+int grid_for(long long n, int block) {
+  return (int)std::max<long long>(1, std::min<long long>((n + block - 1) / block, 152LL * 32));
+}
+
+// In-place inverse of a dense n x n matrix (Gauss-Jordan, partial pivoting).
+bool invert(std::vector<double>& a, int n) {
+  std::vector<double> inv(n * (size_t)n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)piv * n + c])) piv = r;
+    if (a[(size_t)piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)c * n + k], a[(size_t)piv * n + k]);
+        std::swap(inv[(size_t)c * n + k], inv[(size_t)piv * n + k]);
+      }
+    const double d = 1.0 / a[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      a[(size_t)c * n + k] *= d;
+      inv[(size_t)c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+// Reference element matrices of a level: mass (cell independent) and, per
+// cell, the stiffness with the class coefficient cbar(q) = sum_t diag[t] ctab[t][q].
+struct ElementData {
+  int nkd = 0, nqd = 0, dim = 2;
+  std::vector<double> phi;    // [a][q]
+  std::vector<double> grad;   // [d][a][q] reference derivative
+  std::vector<double> wJ;     // [q]
+  std::vector<double> mass;   // [a][b]
+};
+
+ElementData element_data(const HostProblem& hp) {
+  ElementData e;
+  const int n = hp.k + 1;
+  e.dim = hp.dim;
+  e.nkd = hp.dim == 2 ? n * n : n * n * n;
+  e.nqd = e.nkd;
+  e.phi.assign((size_t)e.nkd * e.nqd, 0.0);
+  e.grad.assign((size_t)3 * e.nkd * e.nqd, 0.0);
+  e.wJ.assign(e.nqd, 0.0);
+  double detJ = 1.0;
+  for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];
+  for (int q = 0; q < e.nqd; ++q) {
+    const int qi[3] = {q % n, (q / n) % n, q / (n * n)};
+    double w = detJ;
+    for (int d = 0; d < hp.dim; ++d) w *= hp.wq[qi[d]];
+    e.wJ[q] = w;
+    for (int a = 0; a < e.nkd; ++a) {
+      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+      double v = 1.0;
+      for (int d = 0; d < hp.dim; ++d) v *= hp.S[qi[d] * n + ai[d]];
+      e.phi[(size_t)a * e.nqd + q] = v;
+      for (int dd = 0; dd < hp.dim; ++dd) {
+        double g = 1.0;
+        for (int d = 0; d < hp.dim; ++d) g *= d == dd ? hp.dS[qi[d] * n + ai[d]] : hp.S[qi[d] * n + ai[d]];
+        e.grad[((size_t)dd * e.nkd + a) * e.nqd + q] = g;
+      }
+    }
+  }
+  e.mass.assign((size_t)e.nkd * e.nkd, 0.0);
+  for (int a = 0; a < e.nkd; ++a)
+    for (int b = 0; b < e.nkd; ++b) {
+      double s = 0.0;
+      for (int q = 0; q < e.nqd; ++q) s += e.wJ[q] * e.phi[(size_t)a * e.nqd + q] * e.phi[(size_t)b * e.nqd + q];
+      e.mass[(size_t)a * e.nkd + b] = s;
+    }
+  return e;
+}
+
+// Element stiffness of cell c for the class coefficient (ctab holds
+// w_q |J| a_t / h_0^2; direction d carries (h_0 / h_d)^2).
+void element_stiffness(const HostProblem& hp, const ElementData& e, const std::vector<double>& diag,
+                       long long c, std::vector<double>& K) {
+  std::vector<double> cbar(e.nqd, 0.0);
+  for (int t = 0; t < hp.n_terms; ++t) {
+    if (diag[t] == 0.0) continue;
+    const double* ct = hp.ctab.data() + ((size_t)c * hp.n_terms + t) * e.nqd;
+    for (int q = 0; q < e.nqd; ++q) cbar[q] += diag[t] * ct[q];
+  }
+  double ratio[3];
+  for (int d = 0; d < 3; ++d) ratio[d] = d < hp.dim ? (hp.h[0] * hp.h[0]) / (hp.h[d] * hp.h[d]) : 0.0;
+  K.assign((size_t)e.nkd * e.nkd, 0.0);
+  for (int a = 0; a < e.nkd; ++a)
+    for (int b = a; b < e.nkd; ++b) {
+      double s = 0.0;
+      for (int d = 0; d < hp.dim; ++d) {
+        const double* ga = e.grad.data() + ((size_t)d * e.nkd + a) * e.nqd;
+        const double* gb = e.grad.data() + ((size_t)d * e.nkd + b) * e.nqd;
+        double sd = 0.0;
+        for (int q = 0; q < e.nqd; ++q) sd += cbar[q] * ga[q] * gb[q];
+        s += ratio[d] * sd;
+      }
+      K[(size_t)a * e.nkd + b] = s;
+      K[(size_t)b * e.nkd + a] = s;
+    }
+}
+
+void cell_coords(const HostProblem& hp, long long c, int cc[3]) {
+  cc[0] = (int)(c % hp.cells[0]);
+  cc[1] = (int)((c / hp.cells[0]) % hp.cells[1]);
+  cc[2] = (int)(c / ((long long)hp.cells[0] * hp.cells[1]));
+}
+
+bool node_interior(const HostProblem& hp, const int g[3]) {
+  for (int d = 0; d < hp.dim; ++d)
+    if (g[d] <= 0 || g[d] >= hp.nn[d] - 1) return false;
+  return true;
+}
+
+// Vanka patch inverses of one level and class: [cell][np][np].
+bool patch_inverses(const HostProblem& hp, const ElementData& e, const std::vector<double>& diag,
+                    std::vector<double>& out) {
+  const int n = hp.k + 1, nkd = e.nkd, nt = hp.n_t, np = nt * nkd;
+  std::vector<std::vector<double>> Kc(hp.n_cells);
+  for (long long c = 0; c < hp.n_cells; ++c) element_stiffness(hp, e, diag, c, Kc[c]);
+  out.assign((size_t)hp.n_cells * np * np, 0.0);
+  bool ok = true;
+#pragma omp parallel for schedule(dynamic, 64) reduction(&& : ok)
+  for (long long c = 0; c < hp.n_cells; ++c) {
+    int cc[3];
+    cell_coords(hp, c, cc);
+    std::vector<double> Mg((size_t)nkd * nkd, 0.0), Kg((size_t)nkd * nkd, 0.0);
+    int gi[64][3];
+    for (int a = 0; a < nkd; ++a) {
+      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+      for (int d = 0; d < 3; ++d) gi[a][d] = d < hp.dim ? cc[d] * hp.k + ai[d] : 0;
+    }
+    const int span = hp.dim == 3 ? 1 : 0;
+    for (int oz = -span; oz <= span; ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          const int nc[3] = {cc[0] + ox, cc[1] + oy, cc[2] + oz};
+          bool valid = true;
+          for (int d = 0; d < hp.dim; ++d) valid = valid && nc[d] >= 0 && nc[d] < hp.cells[d];
+          if (!valid) continue;
+          const long long cn = ((long long)nc[2] * hp.cells[1] + nc[1]) * hp.cells[0] + nc[0];
+          int loc[64];
+          for (int a = 0; a < nkd; ++a) {
+            loc[a] = -1;
+            int l = 0, stride = 1;
+            bool in = true;
+            for (int d = 0; d < hp.dim; ++d) {
+              const int off = gi[a][d] - nc[d] * hp.k;
+              if (off < 0 || off > hp.k) { in = false; break; }
+              l += off * stride;
+              stride *= n;
+            }
+            if (in) loc[a] = l;
+          }
+          for (int a = 0; a < nkd; ++a) {
+            if (loc[a] < 0) continue;
+            for (int b = 0; b < nkd; ++b) {
+              if (loc[b] < 0) continue;
+              Mg[(size_t)a * nkd + b] += e.mass[(size_t)loc[a] * nkd + loc[b]];
+              Kg[(size_t)a * nkd + b] += Kc[cn][(size_t)loc[a] * nkd + loc[b]];
+            }
+          }
+        }
+    std::vector<double> P((size_t)np * np, 0.0);
+    for (int i = 0; i < nt; ++i)
+      for (int a = 0; a < nkd; ++a) {
+        const int row = i * nkd + a;
+        if (!node_interior(hp, gi[a])) { P[(size_t)row * np + row] = 1.0; continue; }
+        for (int j = 0; j < nt; ++j)
+          for (int b = 0; b < nkd; ++b) {
+            if (!node_interior(hp, gi[b])) continue;
+            double v = hp.A_hat[i * nt + j] * Mg[(size_t)a * nkd + b];
+            if (i == j) v += hp.tau * hp.B_hat[i * nt + i] * Kg[(size_t)a * nkd + b];
+            P[(size_t)row * np + j * nkd + b] = v;
+          }
+      }
+    if (!invert(P, np)) ok = false;
+    std::copy(P.begin(), P.end(), out.begin() + (size_t)c * np * np);
+  }
+  return ok;
+}
+
+// Coarsest level: dense inverse of the interior block of one class.
+bool coarse_inverse(const HostProblem& hp, const ElementData& e, const std::vector<double>& diag,
+                    const std::vector<long long>& node_of, std::vector<double>& out) {
+  const int n = hp.k + 1, nkd = e.nkd, nt = hp.n_t;
+  const int nin = (int)node_of.size();
+  std::vector<int> idx(hp.n_x, -1);
+  for (int i = 0; i < nin; ++i) idx[node_of[i]] = i;
+  const int N = nt * nin;
+  std::vector<double> C((size_t)N * N, 0.0), K;
+  for (long long c = 0; c < hp.n_cells; ++c) {
+    element_stiffness(hp, e, diag, c, K);
+    int cc[3];
+    cell_coords(hp, c, cc);
+    int g[64];
+    for (int a = 0; a < nkd; ++a) {
+      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+      long long gl = 0, stride = 1;
+      for (int d = 0; d < hp.dim; ++d) {
+        gl += (long long)(cc[d] * hp.k + ai[d]) * stride;
+        stride *= hp.nn[d];
+      }
+      g[a] = idx[gl];
+    }
+    for (int i = 0; i < nt; ++i)
+      for (int a = 0; a < nkd; ++a) {
+        if (g[a] < 0) continue;
+        for (int j = 0; j < nt; ++j)
+          for (int b = 0; b < nkd; ++b) {
+            if (g[b] < 0) continue;
+            double v = hp.A_hat[i * nt + j] * e.mass[(size_t)a * nkd + b];
+            if (i == j) v += hp.tau * hp.B_hat[i * nt + i] * K[(size_t)a * nkd + b];
+            C[(size_t)(i * nin + g[a]) * N + j * nin + g[b]] += v;
+          }
+      }
+  }
+  if (!invert(C, N)) return false;
+  out.swap(C);
+  return true;
+}
+
+// 1D interpolation table of one direction between a fine and a coarse level.
+void transfer_1d(const HostProblem& fine, const HostProblem& coarse, int d, std::vector<int>& pc,
+                 std::vector<double>& pw, std::vector<int>& rptr, std::vector<int>& ridx, std::vector<double>& rw) {
+  const int K = fine.k, n = K + 1;
+  const std::vector<double> gll = lobatto_nodes(K);
+  const int nf = fine.nn[d], nc = coarse.nn[d];
+  pc.assign(nf, 0);
+  pw.assign((size_t)nf * n, 0.0);
+  std::vector<std::vector<std::pair<int, double>>> cols(nc);
+  for (int i = 0; i < nf; ++i) {
+    const int cf = std::min(i / K, fine.cells[d] - 1);
+    const double pos = cf + gll[i - cf * K];
+    const double cpos = 0.5 * pos;
+    const int ccell = std::min((int)std::floor(cpos), coarse.cells[d] - 1);
+    const double s = cpos - ccell;
+    pc[i] = ccell;
+    const bool fine_bd = i == 0 || i == nf - 1;
+    for (int a = 0; a < n; ++a) {
+      const int j = ccell * K + a;
+      const bool coarse_bd = j == 0 || j == nc - 1;
+      double w = (fine_bd || coarse_bd) ? 0.0 : lagrange(gll, a, s);
+      pw[(size_t)i * n + a] = w;
+      if (w != 0.0) cols[j].push_back({i, w});
+    }
+  }
+  rptr.assign(nc + 1, 0);
+  ridx.clear();
+  rw.clear();
+  for (int j = 0; j < nc; ++j) {
+    for (auto& t : cols[j]) {
+      ridx.push_back(t.first);
+      rw.push_back(t.second);
+    }
+    rptr[j + 1] = (int)ridx.size();
+  }
+}
+
+template <typename T>
+cudaError_t upload_vec(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), std::max<size_t>(1, src.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+cudaError_t upload_values(void** dst, const std::vector<double>& src, int precision) {
+  if (precision == kPrecF32) {
+    std::vector<float> f(src.begin(), src.end());
+    return upload_vec(reinterpret_cast<float**>(dst), f);
+  }
+  return upload_vec(reinterpret_cast<double**>(dst), src);
+}
+
+// The diagonal (block-Jacobi) coupling table: row alpha keeps its own column.
+void diagonal_table(const HostProblem& fine, GTable& g, std::vector<std::vector<double>>& diag_of_row) {
+  diag_of_row.assign(fine.n_xi, std::vector<double>(fine.n_terms, 0.0));
+  for (int a = 0; a < fine.n_xi; ++a)
+    for (int e = fine.g.row[a]; e < fine.g.row[a + 1]; ++e)
+      if (fine.g.col[e] == a) diag_of_row[a][fine.g.term[e]] += fine.g.val[e];
+  g.row.assign(fine.n_xi + 1, 0);
+  g.col.clear();
+  g.term.clear();
+  g.val.clear();
+  for (int a = 0; a < fine.n_xi; ++a) {
+    for (int t = 0; t < fine.n_terms; ++t)
+      if (diag_of_row[a][t] != 0.0) {
+        g.col.push_back(a);
+        g.term.push_back(t);
+        g.val.push_back(diag_of_row[a][t]);
+      }
+    g.row[a + 1] = (int)g.col.size();
+  }
+}
+
+// Averages a per-cell scale over the 2^d children of every coarse cell.
+std::vector<double> coarsen_scale(const std::vector<double>& s, const HostProblem& fine) {
+  if (s.empty()) return s;
+  const int cx = fine.cells[0] / 2, cy = fine.cells[1] / 2, cz = fine.dim == 3 ? fine.cells[2] / 2 : 1;
+  std::vector<double> out((size_t)cx * cy * cz, 0.0);
+  const int kz = fine.dim == 3 ? 2 : 1;
+  const double inv = 1.0 / (4 * kz);
+  for (int z = 0; z < cz; ++z)
+    for (int y = 0; y < cy; ++y)
+      for (int x = 0; x < cx; ++x) {
+        double acc = 0.0;
+        for (int dz = 0; dz < kz; ++dz)
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+              acc += s[((size_t)(kz * z + dz) * fine.cells[1] + 2 * y + dy) * fine.cells[0] + 2 * x + dx];
+        out[((size_t)z * cy + y) * cx + x] = acc * inv;
+      }
+  return out;
+}
+
+template <typename T>
+cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s);
+
+template <typename T>
+cudaError_t residual(MG& mg, int l, cudaStream_t s) {
+  MGLevel& L = mg.lv[l];
+  ApplyParams p;
+  fill_apply_params(L.hp, L.ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, 0, p);
+  cudaError_t e = launch_apply(L.hp, L.ls, p, s);
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
+  mg_sub<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_r), n);
+  return cudaGetLastError();
+}
+
+template <typename T, int DIM, int K, int NT>
+void launch_vanka(MG& mg, MGLevel& L, cudaStream_t s) {
+  const long long warps = L.hp.n_cells * ((L.hp.n_xi + 31) / 32);
+  const int block = 128;
+  const long long grid = (warps * 32 + block - 1) / block;
+  mg_vanka<T, DIM, K, NT><<<(unsigned)grid, block, 0, s>>>(
+      static_cast<const T*>(L.d_r), static_cast<T*>(L.d_x), static_cast<const T*>(L.d_inv), mg.d_cls, L.hp.n_xi,
+      L.hp.n_x, L.hp.n_cells, L.hp.cells[0], L.hp.cells[1], L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], T(mg.omega));
+}
+
+template <typename T>
+bool vanka(MG& mg, MGLevel& L, cudaStream_t s) {
+  const int d = L.hp.dim, k = L.hp.k, t = L.hp.n_t;
+#define SG_V(D, KK, TT) \
+  if (d == D && k == KK && t == TT) { launch_vanka<T, D, KK, TT>(mg, L, s); return true; }
+  SG_V(2, 1, 1) SG_V(2, 1, 2) SG_V(2, 1, 3) SG_V(2, 1, 4)
+  SG_V(2, 2, 1) SG_V(2, 2, 2) SG_V(2, 2, 3) SG_V(2, 2, 4)
+  SG_V(2, 3, 1) SG_V(2, 3, 2) SG_V(2, 3, 3) SG_V(2, 3, 4)
+  SG_V(3, 1, 1) SG_V(3, 1, 2) SG_V(3, 2, 1) SG_V(3, 2, 2)
+#undef SG_V
+  return false;
+}
+
+template <typename T>
+bool prolong(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
+  const long long n = (long long)F.hp.n_x * V;
+  const int g = grid_for(n, 256);
+#define SG_P(D, KK)                                                                                             \
+  if (F.hp.dim == D && F.hp.k == KK) {                                                                        \
+    mg_prolong_add<T, D, KK><<<g, 256, 0, s>>>(static_cast<const T*>(C.d_x), static_cast<T*>(F.d_x), V, F.hp.nn[0], \
+                                               F.hp.nn[1], F.hp.nn[2], C.hp.nn[0], C.hp.nn[1], C.hp.nn[2],      \
+                                               F.d_pc[0], static_cast<const T*>(F.d_pw[0]), F.d_pc[1],          \
+                                               static_cast<const T*>(F.d_pw[1]), F.d_pc[2],                      \
+                                               static_cast<const T*>(F.d_pw[2]));                                \
+    return true;                                                                                              \
+  }
+  SG_P(2, 1) SG_P(2, 2) SG_P(2, 3) SG_P(3, 1) SG_P(3, 2)
+#undef SG_P
+  return false;
+}
+
+template <typename T>
+void restrict_to(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
+  const long long n = (long long)C.hp.n_x * V;
+  const int g = grid_for(n, 256);
+  if (F.hp.dim == 2)
+    mg_restrict<T, 2><<<g, 256, 0, s>>>(static_cast<const T*>(F.d_r), static_cast<T*>(C.d_b), V, F.hp.nn[0],
+                                        F.hp.nn[1], F.hp.nn[2], C.hp.nn[0], C.hp.nn[1], C.hp.nn[2], F.d_rptr[0],
+                                        F.d_ridx[0], static_cast<const T*>(F.d_rw[0]), F.d_rptr[1], F.d_ridx[1],
+                                        static_cast<const T*>(F.d_rw[1]), F.d_rptr[2], F.d_ridx[2],
+                                        static_cast<const T*>(F.d_rw[2]));
+  else
+    mg_restrict<T, 3><<<g, 256, 0, s>>>(static_cast<const T*>(F.d_r), static_cast<T*>(C.d_b), V, F.hp.nn[0],
+                                        F.hp.nn[1], F.hp.nn[2], C.hp.nn[0], C.hp.nn[1], C.hp.nn[2], F.d_rptr[0],
+                                        F.d_ridx[0], static_cast<const T*>(F.d_rw[0]), F.d_rptr[1], F.d_ridx[1],
+                                        static_cast<const T*>(F.d_rw[1]), F.d_rptr[2], F.d_ridx[2],
+                                        static_cast<const T*>(F.d_rw[2]));
+}
+
+template <typename T>
+cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
+  MGLevel& L = mg.lv[l];
+  const int V = L.hp.n_xi * L.hp.n_t;
+  const long long n = (long long)V * L.hp.n_x;
+  mg_init_x<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x), n, L.hp.n_x,
+                                                L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
+  if (L.coarsest) {
+    const size_t smem = (size_t)L.n_int * sizeof(T);
+    mg_coarse<T><<<L.hp.n_xi, 256, smem, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
+                                              static_cast<const T*>(L.d_inv), mg.d_cls,
+                                              reinterpret_cast<const long long*>(L.d_inner), L.n_int, L.hp.n_t, L.hp.n_x);
+    return cudaGetLastError();
+  }
+  cudaError_t e;
+  for (int it = 0; it < mg.nu; ++it) {
+    if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
+    if (!vanka<T>(mg, L, s)) return cudaErrorInvalidValue;
+  }
+  if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
+  MGLevel& C = mg.lv[l + 1];
+  restrict_to<T>(L, C, V, s);
+  if ((e = issue_vcycle<T>(mg, l + 1, s)) != cudaSuccess) return e;
+  if (!prolong<T>(L, C, V, s)) return cudaErrorInvalidValue;
+  for (int it = 0; it < mg.nu; ++it) {
+    if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
+    if (!vanka<T>(mg, L, s)) return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void mg_free(MG& mg) {
+  if (mg.exec) cudaGraphExecDestroy(mg.exec);
+  if (mg.graph) cudaGraphDestroy(mg.graph);
+  if (mg.stream) cudaStreamDestroy(mg.stream);
+  cudaFree(mg.d_cls);
+  for (MGLevel& L : mg.lv) {
+    cudaFree(L.d_ctab); cudaFree(L.d_grow); cudaFree(L.d_gcol); cudaFree(L.d_gterm); cudaFree(L.d_gval);
+    cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner);
+    cudaFree(L.d_x); cudaFree(L.d_b); cudaFree(L.d_r);
+    for (int d = 0; d < 3; ++d) {
+      cudaFree(L.d_pc[d]); cudaFree(L.d_pw[d]); cudaFree(L.d_rptr[d]); cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
+    }
+  }
+  mg.lv.clear();
+  mg.exec = nullptr;
+  mg.graph = nullptr;
+  mg.stream = nullptr;
+  mg.d_cls = nullptr;
+}
+
+sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg) {
+  const auto t0 = std::chrono::steady_clock::now();
+  mg.precision = precision;
+  mg.nu = nu;
+  mg.omega = omega;
+  // diagonal classes of the chaos rows
+  GTable gdiag;
+  std::vector<std::vector<double>> drow;
+  diagonal_table(fine, gdiag, drow);
+  std::map<std::vector<double>, int> key;
+  std::vector<std::vector<double>> class_diag;
+  mg.cls.assign(fine.n_xi, 0);
+  for (int a = 0; a < fine.n_xi; ++a) {
+    auto it = key.find(drow[a]);
+    if (it == key.end()) {
+      key[drow[a]] = (int)class_diag.size();
+      mg.cls[a] = (int)class_diag.size();
+      class_diag.push_back(drow[a]);
+    } else {
+      mg.cls[a] = it->second;
+    }
+  }
+  mg.n_classes = (int)class_diag.size();
+  // level problems
+  std::vector<HostProblem> hps;
+  hps.push_back(fine);
+  while (true) {
+    const HostProblem& f = hps.back();
+    bool ok = true;
+    for (int d = 0; d < f.dim; ++d) ok = ok && f.cells[d] % 2 == 0 && f.cells[d] > 2;
+    if (!ok) break;
+    sg_mesh m;
+    std::memset(&m, 0, sizeof(m));
+    m.dim = f.dim;
+    for (int d = 0; d < 3; ++d) {
+      m.cells[d] = d < f.dim ? f.cells[d] / 2 : 1;
+      m.lo[d] = f.lo[d];
+      m.hi[d] = f.lo[d] + f.h[d] * f.cells[d];
+    }
+    std::vector<Piece> pieces = f.pieces;
+    for (Piece& pc : pieces) pc.scale = coarsen_scale(pc.scale, f);
+    HostProblem c;
+    sg_status st = build_host_problem_pieces(&m, f.k, f.r, f.n_slabs, f.T, f.M, f.p, pieces, c, msg);
+    if (st != SG_OK) return st;
+    hps.push_back(std::move(c));
+  }
+  mg.lv.resize(hps.size());
+  cudaError_t e = cudaSuccess;
+  for (size_t l = 0; l < hps.size(); ++l) {
+    MGLevel& L = mg.lv[l];
+    L.hp = std::move(hps[l]);
+    L.hp.g = gdiag;
+    L.hp.perm.resize(L.hp.n_xi);
+    for (int a = 0; a < L.hp.n_xi; ++a) L.hp.perm[a] = a;
+    L.hp.precision = precision;
+    L.coarsest = l + 1 == mg.lv.size();
+    sg_status st = plan_apply(L.hp, L.ls, msg);
+    if (st != SG_OK) return st;
+    if ((e = prepare_apply_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t, L.ls.smem)) != cudaSuccess) break;
+    const int n = L.hp.k + 1;
+    const int nkd = L.hp.dim == 2 ? n * n : n * n * n;
+    L.np = L.hp.n_t * nkd;
+    const ElementData ed = element_data(L.hp);
+    std::vector<double> inv;
+    if (L.coarsest) {
+      std::vector<long long> node_of;
+      for (long long m = 0; m < L.hp.n_x; ++m) {
+        const int g[3] = {(int)(m % L.hp.nn[0]), (int)((m / L.hp.nn[0]) % L.hp.nn[1]),
+                          (int)(m / ((long long)L.hp.nn[0] * L.hp.nn[1]))};
+        if (node_interior(L.hp, g)) node_of.push_back(m);
+      }
+      L.n_int = L.hp.n_t * (int)node_of.size();
+      if (L.n_int > 2048 || L.n_int * sizeof(double) > 48 * 1024) {
+        msg = "coarsest multigrid level too large (mesh cannot be coarsened enough)";
+        return SG_ERR_UNSUPPORTED;
+      }
+      std::vector<long long> inner_dofs;
+      for (int i = 0; i < L.hp.n_t; ++i)
+        for (long long m : node_of) inner_dofs.push_back((long long)i * L.hp.n_x + m);
+      for (int c = 0; c < mg.n_classes; ++c) {
+        std::vector<double> ci;
+        if (!coarse_inverse(L.hp, ed, class_diag[c], node_of, ci)) { msg = "singular coarse operator"; return SG_ERR_ARG; }
+        inv.insert(inv.end(), ci.begin(), ci.end());
+      }
+      if ((e = upload_vec(reinterpret_cast<long long**>(&L.d_inner), inner_dofs)) != cudaSuccess) break;
+    } else {
+      for (int c = 0; c < mg.n_classes; ++c) {
+        std::vector<double> pi;
+        if (!patch_inverses(L.hp, ed, class_diag[c], pi)) { msg = "singular Vanka patch"; return SG_ERR_ARG; }
+        inv.insert(inv.end(), pi.begin(), pi.end());
+      }
+    }
+    if ((e = upload_values(&L.d_inv, inv, precision)) != cudaSuccess) break;
+    // level apply tables (coefficient stays double; vectors use the MG precision)
+    if ((e = upload_vec(reinterpret_cast<double**>(&L.d_ctab), L.hp.ctab)) != cudaSuccess) break;
+    if ((e = upload_vec(&L.d_grow, L.hp.g.row)) != cudaSuccess) break;
+    if ((e = upload_vec(&L.d_gcol, L.hp.g.col)) != cudaSuccess) break;
+    if ((e = upload_vec(&L.d_gterm, L.hp.g.term)) != cudaSuccess) break;
+    if ((e = upload_vec(&L.d_gval, L.hp.g.val)) != cudaSuccess) break;
+    if ((e = upload_vec(&L.d_perm, L.hp.perm)) != cudaSuccess) break;
+    const size_t vb = precision == kPrecF32 ? 4 : 8;
+    const size_t bytes = (size_t)L.hp.n_xi * L.hp.n_t * L.hp.n_x * vb;
+    if ((e = cudaMalloc(&L.d_x, bytes)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&L.d_b, bytes)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&L.d_r, bytes)) != cudaSuccess) break;
+    if (l > 0) {
+      MGLevel& F = mg.lv[l - 1];
+      for (int d = 0; d < 3; ++d) {
+        std::vector<int> pc, rptr, ridx;
+        std::vector<double> pw, rw;
+        if (d < F.hp.dim) {
+          transfer_1d(F.hp, L.hp, d, pc, pw, rptr, ridx, rw);
+        } else {
+          pc = {0};
+          pw.assign(F.hp.k + 1, 0.0);
+          pw[0] = 1.0;
+          rptr = {0, 1};
+          ridx = {0};
+          rw = {1.0};
+        }
+        if ((e = upload_vec(&F.d_pc[d], pc)) != cudaSuccess) break;
+        if ((e = upload_values(&F.d_pw[d], pw, precision)) != cudaSuccess) break;
+        if ((e = upload_vec(&F.d_rptr[d], rptr)) != cudaSuccess) break;
+        if ((e = upload_vec(&F.d_ridx[d], ridx)) != cudaSuccess) break;
+        if ((e = upload_values(&F.d_rw[d], rw, precision)) != cudaSuccess) break;
+      }
+      if (e != cudaSuccess) break;
+    }
+  }
+  if (e == cudaSuccess) e = upload_vec(&mg.d_cls, mg.cls);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
+  }
+  mg.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return SG_OK;
+}
+
+cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream) {
+  MGLevel& L0 = mg.lv[0];
+  const long long n = (long long)L0.hp.n_xi * L0.hp.n_t * L0.hp.n_x;
+  const bool f32 = mg.precision == kPrecF32;
+  cudaError_t e;
+  if (!mg.exec) {
+    if ((e = cudaStreamBeginCapture(mg.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t ei = f32 ? issue_vcycle<float>(mg, 0, mg.stream) : issue_vcycle<double>(mg, 0, mg.stream);
+    e = cudaStreamEndCapture(mg.stream, &mg.graph);
+    if (ei != cudaSuccess) return ei;
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGraphInstantiate(&mg.exec, mg.graph, 0)) != cudaSuccess) return e;
+  }
+  if (f32)
+    mg_convert<double, float><<<grid_for(n, 256), 256, 0, stream>>>(r, static_cast<float*>(L0.d_b), n);
+  else
+    mg_convert<double, double><<<grid_for(n, 256), 256, 0, stream>>>(r, static_cast<double*>(L0.d_b), n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaGraphLaunch(mg.exec, stream)) != cudaSuccess) return e;
+  if (f32)
+    mg_convert<float, double><<<grid_for(n, 256), 256, 0, stream>>>(static_cast<const float*>(L0.d_x), z, n);
+  else
+    mg_convert<double, double><<<grid_for(n, 256), 256, 0, stream>>>(static_cast<const double*>(L0.d_x), z, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -189,14 +189,38 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
                              int M, int p, const sg_coeff* coef, HostProblem& hp,
                              std::string& msg) {
   if (!mesh || !coef) { msg = "null mesh or coefficient"; return SG_ERR_ARG; }
-  if (mesh->dim != 2 && mesh->dim != 3) { msg = "dim must be 2 or 3"; return SG_ERR_UNSUPPORTED; }
-  if (k < 1 || k > kMaxK || (mesh->dim == 3 && k > 2)) { msg = "fe_degree not built"; return SG_ERR_UNSUPPORTED; }
-  if (r < 0 || r + 1 > kMaxNT) { msg = "time_degree not built"; return SG_ERR_UNSUPPORTED; }
-  if (n_slabs < 1 || !(T > 0.0) || M < 1 || p < 0 || M > 16 || p > 12) { msg = "invalid slabs, T, M or order"; return SG_ERR_ARG; }
   if (coef->n_pieces < 1 || !coef->mu || !coef->amp || !coef->factor_kind || !coef->factor_k) {
     msg = "coefficient needs at least one piece and all arrays";
     return SG_ERR_ARG;
   }
+  if (M < 1 || M > 16) { msg = "invalid M"; return SG_ERR_ARG; }
+  int64_t n_cells = 1;
+  for (int d = 0; d < mesh->dim && d < 3; ++d) n_cells *= std::max(1, mesh->cells[d]);
+  std::vector<Piece> pieces(coef->n_pieces);
+  for (int pc = 0; pc < coef->n_pieces; ++pc) {
+    Piece& q = pieces[pc];
+    q.mu.assign(coef->mu + (size_t)pc * M, coef->mu + (size_t)(pc + 1) * M);
+    q.amp = coef->amp[pc];
+    for (int d = 0; d < 3; ++d) {
+      q.kind[d] = coef->factor_kind[pc * 3 + d];
+      q.k[d] = coef->factor_k[pc * 3 + d];
+    }
+    if (coef->cell_scale && coef->cell_scale[pc])
+      q.scale.assign(coef->cell_scale[pc], coef->cell_scale[pc] + n_cells);
+  }
+  return build_host_problem_pieces(mesh, k, r, n_slabs, T, M, p, pieces, hp, msg);
+}
+
+sg_status build_host_problem_pieces(const sg_mesh* mesh, int k, int r, int n_slabs, double T,
+                                    int M, int p, const std::vector<Piece>& pieces,
+                                    HostProblem& hp, std::string& msg) {
+  if (!mesh) { msg = "null mesh"; return SG_ERR_ARG; }
+  if (mesh->dim != 2 && mesh->dim != 3) { msg = "dim must be 2 or 3"; return SG_ERR_UNSUPPORTED; }
+  if (k < 1 || k > kMaxK || (mesh->dim == 3 && k > 2)) { msg = "fe_degree not built"; return SG_ERR_UNSUPPORTED; }
+  if (r < 0 || r + 1 > kMaxNT) { msg = "time_degree not built"; return SG_ERR_UNSUPPORTED; }
+  if (n_slabs < 1 || !(T > 0.0) || M < 1 || p < 0 || M > 16 || p > 12) { msg = "invalid slabs, T, M or order"; return SG_ERR_ARG; }
+  if (pieces.empty()) { msg = "coefficient needs at least one piece"; return SG_ERR_ARG; }
+  hp.pieces = pieces;
   hp.dim = mesh->dim; hp.k = k; hp.r = r; hp.M = M; hp.p = p; hp.n_slabs = n_slabs; hp.T = T;
   hp.tau = T / n_slabs;
   hp.n_x = 1; hp.n_cells = 1;
@@ -220,19 +244,26 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
   if ((long long)hp.n_xi * hp.n_t * hp.n_x > (1LL << 40)) { msg = "problem too large"; return SG_ERR_ARG; }
   // active coefficient terms (first appearance order)
   hp.mus.clear();
-  std::vector<int> piece_term(coef->n_pieces);
-  for (int pc = 0; pc < coef->n_pieces; ++pc) {
-    std::vector<int> mu(coef->mu + (size_t)pc * M, coef->mu + (size_t)(pc + 1) * M);
+  const int n_pieces = (int)pieces.size();
+  std::vector<int> piece_term(n_pieces);
+  for (int pc = 0; pc < n_pieces; ++pc) {
+    const std::vector<int>& mu = pieces[pc].mu;
+    if ((int)mu.size() != M) { msg = "coefficient index of wrong length"; return SG_ERR_ARG; }
     for (int v : mu) if (v < 0) { msg = "negative chaos index in coefficient"; return SG_ERR_ARG; }
     auto it = std::find(hp.mus.begin(), hp.mus.end(), mu);
     if (it == hp.mus.end()) { piece_term[pc] = (int)hp.mus.size(); hp.mus.push_back(mu); }
     else piece_term[pc] = (int)(it - hp.mus.begin());
     for (int d = 0; d < hp.dim; ++d) {
-      int kd = coef->factor_kind[pc * 3 + d];
+      int kd = pieces[pc].kind[d];
       if (kd != SG_F_ONE && kd != SG_F_SIN && kd != SG_F_POW) { msg = "unknown factor kind"; return SG_ERR_ARG; }
-      if (kd == SG_F_POW && coef->factor_k[pc * 3 + d] < 0) { msg = "negative power"; return SG_ERR_ARG; }
+      if (kd == SG_F_POW && pieces[pc].k[d] < 0) { msg = "negative power"; return SG_ERR_ARG; }
+    }
+    if (!pieces[pc].scale.empty() && (int64_t)pieces[pc].scale.size() != hp.n_cells) {
+      msg = "cell scale of wrong length";
+      return SG_ERR_ARG;
     }
   }
+  hp.piece_term = piece_term;
   hp.n_terms = (int)hp.mus.size();
   // stochastic coupling table, row by row
   hp.g.row.assign(hp.n_xi + 1, 0);
@@ -272,10 +303,12 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
   hp.wq = g.w;
   hp.S.assign(nq * nq, 0.0);
   hp.Dhat.assign(nq * nq, 0.0);
+  hp.dS.assign(nq * nq, 0.0);
   for (int q = 0; q < nq; ++q)
     for (int n = 0; n < nq; ++n) {
       hp.S[q * nq + n] = lagrange(gll, n, g.x[q]);
       hp.Dhat[q * nq + n] = lagrange_deriv(g.x, n, g.x[q]);
+      hp.dS[q * nq + n] = lagrange_deriv(gll, n, g.x[q]);
     }
   // coefficient values at the tensor Gauss points of every cell, times w_q |J|
   const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
@@ -297,11 +330,10 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
         xq[d] = hp.lo[d] + (cc[d] + g.x[qi[d]]) * hp.h[d];
         w *= g.w[qi[d]];
       }
-      for (int pc = 0; pc < coef->n_pieces; ++pc) {
-        double v = coef->amp[pc];
-        for (int d = 0; d < hp.dim; ++d)
-          v *= factor_value(coef->factor_kind[pc * 3 + d], coef->factor_k[pc * 3 + d], xq[d]);
-        if (coef->cell_scale && coef->cell_scale[pc]) v *= coef->cell_scale[pc][c];
+      for (int pc = 0; pc < n_pieces; ++pc) {
+        double v = pieces[pc].amp;
+        for (int d = 0; d < hp.dim; ++d) v *= factor_value(pieces[pc].kind[d], pieces[pc].k[d], xq[d]);
+        if (!pieces[pc].scale.empty()) v *= pieces[pc].scale[c];
         hp.ctab[((size_t)c * hp.n_terms + piece_term[pc]) * nqd + qd] += w * v / (hp.h[0] * hp.h[0]);
       }
     }

@@ -220,6 +220,24 @@ sg_status sg_vcycle(sg_ctx* ctx, const double* r, double* z, sg_stream stream);
 sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, double rtol, int max_it,
                         int restart, sg_solve_stats* st, sg_stream stream);
 
+/* sg_apply_host_static - sg_apply_host for callers that cannot let a library
+ * allocate device memory when they call it: applications whose memory pool
+ * owns the whole device, code paths that must not stall or fail on an
+ * allocation after start-up, or phases in which cudaMalloc / cudaFree are not
+ * allowed.  The paper has no counterpart; this is a deployment variant of the
+ * host-buffer apply.  x and y are staged in a fixed 32 MiB array compiled into
+ * the library (reserved on every device that loads the library, held until the
+ * process exits): at most 2,097,152 unknowns, larger problems get SG_ERR_ARG.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make that first call before
+ * any stream capture.  The context's device must be current.  Every call uses
+ * the same array, which keeps the last call's contents (each call overwrites
+ * what it reads); calls that overlap on the GPU, from several threads or
+ * contexts, race on it.  Synchronous; runs on the legacy default stream. */
+sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
+                               int transpose);
+
 /* sg_get_info - sizes and launch shape of a context (host struct out). */
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);
 

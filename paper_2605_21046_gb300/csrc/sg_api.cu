@@ -71,6 +71,10 @@ void fill_params(const sg_ctx* c, const void* x, void* y, int transpose, sg::App
 
 }  // namespace
 
+namespace sg {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace sg
+
 extern "C" {
 
 const char* sg_status_string(sg_status s) {

@@ -180,6 +180,8 @@ cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream);
 }  // namespace sg
 
 namespace sg {
+// Records the message sg_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
                  cudaStream_t s, std::string& msg,
                  cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t));

@@ -223,6 +223,40 @@ def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_cloc
     return elapsed_ms, t_launch, clocks
 
 
+def measure_solve(sg, torch, spec, dev, reps=3, autotune=True):
+    """Time to a 1e-8 relative residual for one slab system, FGMRES(30) from a
+    zero initial guess, for three precision splits."""
+    from paper_2605_21046_gb300 import inputs
+    b = torch.from_numpy(inputs.random_rhs(spec)).to(dev)
+    out, ref = {}, None
+    for name, apply_prec, mg_prec in (("fp64", sg.SG_PREC_FP64, sg.SG_PREC_FP64),
+                                      ("fp32_mg", sg.SG_PREC_FP64, sg.SG_PREC_FP32),
+                                      ("fp32_mg_dw_apply", sg.SG_PREC_DW, sg.SG_PREC_FP32)):
+        ctx = sg.sg_setup_spec(spec, apply_prec)
+        if autotune:
+            sg.sg_autotune(ctx, reps=5)
+        sg.sg_mg_setup(ctx, mg_prec)
+        x = torch.zeros_like(b)
+        st = sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-8)          # warm-up, records the V-cycle graph
+        times = []
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-8)
+            torch.cuda.synchronize()
+            times.append(1e3 * (time.perf_counter() - t0))
+        if ref is None:
+            ref = x.clone()
+        err = float((x - ref).abs().max() / ref.abs().max())
+        out[name] = {"ms_per_slab": statistics.median(times), "iterations": st["iterations"],
+                     "rel_residual": st["rel_residual"], "max_rel_diff_vs_fp64_solution": err,
+                     "mg_setup_ms": st["mg_setup_ms"]}
+        ctx.destroy()
+    return {"metric": "time to 1e-8 relative residual per slab", "unit": "ms",
+            "solver": "FGMRES(30), block-Jacobi GMG V-cycle (Vanka, nu=2, omega=0.7)", "splits": out}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2605_21046_gb300 as sg
@@ -232,6 +266,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(dev)
     spec = workload()
     ctx = sg.sg_setup_spec(spec, sg.SG_PREC_FP64)
+    if not args.no_autotune:
+        sg.sg_autotune(ctx, reps=10)
     n = ctx.info["n_unknowns"]
     # rotating x/y pairs whose total exceeds L2, so no step reads another's cache
     vec_bytes = 8 * n
@@ -251,6 +287,8 @@ def run_ours(args, world, rank, local):
     dw = None
     if not args.no_dw:
         ctx_dw = sg.sg_setup_spec(spec, sg.SG_PREC_DW)
+        if not args.no_autotune:
+            sg.sg_autotune(ctx_dw, reps=10)
         e_dw, t_dw, _ = time_applies(sg, torch, ctx_dw, X, Y, args.steps, args.warmup, stream, world, False, local)
         sg.sg_apply(ctx_dw, 0, X[0], Y[0], False, stream)
         torch.cuda.synchronize()
@@ -259,8 +297,12 @@ def run_ours(args, world, rank, local):
         dw = {"value": v_dw, "unit": UNIT, "ms_per_step": e_dw / args.steps, "dtype": "f32x2 double-word",
               "speedup_vs_fp64": v_dw / value, "max_rel_diff_vs_fp64": err,
               "fp64_equivalent_tflops": FLOP_PER_UNKNOWN * n / t_dw / 1e12,
-              "gpu_launches": 2 * args.steps}
+              "gpu_launches": 2 * args.steps,
+              "launch": {"chunk_cells": ctx_dw.info["chunk"], "grid": ctx_dw.info["grid"],
+                         "threads": ctx_dw.info["threads"]}}
         ctx_dw.destroy()
+
+    solve = None if args.no_solve else measure_solve(sg, torch, spec, dev, autotune=not args.no_autotune)
 
     # end to end through the host-buffer entry point: pinned x in, y out
     xh = X[0].cpu().pin_memory()
@@ -304,6 +346,7 @@ def run_ours(args, world, rank, local):
                                  "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0)}},
             "cpu_baseline": cpu,
             "variants": {"dw": dw},
+            "solve": solve,
         }
         print(json.dumps(line), flush=True)
     ctx.destroy()
@@ -318,6 +361,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dw", action="store_true", help="skip the double-word variant")
+    ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_init()

@@ -238,6 +238,14 @@ sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, dou
 sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
                                int transpose);
 
+/* sg_autotune - time the apply kernel of this context over candidate launch
+ * shapes (cells per shared-memory chunk x threads per CTA) on the current
+ * device and keep the fastest for every later sg_apply / sg_solve_slab; each
+ * candidate runs 2 + reps applies on a synthetic vector.  Allocates and frees
+ * two temporary device vectors.  Synchronous.  Results are unchanged up to
+ * the order of the atomic additions. */
+sg_status sg_autotune(sg_ctx* ctx, int reps);
+
 /* sg_get_info - sizes and launch shape of a context (host struct out). */
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);
 

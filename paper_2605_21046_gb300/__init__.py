@@ -18,7 +18,7 @@ from . import _abi
 
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = _abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -217,6 +217,13 @@ def sg_solve_slab(ctx, slab, rhs, x, rtol=1e-8, max_it=500, restart=30, stream=N
     if check:
         _check(status, "sg_solve_slab")
     return out
+
+
+def sg_autotune(ctx, reps=10):
+    """Pick the fastest apply launch shape for this context (sg_autotune)."""
+    _check(_abi.load().sg_autotune(ctx.handle, int(reps)), "sg_autotune")
+    ctx.info = sg_get_info(ctx)
+    return ctx.info
 
 
 def sg_get_info(ctx):

@@ -13,7 +13,7 @@ SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = 0, 1, 2
 # every symbol include/sg.h declares
 EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
                    "sg_destroy", "sg_status_string", "sg_last_error", "sg_mg_setup", "sg_vcycle",
-                   "sg_solve_slab", "sg_apply_host_static"])
+                   "sg_solve_slab", "sg_apply_host_static", "sg_autotune"])
 
 
 class sg_mesh(C.Structure):
@@ -72,6 +72,8 @@ def load():
     lib.sg_solve_slab.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int,
                                   C.POINTER(sg_solve_stats), vp]
     lib.sg_solve_slab.restype = C.c_int
+    lib.sg_autotune.argtypes = [vp, C.c_int]
+    lib.sg_autotune.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     lib.sg_apply_host_static.restype = C.c_int
     lib.sg_destroy.argtypes = [vp]

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "sg_internal.h"
 
@@ -235,6 +236,75 @@ sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, dou
   sg_status s = sg::fgmres(ctx, rhs, x, rtol, max_it, restart, st, reinterpret_cast<cudaStream_t>(stream), msg,
                            &apply_device);
   if (s != SG_OK) return fail(s, "sg_solve_slab: " + msg);
+  return SG_OK;
+}
+
+__global__ void autotune_fill(double* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = (double)((i * 2654435761LL) % 2001) / 1000.0 - 1.0;
+}
+
+sg_status sg_autotune(sg_ctx* ctx, int reps) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_autotune: ctx is NULL");
+  if (reps < 1 || reps > 1000) return fail(SG_ERR_ARG, "sg_autotune: reps out of range");
+  const long long n = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
+  double *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&y, n * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(x);
+    return cuda_fail(e, "sg_autotune: workspace");
+  }
+  cudaStream_t s = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) {
+    autotune_fill<<<256, 256, 0, s>>>(x, n);
+    e = cudaGetLastError();
+  }
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const sg::LaunchShape orig = ctx->ls;
+  sg::LaunchShape best = ctx->ls;
+  float best_ms = 1e30f;
+  const int max1 = sg::max_apply_chunk(ctx->hp, (size_t)optin - 1024);
+  std::vector<int> chunks;
+  for (int c = max1; c >= 1; c = c > 1 ? (c + 1) / 2 - (c == 2) : 0) chunks.push_back(c);
+  const int thread_opts[] = {128, 256, 384, 512};
+  for (int c : chunks) {
+    if (e != cudaSuccess) break;
+    for (int t : thread_opts) {
+      if (t < ctx->hp.n_xi) continue;
+      sg::LaunchShape ls;
+      std::string msg;
+      if (sg::plan_apply_shape(ctx->hp, c, t, ls, msg) != SG_OK) continue;
+      ctx->ls = ls;
+      sg::ApplyParams p;
+      fill_params(ctx, x, y, 0, p);
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = sg::launch_apply(ctx->hp, ls, p, s);
+      if (e == cudaSuccess) e = cudaEventRecord(a, s);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = sg::launch_apply(ctx->hp, ls, p, s);
+      if (e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ls;
+      }
+    }
+  }
+  ctx->ls = e == cudaSuccess ? best : orig;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(x);
+  cudaFree(y);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_autotune");
   return SG_OK;
 }
 

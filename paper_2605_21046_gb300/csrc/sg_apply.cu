@@ -51,9 +51,10 @@ void* select_kernel_f64(int dim, int k, int n_t);
 void* select_kernel_dw(int dim, int k, int n_t);
 void* select_kernel_f32(int dim, int k, int n_t);
 
-// y = (x on Dirichlet nodes, 0 elsewhere).
+// y = (x on Dirichlet nodes, 0 elsewhere), or in residual mode
+// y = b - (x on Dirichlet nodes, 0 elsewhere).
 template <typename IO>
-__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* __restrict__ y,
+__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* __restrict__ y, const IO* __restrict__ b,
                                  long long n_total, long long n_x, int nnx, int nny, int nnz,
                                  int dim) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
@@ -64,7 +65,8 @@ __global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* __restrict__ y,
     int iz = (int)(m / ((long long)nnx * nny));
     bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    y[idx] = bd ? x[idx] : IO(0);
+    const IO v = bd ? x[idx] : IO(0);
+    y[idx] = b ? b[idx] - v : v;
   }
 }
 
@@ -113,7 +115,20 @@ cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t 
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
-sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
+int max_apply_chunk(const HostProblem& hp, size_t budget) {
+  const int nnz = (int)hp.g.col.size();
+  const int vb = hp.precision == kPrecF32 ? 4 : 8;
+  int chunk = 0;
+  for (int c = 1; c <= 64; ++c) {
+    if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c, vb) > budget) break;
+    chunk = c;
+  }
+  return chunk;
+}
+
+// Launch shape for a given chunk and thread count (0 = defaults).  Phase 2
+// runs whole (cell, point) groups of n_xi threads, so threads >= n_xi.
+sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, LaunchShape& ls, std::string& msg) {
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) {
     msg = "no apply kernel built for this (dim, degree, time nodes)";
@@ -138,40 +153,42 @@ sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
   const int nnz = (int)hp.g.col.size();
   const int vb = hp.precision == kPrecF32 ? 4 : 8;
   const long long cells_per_sm = (hp.n_cells + n_sm - 1) / n_sm;
-  // Largest chunk that lets two CTAs share an SM; one CTA per SM otherwise.
-  const size_t budget2 = (size_t)smem_optin / 2 - 1024;
-  const size_t budget1 = (size_t)smem_optin - 1024;
-  int chunk = 0;
-  for (int c = 1; c <= 64; ++c) {
-    if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c, vb) > budget2) break;
-    chunk = c;
-  }
-  if (chunk == 0) {
-    for (int c = 1; c <= 64; ++c) {
-      if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c, vb) > budget1) break;
-      chunk = c;
-    }
-  }
-  if (chunk == 0) {
+  const int max1 = max_apply_chunk(hp, (size_t)smem_optin - 1024);
+  if (max1 == 0) {
     msg = "one cell with all chaos modes does not fit in shared memory";
     return SG_ERR_UNSUPPORTED;
   }
-  chunk = (int)std::min<long long>(chunk, std::max<long long>(1, (cells_per_sm + 1) / 2));
+  if (chunk <= 0) {
+    // default: the largest chunk that lets two CTAs share an SM
+    chunk = max_apply_chunk(hp, (size_t)smem_optin / 2 - 1024);
+    if (chunk == 0) chunk = max1;
+    chunk = (int)std::min<long long>(chunk, std::max<long long>(1, (cells_per_sm + 1) / 2));
+  }
+  if (chunk > max1) { msg = "chunk does not fit in shared memory"; return SG_ERR_ARG; }
+  if (threads <= 0) {
+    const int groups = std::max(1, 256 / hp.n_xi);
+    threads = ((groups * hp.n_xi + 31) / 32) * 32;
+  }
+  if (threads < hp.n_xi || threads > 512 || threads % 32) { msg = "invalid thread count"; return SG_ERR_ARG; }
   ls.chunk = chunk;
+  ls.threads = threads;
   ls.smem = apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, chunk, vb);
-  // threads: phase 2 runs whole (cell, point) groups of n_xi threads
-  int groups = std::max(1, 256 / hp.n_xi);
-  int thr = ((groups * hp.n_xi + 31) / 32) * 32;
-  if (thr < 128) thr = std::min(512, ((128 / hp.n_xi) * hp.n_xi + 31) / 32 * 32);
-  ls.threads = std::min(thr, 512);
   cudaError_t e = prepare_apply_kernel(hp.precision, hp.dim, hp.k, hp.n_t, ls.smem);
-  int per_sm = 1;
+  int per_sm = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, ls.threads, ls.smem);
-  if (e != cudaSuccess || per_sm < 1) { cudaGetLastError(); per_sm = 1; }
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    msg = "launch shape does not fit on an SM";
+    return SG_ERR_ARG;
+  }
   long long grid = (long long)n_sm * per_sm;
   grid = std::min<long long>(grid, hp.n_cells);
   ls.grid = (int)std::max<long long>(1, grid);
   return SG_OK;
+}
+
+sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg) {
+  return plan_apply_shape(hp, 0, 0, ls, msg);
 }
 
 void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void* ctab,
@@ -227,10 +244,10 @@ cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const App
   long long ig = std::min<long long>((n_total + ib - 1) / ib, 152LL * 16);
   if (hp.precision == kPrecF32)
     sg_init_y_kernel<float><<<(int)ig, ib, 0, stream>>>(static_cast<const float*>(prm.x), static_cast<float*>(prm.y),
-                                                        n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+                                                        static_cast<const float*>(prm.b), n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
   else
     sg_init_y_kernel<double><<<(int)ig, ib, 0, stream>>>(static_cast<const double*>(prm.x), static_cast<double*>(prm.y),
-                                                         n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+                                                         static_cast<const double*>(prm.b), n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<ApplyParams*>(&prm)};

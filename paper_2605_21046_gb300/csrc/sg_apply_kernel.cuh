@@ -344,9 +344,11 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
       const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
-      if (interior)
-        A::add_out(yout + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx,
-                   A::mul(Tb[v % NT], Qs[(size_t)cv * SLOT + a]));
+      if (interior) {
+        T val = A::mul(Tb[v % NT], Qs[(size_t)cv * SLOT + a]);
+        if (p.b) val = A::neg(val);
+        A::add_out(yout + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx, val);
+      }
     }
   }
 }

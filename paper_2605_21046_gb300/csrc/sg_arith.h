@@ -40,6 +40,7 @@ struct F64 {
   __device__ __forceinline__ static T mul(T a, T b) { return a * b; }
   __device__ __forceinline__ static void fma(T a, T b, T& acc) { acc = ::fma(a, b, acc); }
   __device__ __forceinline__ static T add(T a, T b) { return a + b; }
+  __device__ __forceinline__ static T neg(T a) { return -a; }
   __device__ __forceinline__ static T fin(T a) { return a; }
   __device__ __forceinline__ static void add_out(double* y, T v) { atomicAdd(y, v); }
 };
@@ -136,6 +137,7 @@ struct DW {
     acc_add(s, b.h, b.l);
     return s;
   }
+  __device__ __forceinline__ static T neg(T a) { return {-a.h, -a.l}; }
   __device__ __forceinline__ static T fin(T a) {
     float s, e;
     two_sum(a.h, a.l, s, e);
@@ -161,6 +163,7 @@ struct F32 {
   __device__ __forceinline__ static T mul(T a, T b) { return a * b; }
   __device__ __forceinline__ static void fma(T a, T b, T& acc) { acc = fmaf(a, b, acc); }
   __device__ __forceinline__ static T add(T a, T b) { return a + b; }
+  __device__ __forceinline__ static T neg(T a) { return -a; }
   __device__ __forceinline__ static T fin(T a) { return a; }
   __device__ __forceinline__ static void add_out(float* y, T v) { atomicAdd(y, v); }
 };

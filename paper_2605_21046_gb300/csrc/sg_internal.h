@@ -101,6 +101,7 @@ struct ApplyParams {
   double ratio[3];        // (h_0 / h_d)^2
   double amq[kMaxAmq];    // [q][i][j] w_q |J| A_t[i][j] / (tau Bhat_ii) (A_t^T for the transpose)
   double tb[kMaxNT];      // tau Bhat_ii
+  const void* b;          // residual mode: y = b - A x (nullptr: y = A x)
 };
 
 struct LaunchShape {
@@ -110,8 +111,12 @@ struct LaunchShape {
   int grid;               // persistent CTAs
 };
 
-// Chooses a tile shape and thread count for the apply kernel of a problem.
+// Chooses a chunk size and thread count for the apply kernel of a problem.
 sg_status plan_apply(const HostProblem& hp, LaunchShape& ls, std::string& msg);
+// The same for a given chunk / thread count (0 = default); used by the autotuner.
+sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, LaunchShape& ls, std::string& msg);
+// Largest chunk whose shared memory fits the budget.
+int max_apply_chunk(const HostProblem& hp, size_t budget);
 // Size of the dynamic shared memory the apply kernel needs for a chunk of cells
 // (value_bytes = 8 for FP64 / DW, 4 for FP32).
 size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk,

@@ -50,12 +50,6 @@ __global__ void mg_init_x(const T* __restrict__ b, T* __restrict__ x, long long 
   }
 }
 
-template <typename T>
-__global__ void mg_sub(const T* __restrict__ b, T* __restrict__ r, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    r[i] = b[i] - r[i];
-}
-
 template <typename S, typename D>
 __global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -531,16 +525,30 @@ std::vector<double> coarsen_scale(const std::vector<double>& s, const HostProble
 template <typename T>
 cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s);
 
+// r = b - A x in one apply (residual mode: the init kernel writes b minus the
+// Dirichlet rows, the cell kernel subtracts).
 template <typename T>
 cudaError_t residual(MG& mg, int l, cudaStream_t s) {
   MGLevel& L = mg.lv[l];
   ApplyParams p;
   fill_apply_params(L.hp, L.ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, 0, p);
-  cudaError_t e = launch_apply(L.hp, L.ls, p, s);
-  if (e != cudaSuccess) return e;
-  const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
-  mg_sub<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_r), n);
-  return cudaGetLastError();
+  p.b = L.d_b;
+  return launch_apply(L.hp, L.ls, p, s);
+}
+
+// r = b on interior dofs, 0 on Dirichlet dofs: the residual of the initial
+// iterate (x = 0 inside, x = b on the boundary), without an apply.
+template <typename T>
+__global__ void mg_first_residual(const T* __restrict__ b, T* __restrict__ r, long long n_total, long long n_x,
+                                  int nnx, int nny, int nnz, int dim) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long m = idx % n_x;
+    const int ix = (int)(m % nnx), iy = (int)((m / nnx) % nny), iz = (int)(m / ((long long)nnx * nny));
+    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
+    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
+    r[idx] = bd ? T(0) : b[idx];
+  }
 }
 
 template <typename T, int DIM, int K, int NT>
@@ -618,7 +626,12 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
   }
   cudaError_t e;
   for (int it = 0; it < mg.nu; ++it) {
-    if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
+    if (it == 0) {
+      mg_first_residual<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_r), n,
+                                                            L.hp.n_x, L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
+    } else if ((e = residual<T>(mg, l, s)) != cudaSuccess) {
+      return e;
+    }
     if (!vanka<T>(mg, L, s)) return cudaErrorInvalidValue;
   }
   if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;

@@ -95,3 +95,21 @@ def n_unknowns(spec):
 def random_vector(spec, seed=SEED_X):
     """x ~ U(-1, 1), float64, flat slab vector (boundary entries included)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, n_unknowns(spec))
+
+
+def boundary_mask(spec):
+    """True at the nodes on the domain boundary (lexicographic, x fastest)."""
+    nn = [spec["k"] * spec["cells"][d] + 1 for d in range(spec["dim"])]
+    grids = np.meshgrid(*[np.arange(n) for n in reversed(nn)], indexing="ij")
+    mask = np.zeros(tuple(reversed(nn)), dtype=bool)
+    for d in range(spec["dim"]):
+        g = grids[spec["dim"] - 1 - d]
+        mask |= (g == 0) | (g == nn[d] - 1)
+    return mask.reshape(-1)
+
+
+def random_rhs(spec, seed=SEED_X + 1):
+    """A right-hand side ~ U(-1, 1) that vanishes on Dirichlet nodes."""
+    b = random_vector(spec, seed).reshape(n_modes(spec), spec["r"] + 1, n_nodes(spec))
+    b[:, :, boundary_mask(spec)] = 0.0
+    return b.reshape(-1)

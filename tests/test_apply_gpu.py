@@ -198,3 +198,17 @@ def test_dw_nonfinite_propagates(cuda):
     x[40] = np.nan
     y = gpu_apply(cuda, spec, x, precision=sg.SG_PREC_DW)
     assert np.isnan(y).any()
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+def test_autotune_keeps_parity(cuda, prec):
+    spec = I.config_2d_q2_64()
+    ctx = sg.sg_setup_spec(spec, PRECISIONS[prec])
+    before = dict(ctx.info)
+    info = sg.sg_autotune(ctx, reps=3)
+    assert info["threads"] >= spec["M"] and info["chunk"] >= 1 and info["grid"] >= 1
+    x = I.random_vector(spec, seed=31)
+    got = gpu_apply(cuda, spec, x, ctx=ctx)
+    want = operator.SGProblem(spec).apply(x).reshape(-1)
+    ctx.destroy()
+    assert _rel(got, want) < TOL, (before, info)

@@ -249,3 +249,27 @@ def fgmres(problem, b, precond, x0=None, rtol=1e-8, restart=30, max_it=500):
         y, *_ = np.linalg.lstsq(H[: j_done + 1, :j_done], g[: j_done + 1], rcond=None)
         for i in range(j_done):
             x = x + y[i] * Z[i]
+
+
+class BlockJacobiLU:
+    """Exact block-Jacobi preconditioner: the diagonal block A_alpha of every
+    chaos mode (Sec. 3.5 remark) inverted by a sparse LU, one factorisation per
+    diagonal class."""
+
+    def __init__(self, problem):
+        self.p = problem
+        self.keys, self.cls = diagonal_classes(problem.G)
+        Md, Kd = problem.dirichlet_factors()
+        bd = sp.diags(np.tile(problem.bmask.astype(np.float64), problem.n_t))
+        self.lu = []
+        for key in self.keys:
+            Kbar = sum(float(g) * K for g, K in zip(key, Kd))
+            A = (sp.kron(problem.At, Md) + sp.kron(problem.Bt, Kbar) + bd).tocsc()
+            self.lu.append(spla.splu(A))
+
+    def apply(self, r):
+        r = np.asarray(r, dtype=np.float64).reshape(self.p.shape)
+        z = np.zeros_like(r)
+        for a in range(r.shape[0]):
+            z[a] = self.lu[self.cls[a]].solve(r[a].reshape(-1)).reshape(r.shape[1:])
+        return z

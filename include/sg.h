@@ -246,6 +246,46 @@ sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, doub
  * the order of the atomic additions. */
 sg_status sg_autotune(sg_ctx* ctx, int reps);
 
+/* sg_set_exact - attach a manufactured finite-chaos solution (Sec. 4.3,
+ * eqs. finite-exact-separated .. finite-chaos-coefficients)
+ *     u(x, t, xi) = T(t) sum_{alpha in Lambda_q} c_alpha Phi_alpha(x) Psi_alpha(xi),
+ *     Phi_alpha(x) = prod_d sin(pi freq[alpha][d] (x_d - lo_d) / (hi_d - lo_d)),
+ *     T(t) = sum_{j <= t_degree} t_coef[j] t^j,
+ * (zero on the boundary of the box) and precompute the slab-independent parts
+ * of its load vector (eq. load_vector with f = d_t u - div(a grad u), eq.
+ * manufactured_rhs_benchmark).  q may differ from the context's chaos order:
+ * modes outside Lambda_p enter through the coupling G_mu[beta][alpha].
+ *   c       N_xi(q) coefficients in the order of Lambda_q (graded, as
+ *           sg_get_multi_indices orders Lambda_p)          (host)
+ *   freq    N_xi(q) x 3 integer frequencies (entries beyond dim ignored) (host)
+ * Integrals use (k+4)^d Gauss points per cell.  Synchronous; allocates two
+ * slab-mode arrays on the device (kept by the context). */
+sg_status sg_set_exact(sg_ctx* ctx, int q, const double* c, const int* freq, int t_degree,
+                       const double* t_coef);
+
+/* sg_rhs - right-hand side of slab n (eq. local_tensor_system):
+ *   rhs = F^(n) + J u_prev  with J = I (x) C_t (x) M_x (eq. local_rhs_tensor),
+ *   rhs = F^(1) + B_0^(1)   on the first slab (eq. initial_vector, with the L2
+ *                           projection of u(0); u_prev ignored, may be NULL).
+ * u_prev: DEVICE solution of the previous slab (layout above); rhs: DEVICE
+ * output; Dirichlet entries are 0.  Needs sg_set_exact.  Stream ordered. */
+sg_status sg_rhs(sg_ctx* ctx, int slab, const double* u_prev, double* rhs, sg_stream stream);
+
+/* sg_moments - pointwise mean and variance of a slab solution at one time
+ * node (eqs. qoi-mean-chaos and qoi-variance-chaos): mean[m] = u[0, i, m],
+ * var[m] = sum_{alpha != 0} u[alpha, i, m]^2.  u, mean, var: DEVICE (mean or
+ * var may be NULL; n_x doubles each).  Stream ordered. */
+sg_status sg_moments(sg_ctx* ctx, const double* u, int time_node, double* mean, double* var,
+                     sg_stream stream);
+
+/* sg_qoi_errors - L2(D) errors at the end time t_n of slab n of the mean, the
+ * variance and the full stochastic solution against the manufactured solution
+ * (Definition "error norms and quantities" at one time; the full error by the
+ * modal identity eq. modal-sum-L2, truncated modes included).  u: DEVICE slab
+ * solution; err: HOST array of 3 doubles (mean, variance, full).  Needs
+ * sg_set_exact.  Synchronous (evaluated on the host, post-processing). */
+sg_status sg_qoi_errors(sg_ctx* ctx, const double* u, int slab, double* err);
+
 /* sg_get_info - sizes and launch shape of a context (host struct out). */
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);
 

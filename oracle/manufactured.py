@@ -271,6 +271,34 @@ class Manufactured:
         return {"full": np.sqrt(full), "mean": np.sqrt(mean), "var": np.sqrt(var)}
 
 
+def errors_at_end(man, U, n):
+    """L2(D) errors of the mean, variance and full solution at the end time
+    t_n of slab n (time node r), the same definitions at one time."""
+    p, ex = man.p, man.ex
+    sp = man._spatial_parts()
+    pos = {tuple(a): i for i, a in enumerate(ex.idx_q)}
+    r = p.n_t - 1
+    uq = np.einsum('acl,lq->acq', U[:, r][:, man.conn], man.phi)          # (N_xi, C, Q)
+    Tt = ex.T((n + 1) * p.tau)
+    idx_p = {tuple(a) for a in p.idx}
+    full = np.zeros(uq.shape[1:])
+    for b in range(p.n_xi):
+        jb = pos.get(tuple(p.idx[b]))
+        full += (uq[b] - (Tt * ex.c[jb] * sp[jb][0] if jb is not None else 0.0)) ** 2
+    for j in range(ex.idx_q.shape[0]):
+        if tuple(ex.idx_q[j]) not in idx_p:
+            full += (Tt * ex.c[j] * sp[j][0]) ** 2
+    i0 = [b for b in range(p.n_xi) if not any(p.idx[b])][0]
+    j0 = [j for j in range(ex.idx_q.shape[0]) if not any(ex.idx_q[j])]
+    mean_ex = Tt * ex.c[j0[0]] * sp[j0[0]][0] if j0 else 0.0
+    var_h = (uq ** 2).sum(axis=0) - uq[i0] ** 2
+    var_ex = sum((Tt * ex.c[j] * sp[j][0]) ** 2 for j in range(ex.idx_q.shape[0]) if any(ex.idx_q[j]))
+    w = man.wJ
+    return {"mean": float(np.sqrt(np.einsum('cq,q->', (uq[i0] - mean_ex) ** 2, w))),
+            "var": float(np.sqrt(np.einsum('cq,q->', (var_h - var_ex) ** 2, w))),
+            "full": float(np.sqrt(np.einsum('cq,q->', full, w)))}
+
+
 def paper_exact(M=4, q=6, eta=0.35):
     """The paper's finite-chaos solution (eqs. finite-exact-separated ..
     finite-chaos-coefficients): u = t^4 sin(pi/2 (x1+1)) sin(pi/2 (x2+1)) G_q(xi),

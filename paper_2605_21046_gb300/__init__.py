@@ -18,7 +18,7 @@ from . import _abi
 
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = _abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -217,6 +217,49 @@ def sg_solve_slab(ctx, slab, rhs, x, rtol=1e-8, max_it=500, restart=30, stream=N
     if check:
         _check(status, "sg_solve_slab")
     return out
+
+
+def sg_set_exact(ctx, exact):
+    """Attach a manufactured solution {"q", "c", "freq" (per mode, per
+    direction), "T" (polynomial coefficients)} (sg_set_exact)."""
+    c = np.ascontiguousarray(exact["c"], dtype=np.float64)
+    freq = np.zeros((c.size, 3), dtype=np.int32)
+    for a, f in enumerate(exact["freq"]):
+        freq[a, :len(f)] = f
+    tc = np.ascontiguousarray(exact["T"], dtype=np.float64)
+    _check(_abi.load().sg_set_exact(ctx.handle, int(exact["q"]), c.ctypes.data_as(C.POINTER(C.c_double)),
+                                    freq.ctypes.data_as(C.POINTER(C.c_int)), tc.size - 1,
+                                    tc.ctypes.data_as(C.POINTER(C.c_double))), "sg_set_exact")
+
+
+def sg_rhs(ctx, slab, u_prev, rhs, stream=None):
+    """rhs = F^(n) + J u_prev (first slab: F^(1) + B_0) on ``stream``."""
+    _check_vec(ctx, rhs)
+    if u_prev is not None:
+        _check_vec(ctx, u_prev)
+    _check(_abi.load().sg_rhs(ctx.handle, int(slab), C.c_void_p(u_prev.data_ptr() if u_prev is not None else None),
+                              C.c_void_p(rhs.data_ptr()), C.c_void_p(_stream_handle(stream))), "sg_rhs")
+    return rhs
+
+
+def sg_moments(ctx, u, time_node, mean=None, var=None, stream=None):
+    """Pointwise mean and variance at one time node (device tensors of n_x)."""
+    import torch
+    _check_vec(ctx, u)
+    n_x = ctx.info["n_x"]
+    mean = torch.empty(n_x, dtype=torch.float64, device=u.device) if mean is None else mean
+    var = torch.empty(n_x, dtype=torch.float64, device=u.device) if var is None else var
+    _check(_abi.load().sg_moments(ctx.handle, C.c_void_p(u.data_ptr()), int(time_node), C.c_void_p(mean.data_ptr()),
+                                  C.c_void_p(var.data_ptr()), C.c_void_p(_stream_handle(stream))), "sg_moments")
+    return mean, var
+
+
+def sg_qoi_errors(ctx, u, slab):
+    """(mean, variance, full) L2 errors at the end of slab ``slab``."""
+    _check_vec(ctx, u)
+    err = (C.c_double * 3)()
+    _check(_abi.load().sg_qoi_errors(ctx.handle, C.c_void_p(u.data_ptr()), int(slab), err), "sg_qoi_errors")
+    return {"mean": err[0], "var": err[1], "full": err[2]}
 
 
 def sg_autotune(ctx, reps=10):

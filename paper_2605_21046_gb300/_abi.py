@@ -13,7 +13,8 @@ SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = 0, 1, 2
 # every symbol include/sg.h declares
 EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
                    "sg_destroy", "sg_status_string", "sg_last_error", "sg_mg_setup", "sg_vcycle",
-                   "sg_solve_slab", "sg_apply_host_static", "sg_autotune"])
+                   "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
+                   "sg_rhs", "sg_moments", "sg_qoi_errors"])
 
 
 class sg_mesh(C.Structure):
@@ -72,6 +73,15 @@ def load():
     lib.sg_solve_slab.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int,
                                   C.POINTER(sg_solve_stats), vp]
     lib.sg_solve_slab.restype = C.c_int
+    lib.sg_set_exact.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int,
+                                 C.POINTER(C.c_double)]
+    lib.sg_set_exact.restype = C.c_int
+    lib.sg_rhs.argtypes = [vp, C.c_int, vp, vp, vp]
+    lib.sg_rhs.restype = C.c_int
+    lib.sg_moments.argtypes = [vp, vp, C.c_int, vp, vp, vp]
+    lib.sg_moments.restype = C.c_int
+    lib.sg_qoi_errors.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double)]
+    lib.sg_qoi_errors.restype = C.c_int
     lib.sg_autotune.argtypes = [vp, C.c_int]
     lib.sg_autotune.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]

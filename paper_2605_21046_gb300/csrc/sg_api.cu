@@ -48,6 +48,8 @@ void free_ctx_device(sg_ctx* c) {
     delete c->mg;
     c->mg = nullptr;
   }
+  sg::exact_free(c->exact);
+  c->exact = nullptr;
 }
 
 cudaError_t apply_device(sg_ctx* c, const double* x, double* y, cudaStream_t s) {
@@ -305,6 +307,58 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
   cudaFree(x);
   cudaFree(y);
   if (e != cudaSuccess) return cuda_fail(e, "sg_autotune");
+  return SG_OK;
+}
+
+sg_status sg_set_exact(sg_ctx* ctx, int q, const double* c, const int* freq, int t_degree, const double* t_coef) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_set_exact: ctx is NULL");
+  std::string msg;
+  sg::ExactData* e = nullptr;
+  sg_status st = sg::exact_build(ctx->hp, q, c, freq, t_degree, t_coef, e, msg);
+  if (st != SG_OK) return fail(st, "sg_set_exact: " + msg);
+  sg::exact_free(ctx->exact);
+  ctx->exact = e;
+  return SG_OK;
+}
+
+sg_status sg_rhs(sg_ctx* ctx, int slab, const double* u_prev, double* rhs, sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_rhs: ctx is NULL");
+  if (!ctx->exact) return fail(SG_ERR_ARG, "sg_rhs: call sg_set_exact first");
+  if (slab < 0 || slab >= ctx->hp.n_slabs) return fail(SG_ERR_ARG, "sg_rhs: slab out of range");
+  if (!rhs || !is_device_ptr(rhs)) return fail(SG_ERR_ARG, "sg_rhs: rhs must be device memory");
+  const long long n = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
+  if (u_prev) {
+    if (!is_device_ptr(u_prev)) return fail(SG_ERR_ARG, "sg_rhs: u_prev must be device memory");
+    if (u_prev < rhs + n && rhs < u_prev + n) return fail(SG_ERR_ARG, "sg_rhs: u_prev and rhs overlap");
+  } else if (slab > 0) {
+    return fail(SG_ERR_ARG, "sg_rhs: u_prev is required after the first slab");
+  }
+  cudaError_t e = sg::exact_rhs(ctx->hp, ctx->ls, *ctx->exact, ctx->d_ctab, ctx->d_gcol, ctx->d_gterm, ctx->d_gval,
+                                ctx->d_perm, slab, u_prev, rhs, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "sg_rhs");
+  return SG_OK;
+}
+
+sg_status sg_moments(sg_ctx* ctx, const double* u, int time_node, double* mean, double* var, sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_moments: ctx is NULL");
+  if (!u || !is_device_ptr(u)) return fail(SG_ERR_ARG, "sg_moments: u must be device memory");
+  if (time_node < 0 || time_node >= ctx->hp.n_t) return fail(SG_ERR_ARG, "sg_moments: time node out of range");
+  if ((mean && !is_device_ptr(mean)) || (var && !is_device_ptr(var)))
+    return fail(SG_ERR_ARG, "sg_moments: outputs must be device memory");
+  cudaError_t e = sg::moments(ctx->hp, u, time_node, mean, var, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "sg_moments");
+  return SG_OK;
+}
+
+sg_status sg_qoi_errors(sg_ctx* ctx, const double* u, int slab, double* err) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_qoi_errors: ctx is NULL");
+  if (!ctx->exact) return fail(SG_ERR_ARG, "sg_qoi_errors: call sg_set_exact first");
+  if (!u || !is_device_ptr(u) || !err) return fail(SG_ERR_ARG, "sg_qoi_errors: bad pointer");
+  if (slab < 0 || slab >= ctx->hp.n_slabs) return fail(SG_ERR_ARG, "sg_qoi_errors: slab out of range");
+  cudaDeviceSynchronize();
+  std::string msg;
+  sg_status st = sg::exact_errors(ctx->hp, *ctx->exact, u, slab, err, msg);
+  if (st != SG_OK) return fail(st, "sg_qoi_errors: " + msg);
   return SG_OK;
 }
 

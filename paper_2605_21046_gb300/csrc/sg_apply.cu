@@ -51,10 +51,11 @@ void* select_kernel_f64(int dim, int k, int n_t);
 void* select_kernel_dw(int dim, int k, int n_t);
 void* select_kernel_f32(int dim, int k, int n_t);
 
-// y = (x on Dirichlet nodes, 0 elsewhere), or in residual mode
-// y = b - (x on Dirichlet nodes, 0 elsewhere).
+// Starting value of y before the cell kernel adds: (x on Dirichlet nodes, 0
+// elsewhere) for a plain apply, b minus that for a residual, b for an
+// accumulation (y == b allowed there).
 template <typename IO>
-__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* __restrict__ y, const IO* __restrict__ b,
+__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* y, const IO* b, int mode,
                                  long long n_total, long long n_x, int nnx, int nny, int nnz,
                                  int dim) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
@@ -65,8 +66,12 @@ __global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* __restrict__ y, c
     int iz = (int)(m / ((long long)nnx * nny));
     bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    const IO v = bd ? x[idx] : IO(0);
-    y[idx] = b ? b[idx] - v : v;
+    if (mode == kApplyAccumulate) {
+      y[idx] = b[idx];
+    } else {
+      const IO v = bd ? x[idx] : IO(0);
+      y[idx] = mode == kApplyResidual ? b[idx] - v : v;
+    }
   }
 }
 
@@ -244,10 +249,10 @@ cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const App
   long long ig = std::min<long long>((n_total + ib - 1) / ib, 152LL * 16);
   if (hp.precision == kPrecF32)
     sg_init_y_kernel<float><<<(int)ig, ib, 0, stream>>>(static_cast<const float*>(prm.x), static_cast<float*>(prm.y),
-                                                        static_cast<const float*>(prm.b), n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+                                                        static_cast<const float*>(prm.b), prm.mode, n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
   else
     sg_init_y_kernel<double><<<(int)ig, ib, 0, stream>>>(static_cast<const double*>(prm.x), static_cast<double*>(prm.y),
-                                                         static_cast<const double*>(prm.b), n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+                                                         static_cast<const double*>(prm.b), prm.mode, n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<ApplyParams*>(&prm)};

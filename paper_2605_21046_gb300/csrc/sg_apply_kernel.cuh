@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
       if (interior) {
         T val = A::mul(Tb[v % NT], Qs[(size_t)cv * SLOT + a]);
-        if (p.b) val = A::neg(val);
+        if (p.mode == kApplyResidual) val = A::neg(val);
         A::add_out(yout + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx, val);
       }
     }

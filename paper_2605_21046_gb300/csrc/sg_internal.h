@@ -101,8 +101,11 @@ struct ApplyParams {
   double ratio[3];        // (h_0 / h_d)^2
   double amq[kMaxAmq];    // [q][i][j] w_q |J| A_t[i][j] / (tau Bhat_ii) (A_t^T for the transpose)
   double tb[kMaxNT];      // tau Bhat_ii
-  const void* b;          // residual mode: y = b - A x (nullptr: y = A x)
+  const void* b;          // right-hand side of the residual / accumulate modes
+  int mode;               // kApplyPlain: y = A x; kApplyResidual: y = b - A x;
+                          // kApplyAccumulate: y = b + A x without the Dirichlet identity rows
 };
+constexpr int kApplyPlain = 0, kApplyResidual = 1, kApplyAccumulate = 2;
 
 struct LaunchShape {
   int chunk;              // cells per chunk
@@ -185,6 +188,16 @@ cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream);
 }  // namespace sg
 
 namespace sg {
+struct ExactData;
+sg_status exact_build(const HostProblem& hp, int q, const double* c, const int* freq, int t_degree,
+                      const double* t_coef, ExactData*& out, std::string& msg);
+void exact_free(ExactData* e);
+cudaError_t exact_rhs(const HostProblem& hp, const LaunchShape& ls, ExactData& E, const void* ctab, const int* gcol,
+                      const int* gterm, const double* gval, const int* perm, int slab, const double* u_prev,
+                      double* rhs, cudaStream_t s);
+cudaError_t moments(const HostProblem& hp, const double* u, int node, double* mean, double* var, cudaStream_t s);
+sg_status exact_errors(const HostProblem& hp, const ExactData& E, const double* u_dev, int slab, double err[3],
+                       std::string& msg);
 // Records the message sg_last_error() returns on this thread.
 void set_last_error(const std::string& msg);
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
@@ -206,6 +219,7 @@ struct sg_ctx {
   double* d_ybuf = nullptr;
   cudaStream_t host_stream = nullptr;
   sg::MG* mg = nullptr;       // multigrid preconditioner (sg_mg_setup)
+  sg::ExactData* exact = nullptr;  // manufactured solution (sg_set_exact)
   double* d_krylov = nullptr; // FGMRES workspace (lazy): V, Z, w, r and partial sums
   size_t krylov_bytes = 0;
   int krylov_restart = 0;

@@ -533,6 +533,7 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s) {
   ApplyParams p;
   fill_apply_params(L.hp, L.ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, 0, p);
   p.b = L.d_b;
+  p.mode = kApplyResidual;
   return launch_apply(L.hp, L.ls, p, s);
 }
 

@@ -143,6 +143,16 @@ typedef struct {
   double mg_setup_ms;   /* wall time of the last sg_mg_setup                  */
 } sg_solve_stats;
 
+/* Statistics of one mc_solve_batch call (host struct out). */
+typedef struct {
+  int n_samples;
+  int batches;
+  int total_iterations;    /* FGMRES iterations over all batches and slabs   */
+  int max_slab_iterations; /* largest per-slab iteration count               */
+  double max_rel_residual; /* largest final relative residual of a slab      */
+  double solve_ms;         /* wall time of the call                          */
+} sg_mc_stats;
+
 /* sg_setup - discretise one problem and make it resident on the current
  * CUDA device (Sec. 3: Q_k in space, dG(r) in time, Lambda_p chaos; Sec. 3.5:
  * time matrices eqs. At/Bt/Ct, G_mu eq. triple_stoch and its factorisation
@@ -285,6 +295,29 @@ sg_status sg_moments(sg_ctx* ctx, const double* u, int time_node, double* mean, 
  * solution; err: HOST array of 3 doubles (mean, variance, full).  Needs
  * sg_set_exact.  Synchronous (evaluated on the host, post-processing). */
 sg_status sg_qoi_errors(sg_ctx* ctx, const double* u, int slab, double* err);
+
+/* mc_solve_batch - Monte-Carlo estimate of the mean and variance at t = T
+ * (Sec. 5: the pathwise problem and its slab system eq. mc-slab-system, the
+ * sample mean eq. mc-mean-estimator and the unbiased variance eq.
+ * mc-variance-estimator-unbiased; Algorithm 1).  For every sample xi_s the
+ * deterministic heat equation with a(x, xi_s) = sum_mu a_mu(x) Psi_mu(xi_s) and
+ * the manufactured forcing f(x, t, xi_s) of sg_set_exact is marched over all
+ * slabs of the context (same mesh, Q_k and dG(r)).  `batch` samples are solved
+ * together: one apply launch covers the whole batch, FGMRES(30) iterates on
+ * the batch to rtol with a mean-operator V-cycle as preconditioner.
+ *   xi        HOST n_samples x M standard-normal samples
+ *   batch     samples per batch, 1..512
+ *   mg_precision  SG_PREC_FP64 or SG_PREC_FP32 V-cycle
+ *   mean_T, var_T  DEVICE n_x doubles out: nodal sample mean and unbiased
+ *             sample variance of u(x, T)
+ *   u_T       DEVICE n_samples x N_t x n_x doubles out (last slab of every
+ *             sample), or NULL
+ *   st        statistics out (may be NULL)
+ * Needs sg_set_exact.  Allocates and frees per-batch device workspaces.
+ * Synchronous. */
+sg_status mc_solve_batch(sg_ctx* ctx, int n_samples, const double* xi, int batch, int mg_precision,
+                         double rtol, int max_it, double* mean_T, double* var_T, double* u_T,
+                         sg_mc_stats* st, sg_stream stream);
 
 /* sg_get_info - sizes and launch shape of a context (host struct out). */
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);

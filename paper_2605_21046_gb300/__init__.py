@@ -18,7 +18,7 @@ from . import _abi
 
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = _abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -260,6 +260,26 @@ def sg_qoi_errors(ctx, u, slab):
     err = (C.c_double * 3)()
     _check(_abi.load().sg_qoi_errors(ctx.handle, C.c_void_p(u.data_ptr()), int(slab), err), "sg_qoi_errors")
     return {"mean": err[0], "var": err[1], "full": err[2]}
+
+
+def mc_solve_batch(ctx, xi, batch=256, mg_precision=SG_PREC_FP32, rtol=1e-8, max_it=500, keep_paths=False,
+                   stream=None):
+    """Monte-Carlo mean and unbiased variance at t = T over the samples ``xi``
+    (numpy array n_samples x M); returns (mean, var, u_T or None, stats)."""
+    import torch
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    n_s = xi.shape[0]
+    n_x, n_t = ctx.info["n_x"], ctx.info["n_t"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mean = torch.empty(n_x, dtype=torch.float64, device=dev)
+    var = torch.empty(n_x, dtype=torch.float64, device=dev)
+    u_T = torch.empty(n_s * n_t * n_x, dtype=torch.float64, device=dev) if keep_paths else None
+    st = _abi.sg_mc_stats()
+    _check(_abi.load().mc_solve_batch(ctx.handle, n_s, xi.ctypes.data_as(C.POINTER(C.c_double)), int(batch),
+                                      int(mg_precision), float(rtol), int(max_it), C.c_void_p(mean.data_ptr()),
+                                      C.c_void_p(var.data_ptr()), C.c_void_p(u_T.data_ptr() if u_T is not None else None),
+                                      C.byref(st), C.c_void_p(_stream_handle(stream))), "mc_solve_batch")
+    return mean, var, u_T, {name: getattr(st, name) for name, _ in _abi.sg_mc_stats._fields_}
 
 
 def sg_autotune(ctx, reps=10):

@@ -14,7 +14,7 @@ SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = 0, 1, 2
 EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
                    "sg_destroy", "sg_status_string", "sg_last_error", "sg_mg_setup", "sg_vcycle",
                    "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
-                   "sg_rhs", "sg_moments", "sg_qoi_errors"])
+                   "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch"])
 
 
 class sg_mesh(C.Structure):
@@ -40,6 +40,11 @@ class sg_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("vmult_calls", C.c_int),
                 ("prec_calls", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
                 ("solve_ms", C.c_double), ("mg_setup_ms", C.c_double)]
+
+
+class sg_mc_stats(C.Structure):
+    _fields_ = [("n_samples", C.c_int), ("batches", C.c_int), ("total_iterations", C.c_int),
+                ("max_slab_iterations", C.c_int), ("max_rel_residual", C.c_double), ("solve_ms", C.c_double)]
 
 
 _lib = None
@@ -82,6 +87,9 @@ def load():
     lib.sg_moments.restype = C.c_int
     lib.sg_qoi_errors.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double)]
     lib.sg_qoi_errors.restype = C.c_int
+    lib.mc_solve_batch.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double, C.c_int,
+                                   vp, vp, vp, C.POINTER(sg_mc_stats), vp]
+    lib.mc_solve_batch.restype = C.c_int
     lib.sg_autotune.argtypes = [vp, C.c_int]
     lib.sg_autotune.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]

@@ -53,9 +53,7 @@ void free_ctx_device(sg_ctx* c) {
 }
 
 cudaError_t apply_device(sg_ctx* c, const double* x, double* y, cudaStream_t s) {
-  sg::ApplyParams p;
-  sg::fill_apply_params(c->hp, c->ls, c->d_ctab, c->d_grow, c->d_gcol, c->d_gterm, c->d_gval, c->d_perm, x, y, 0, p);
-  return sg::launch_apply(c->hp, c->ls, p, s);
+  return sg::apply_device_ctx(c, x, y, s);
 }
 
 bool is_device_ptr(const void* ptr) {
@@ -78,6 +76,47 @@ namespace sg {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace sg
 
+namespace sg {
+cudaError_t apply_device_ctx(sg_ctx* c, const double* x, double* y, cudaStream_t s) {
+  ApplyParams p;
+  fill_apply_params(c->hp, c->ls, c->d_ctab, c->d_grow, c->d_gcol, c->d_gterm, c->d_gval, c->d_perm, x, y, 0, p);
+  return launch_apply(c->hp, c->ls, p, s);
+}
+
+// Plans the apply kernel and uploads the tables of a host problem into a new
+// context (used by sg_setup and by the Monte-Carlo sample batches).
+sg_status make_ctx(HostProblem&& hp, int precision, sg_ctx** out, std::string& msg) {
+  sg_ctx* c = new (std::nothrow) sg_ctx();
+  if (!c) { msg = "host allocation failed"; return SG_ERR_OOM; }
+  c->hp = std::move(hp);
+  c->hp.precision = precision;
+  cudaGetDevice(&c->device);
+  sg_status st = sg::plan_apply(c->hp, c->ls, msg);
+  if (st != SG_OK) { delete c; return st; }
+  cudaError_t e = sg::prepare_apply_kernel(precision, c->hp.dim, c->hp.k, c->hp.n_t, c->ls.smem);
+  if (e != cudaSuccess) { delete c; msg = cudaGetErrorString(e); return SG_ERR_CUDA; }
+  if ((e = upload(&c->d_ctab, c->hp.ctab)) != cudaSuccess ||
+      (e = upload(&c->d_grow, c->hp.g.row)) != cudaSuccess ||
+      (e = upload(&c->d_gcol, c->hp.g.col)) != cudaSuccess ||
+      (e = upload(&c->d_gterm, c->hp.g.term)) != cudaSuccess ||
+      (e = upload(&c->d_gval, c->hp.g.val)) != cudaSuccess ||
+      (e = upload(&c->d_perm, c->hp.perm)) != cudaSuccess) {
+    free_ctx_device(c);
+    delete c;
+    msg = std::string("upload of tables: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
+  }
+  *out = c;
+  return SG_OK;
+}
+
+void destroy_ctx(sg_ctx* c) {
+  if (!c) return;
+  free_ctx_device(c);
+  delete c;
+}
+}  // namespace sg
+
 extern "C" {
 
 const char* sg_status_string(sg_status s) {
@@ -96,34 +135,18 @@ const char* sg_status_string(sg_status s) {
 
 const char* sg_last_error(void) { return g_last_error.c_str(); }
 
+
 sg_status sg_setup(const sg_mesh* mesh, int fe_degree, int time_degree, int n_slabs, double T,
                    int M, int chaos_order, const sg_coeff* coef, int precision, sg_ctx** out) {
   if (!out) return fail(SG_ERR_ARG, "sg_setup: out is NULL");
   if (precision != SG_PREC_FP64 && precision != SG_PREC_DW)
     return fail(SG_ERR_UNSUPPORTED, "sg_setup: precision not built");
-  sg_ctx* c = new (std::nothrow) sg_ctx();
-  if (!c) return fail(SG_ERR_OOM, "sg_setup: host allocation failed");
   std::string msg;
-  sg_status st = sg::build_host_problem(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order,
-                                        coef, c->hp, msg);
-  if (st != SG_OK) { delete c; return fail(st, "sg_setup: " + msg); }
-  c->hp.precision = precision;
-  cudaGetDevice(&c->device);
-  st = sg::plan_apply(c->hp, c->ls, msg);
-  if (st != SG_OK) { delete c; return fail(st, "sg_setup: " + msg); }
-  cudaError_t e = sg::prepare_apply_kernel(precision, c->hp.dim, c->hp.k, c->hp.n_t, c->ls.smem);
-  if (e != cudaSuccess) { delete c; return cuda_fail(e, "sg_setup: kernel attributes"); }
-  if ((e = upload(&c->d_ctab, c->hp.ctab)) != cudaSuccess ||
-      (e = upload(&c->d_grow, c->hp.g.row)) != cudaSuccess ||
-      (e = upload(&c->d_gcol, c->hp.g.col)) != cudaSuccess ||
-      (e = upload(&c->d_gterm, c->hp.g.term)) != cudaSuccess ||
-      (e = upload(&c->d_gval, c->hp.g.val)) != cudaSuccess ||
-      (e = upload(&c->d_perm, c->hp.perm)) != cudaSuccess) {
-    free_ctx_device(c);
-    delete c;
-    return cuda_fail(e, "sg_setup: upload of tables");
-  }
-  *out = c;
+  sg::HostProblem hp;
+  sg_status st = sg::build_host_problem(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef, hp, msg);
+  if (st != SG_OK) return fail(st, "sg_setup: " + msg);
+  st = sg::make_ctx(std::move(hp), precision, out, msg);
+  if (st != SG_OK) return fail(st, "sg_setup: " + msg);
   return SG_OK;
 }
 
@@ -359,6 +382,25 @@ sg_status sg_qoi_errors(sg_ctx* ctx, const double* u, int slab, double* err) {
   std::string msg;
   sg_status st = sg::exact_errors(ctx->hp, *ctx->exact, u, slab, err, msg);
   if (st != SG_OK) return fail(st, "sg_qoi_errors: " + msg);
+  return SG_OK;
+}
+
+sg_status mc_solve_batch(sg_ctx* ctx, int n_samples, const double* xi, int batch, int mg_precision, double rtol,
+                         int max_it, double* mean_T, double* var_T, double* u_T, sg_mc_stats* st, sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "mc_solve_batch: ctx is NULL");
+  if (!ctx->exact) return fail(SG_ERR_ARG, "mc_solve_batch: call sg_set_exact first");
+  if (n_samples < 1 || !xi) return fail(SG_ERR_ARG, "mc_solve_batch: no samples");
+  if (batch < 1 || batch > 512) return fail(SG_ERR_ARG, "mc_solve_batch: batch must be 1..512");
+  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32)
+    return fail(SG_ERR_ARG, "mc_solve_batch: mg_precision must be SG_PREC_FP64 or SG_PREC_FP32");
+  if (!(rtol > 0.0) || max_it < 1) return fail(SG_ERR_ARG, "mc_solve_batch: rtol or max_it out of range");
+  if (!mean_T || !var_T || !is_device_ptr(mean_T) || !is_device_ptr(var_T) || mean_T == var_T)
+    return fail(SG_ERR_ARG, "mc_solve_batch: mean_T and var_T must be distinct device vectors");
+  if (u_T && !is_device_ptr(u_T)) return fail(SG_ERR_ARG, "mc_solve_batch: u_T must be device memory");
+  std::string msg;
+  sg_status s = sg::mc_solve(ctx, n_samples, xi, batch, mg_precision, rtol, max_it, mean_T, var_T, u_T, st,
+                             reinterpret_cast<cudaStream_t>(stream), msg);
+  if (s != SG_OK) return fail(s, "mc_solve_batch: " + msg);
   return SG_OK;
 }
 

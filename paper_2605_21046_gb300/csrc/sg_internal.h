@@ -179,7 +179,10 @@ struct MG {
   double setup_ms = 0.0;
 };
 
-sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg);
+// single_class: precondition every row with the block of the mean coefficient
+// term (used for Monte-Carlo sample batches, whose rows all differ).
+sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg,
+                   bool single_class = false);
 size_t krylov_bytes(long long N, int m);
 void mg_free(MG& mg);
 // z = P^{-1} r for one slab vector (double in, double out) on a stream.
@@ -188,7 +191,27 @@ cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream);
 }  // namespace sg
 
 namespace sg {
-struct ExactData;
+sg_status make_ctx(HostProblem&& hp, int precision, sg_ctx** out, std::string& msg);
+void destroy_ctx(sg_ctx* c);
+// y = A x with the context's own tables (FP64 / DW vectors).
+cudaError_t apply_device_ctx(sg_ctx* c, const double* x, double* y, cudaStream_t s);
+// A manufactured finite-chaos solution and the slab-independent parts of its
+// load vector (see sg_manufactured.cu).
+struct ExactData {
+  int q = 0;
+  std::vector<int> idx_q;            // Lambda_q, graded order
+  std::vector<double> c;             // per alpha in Lambda_q
+  std::vector<int> freq;             // per alpha: 3 integer frequencies
+  std::vector<double> t_coef;
+  std::vector<int> p_in_q;           // position in Lambda_q of every row of the context, or -1
+  double* d_P = nullptr;             // [n_xi][n_x]
+  double* d_K = nullptr;             // [n_xi][n_x]
+  double* d_tpk = nullptr;           // 2 * kMaxNT slab scalars
+  int* d_zero_rows = nullptr;        // empty coupling table of the transfer apply
+};
+sg_status mc_solve(sg_ctx* parent, int n_samples, const double* xi, int batch, int mg_precision, double rtol,
+                   int max_it, double* mean_T, double* var_T, double* u_T, sg_mc_stats* st, cudaStream_t stream,
+                   std::string& msg);
 sg_status exact_build(const HostProblem& hp, int q, const double* c, const int* freq, int t_degree,
                       const double* t_coef, ExactData*& out, std::string& msg);
 void exact_free(ExactData* e);

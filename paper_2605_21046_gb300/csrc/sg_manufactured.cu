@@ -74,18 +74,6 @@ double poly_deriv(const std::vector<double>& c, double t) {
 
 }  // namespace
 
-struct ExactData {
-  int q = 0;
-  std::vector<int> idx_q;            // Lambda_q, graded order
-  std::vector<double> c;             // per alpha in Lambda_q
-  std::vector<int> freq;             // per alpha: 3 integer frequencies
-  std::vector<double> t_coef;
-  std::vector<int> p_in_q;           // position in Lambda_q of every alpha in Lambda_p, or -1
-  double* d_P = nullptr;             // [n_xi][n_x]
-  double* d_K = nullptr;             // [n_xi][n_x]
-  double* d_tpk = nullptr;           // 2 * n_t slab scalars
-  int* d_zero_rows = nullptr;        // empty coupling table of the transfer apply
-};
 
 void exact_free(ExactData* e) {
   if (!e) return;

@@ -637,6 +637,7 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
   }
   if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
   MGLevel& C = mg.lv[l + 1];
+  if (C.hp.n_xi * C.hp.n_t != V) return cudaErrorInvalidValue;   // level buffers hold V vectors
   restrict_to<T>(L, C, V, s);
   if ((e = issue_vcycle<T>(mg, l + 1, s)) != cudaSuccess) return e;
   if (!prolong<T>(L, C, V, s)) return cudaErrorInvalidValue;
@@ -669,7 +670,8 @@ void mg_free(MG& mg) {
   mg.d_cls = nullptr;
 }
 
-sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg) {
+sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg,
+                   bool single_class) {
   const auto t0 = std::chrono::steady_clock::now();
   mg.precision = precision;
   mg.nu = nu;
@@ -690,6 +692,14 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     } else {
       mg.cls[a] = it->second;
     }
+  }
+  if (single_class) {
+    // the mean block: coefficient term with the zero chaos index, weight 1
+    std::vector<double> mean_diag(fine.n_terms, 0.0);
+    for (int t = 0; t < fine.n_terms; ++t)
+      if (std::all_of(fine.mus[t].begin(), fine.mus[t].end(), [](int v) { return v == 0; })) mean_diag[t] = 1.0;
+    class_diag.assign(1, mean_diag);
+    std::fill(mg.cls.begin(), mg.cls.end(), 0);
   }
   mg.n_classes = (int)class_diag.size();
   // level problems
@@ -713,8 +723,17 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     HostProblem c;
     sg_status st = build_host_problem_pieces(&m, f.k, f.r, f.n_slabs, f.T, f.M, f.p, pieces, c, msg);
     if (st != SG_OK) return st;
+    // every level carries the rows of the fine problem (chaos modes, or the
+    // samples of a Monte-Carlo batch): same count, same coupling table
+    c.n_xi = fine.n_xi;
+    c.idx = fine.idx;
     hps.push_back(std::move(c));
   }
+  for (const HostProblem& h : hps)
+    if (h.n_xi != fine.n_xi || h.n_t != fine.n_t || h.n_terms != fine.n_terms) {
+      msg = "multigrid levels disagree in rows, time nodes or coefficient terms";
+      return SG_ERR_ARG;
+    }
   mg.lv.resize(hps.size());
   cudaError_t e = cudaSuccess;
   for (size_t l = 0; l < hps.size(); ++l) {

@@ -153,6 +153,16 @@ typedef struct {
   double solve_ms;         /* wall time of the call                          */
 } sg_mc_stats;
 
+/* Statistics of one sg_adjoint_gradient call (host struct out). */
+typedef struct {
+  int forward_solves;   /* slab solves of the forward sweep and the recomputed segments */
+  int adjoint_solves;   /* transposed slab solves (one per slab)                        */
+  int max_iterations;   /* largest FGMRES iteration count of any of them                */
+  int checkpoints;      /* slab states kept between the sweeps                          */
+  double J;             /* the quantity of interest (as returned in *J)                 */
+  double solve_ms;      /* wall time of the call                                        */
+} sg_adjoint_stats;
+
 /* sg_setup - discretise one problem and make it resident on the current
  * CUDA device (Sec. 3: Q_k in space, dG(r) in time, Lambda_p chaos; Sec. 3.5:
  * time matrices eqs. At/Bt/Ct, G_mu eq. triple_stoch and its factorisation
@@ -229,6 +239,53 @@ sg_status sg_vcycle(sg_ctx* ctx, const double* r, double* z, sg_stream stream);
  * not finite. */
 sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, double rtol, int max_it,
                         int restart, sg_solve_stats* st, sg_stream stream);
+
+/* sg_set_coefficient - replace the coefficient of a context (Sec. 2,
+ * eq. coeff_expansion: the fields a_mu(x)) by pieces with the same count and
+ * the same chaos index mu per piece (amplitudes, factors and cell scales may
+ * change), keeping the mesh, the coupling tables and the manufactured load
+ * vector of sg_set_exact (which stays the one of the old coefficient).  The
+ * paper has no counterpart; an optimisation loop over the coefficient uses it.
+ * Rebuilds the multigrid preconditioner when there is one.  Synchronous. */
+sg_status sg_set_coefficient(sg_ctx* ctx, const sg_coeff* coef);
+
+/* sg_solve_slab_adjoint - solve the transposed slab system A^T x = rhs
+ * (A of eq. local_tensor_system) with FGMRES preconditioned by the V-cycle of
+ * the transposed blocks A_alpha^T.  The paper solves only A; the transposed
+ * system is the adjoint equation of sg_adjoint_gradient.  A^T here keeps the
+ * Dirichlet rows as identity rows (transpose of the interior block).
+ * Arguments, layout, workspace and errors as sg_solve_slab. */
+sg_status sg_solve_slab_adjoint(sg_ctx* ctx, int slab, const double* rhs, double* x, double rtol,
+                                int max_it, int restart, sg_solve_stats* st, sg_stream stream);
+
+/* sg_adjoint_gradient - march the manufactured problem of sg_set_exact over
+ * all slabs (eq. local_tensor_system with the load vector of eq. load_vector
+ * held fixed as data) and return the quantity of interest
+ *     J = sum_alpha U_alpha(T)^T M_x U_alpha(T) = E[ ||u_h(., T)||^2_{L2(D)} ]
+ * (the variance identity eq. qoi-variance-chaos summed with the mean) and its
+ * gradient with respect to the coefficient: the amplitude of every piece
+ * (sg_coeff.amp) and the per-cell scale of one piece.  The paper has no
+ * gradient; this is the discrete adjoint of its marching: transposed slab
+ * solves (sg_solve_slab_adjoint) backwards in time with the adjoint transfer
+ * (I (x) C_t^T (x) M_x) (eq. Ct transposed), then
+ *     dJ/dp = - sum_n lambda_n^T (G_mu (x) B_t (x) dK/dp) U_n.
+ * Forward states are kept every `checkpoint_every` slabs and each segment is
+ * recomputed before its backward pass (memory (N / checkpoint_every +
+ * checkpoint_every + 4) slab vectors).
+ *   rtol, max_it      FGMRES(30) tolerance and limit of every slab solve
+ *   cell_piece        index of the piece whose per-cell scale gets a gradient
+ *                     (-1: none)
+ *   J                 HOST double out (may be NULL)
+ *   grad_amp          HOST n_pieces doubles out (may be NULL)
+ *   grad_cell         HOST n_cells doubles out (NULL allowed; ignored if
+ *                     cell_piece < 0)
+ *   st                statistics out (may be NULL)
+ * Needs sg_set_exact and sg_mg_setup; the Dirichlet data of the manufactured
+ * solution are zero, so J covers all nodes.  At most 16 coefficient terms.
+ * Allocates and frees its device workspaces.  Synchronous. */
+sg_status sg_adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int checkpoint_every, int cell_piece,
+                              double* J, double* grad_amp, double* grad_cell, sg_adjoint_stats* st,
+                              sg_stream stream);
 
 /* sg_apply_host_static - sg_apply_host for callers that cannot let a library
  * allocate device memory when they call it: applications whose memory pool

@@ -40,9 +40,10 @@ def _check(status, where):
 class SGContext:
     """Owns one sg_ctx; ``info`` holds its sizes."""
 
-    def __init__(self, handle):
+    def __init__(self, handle, n_pieces=None):
         self._h = C.c_void_p(handle)
         self.info = sg_get_info(self)
+        self.n_pieces = n_pieces
 
     @property
     def handle(self):
@@ -127,7 +128,7 @@ def sg_setup(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef, pre
     _check(lib.sg_setup(C.byref(mesh), fe_degree, time_degree, n_slabs, float(T), M, chaos_order,
                         C.byref(cs), precision, C.byref(h)), "sg_setup")
     del keep
-    return SGContext(h.value)
+    return SGContext(h.value, len(coef))
 
 
 def sg_setup_spec(spec, precision=0):
@@ -217,6 +218,105 @@ def sg_solve_slab(ctx, slab, rhs, x, rtol=1e-8, max_it=500, restart=30, stream=N
     if check:
         _check(status, "sg_solve_slab")
     return out
+
+
+def sg_solve_slab_adjoint(ctx, slab, rhs, x, rtol=1e-8, max_it=500, restart=30, stream=None, check=True):
+    """FGMRES solve of the transposed slab system A^T x = rhs (the adjoint
+    equation); x holds the initial guess.  Returns the statistics dict."""
+    _check_vec(ctx, rhs, x)
+    st = _abi.sg_solve_stats()
+    status = _abi.load().sg_solve_slab_adjoint(ctx.handle, int(slab), C.c_void_p(rhs.data_ptr()),
+                                               C.c_void_p(x.data_ptr()), float(rtol), int(max_it), int(restart),
+                                               C.byref(st), C.c_void_p(_stream_handle(stream)))
+    out = {name: getattr(st, name) for name, _ in _abi.sg_solve_stats._fields_}
+    out["status"] = status
+    if check:
+        _check(status, "sg_solve_slab_adjoint")
+    return out
+
+
+def sg_adjoint_gradient(ctx, rtol=1e-10, max_it=500, checkpoint_every=10, cell_piece=-1, stream=None):
+    """J = E ||u_h(T)||^2 of the marched manufactured problem and its gradient
+    with respect to every piece amplitude and (cell_piece >= 0) the per-cell
+    scale of one piece.  Returns (J, grad_amp, grad_cell or None, stats)."""
+    n_pieces = ctx.n_pieces
+    g_amp = np.zeros(max(n_pieces, 1), dtype=np.float64)
+    g_cell = np.zeros(ctx.info["n_cells"], dtype=np.float64) if cell_piece >= 0 else None
+    J = C.c_double(0.0)
+    st = _abi.sg_adjoint_stats()
+    _check(_abi.load().sg_adjoint_gradient(
+        ctx.handle, float(rtol), int(max_it), int(checkpoint_every), int(cell_piece), C.byref(J),
+        g_amp.ctypes.data_as(C.POINTER(C.c_double)),
+        g_cell.ctypes.data_as(C.POINTER(C.c_double)) if g_cell is not None else None,
+        C.byref(st), C.c_void_p(_stream_handle(stream))), "sg_adjoint_gradient")
+    return J.value, g_amp[:n_pieces], g_cell, {name: getattr(st, name) for name, _ in _abi.sg_adjoint_stats._fields_}
+
+
+def sg_set_coefficient(ctx, coef):
+    """Replace the coefficient pieces (same count, same mu per piece) keeping
+    the mesh, tables and manufactured load vector (sg_set_coefficient)."""
+    cs, keep = _coeff_struct(coef, ctx.info["M"], ctx.info["dim"])
+    _check(_abi.load().sg_set_coefficient(ctx.handle, C.byref(cs)), "sg_set_coefficient")
+    del keep
+
+
+def _pieces_with(spec, amp, cell_piece=-1, cell_scale=None):
+    coef = [dict(p) for p in spec["coef"]]
+    for i, p in enumerate(coef):
+        p["amp"] = float(amp[i])
+    if cell_piece >= 0 and cell_scale is not None:
+        coef[cell_piece]["cell_scale"] = np.asarray(cell_scale, dtype=np.float64)
+    return coef
+
+
+def _make_energy_function():
+    import torch
+
+    class EnergyAtT(torch.autograd.Function):
+        """J(amp, cell_scale) = E ||u_h(T)||^2 of the marched manufactured
+        problem; backward is the discrete adjoint (sg_adjoint_gradient)."""
+
+        @staticmethod
+        def forward(fctx, amp, cell_scale, spec, exact, cell_piece, mg_precision, rtol, checkpoint_every):
+            a = amp.detach().cpu().numpy()
+            cs = cell_scale.detach().cpu().numpy() if cell_scale is not None else None
+            ctx = sg_setup_spec(spec)
+            try:
+                sg_set_exact(ctx, exact)   # load vector of the nominal coefficient, held fixed
+                sg_set_coefficient(ctx, _pieces_with(spec, a, cell_piece, cs))
+                sg_mg_setup(ctx, mg_precision)
+                J, g_amp, g_cell, _ = sg_adjoint_gradient(ctx, rtol=rtol, checkpoint_every=checkpoint_every,
+                                                          cell_piece=cell_piece if cs is not None else -1)
+            finally:
+                ctx.destroy()
+            fctx.has_cell = g_cell is not None
+            fctx.save_for_backward(torch.from_numpy(g_amp.copy()).to(amp),
+                                   torch.from_numpy(g_cell.copy()).to(cell_scale) if fctx.has_cell
+                                   else amp.new_zeros(0))
+            return amp.new_tensor(J)
+
+        @staticmethod
+        def backward(fctx, gJ):
+            g_amp, g_cell = fctx.saved_tensors
+            return (gJ * g_amp, gJ * g_cell if fctx.has_cell else None, None, None, None, None, None, None)
+
+    return EnergyAtT
+
+
+_ENERGY = None
+
+
+def energy_at_T(spec, exact, amp, cell_scale=None, cell_piece=-1, mg_precision=0, rtol=1e-10,
+                checkpoint_every=10):
+    """J = E ||u_h(T)||^2 as a differentiable torch function of the piece
+    amplitudes (1-D float64 CPU tensor) and, with cell_piece >= 0, of the
+    per-cell scale of that piece.  The operator uses (amp, cell_scale); the
+    load vector is the one of ``spec``'s own coefficient, held fixed; the
+    gradient comes from the discrete adjoint on the GPU."""
+    global _ENERGY
+    if _ENERGY is None:
+        _ENERGY = _make_energy_function()
+    return _ENERGY.apply(amp, cell_scale, spec, exact, cell_piece, mg_precision, rtol, checkpoint_every)
 
 
 def sg_set_exact(ctx, exact):

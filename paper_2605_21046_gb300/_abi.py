@@ -14,7 +14,8 @@ SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = 0, 1, 2
 EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",
                    "sg_destroy", "sg_status_string", "sg_last_error", "sg_mg_setup", "sg_vcycle",
                    "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
-                   "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch"])
+                   "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch",
+                   "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient"])
 
 
 class sg_mesh(C.Structure):
@@ -40,6 +41,11 @@ class sg_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("vmult_calls", C.c_int),
                 ("prec_calls", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
                 ("solve_ms", C.c_double), ("mg_setup_ms", C.c_double)]
+
+
+class sg_adjoint_stats(C.Structure):
+    _fields_ = [("forward_solves", C.c_int), ("adjoint_solves", C.c_int), ("max_iterations", C.c_int),
+                ("checkpoints", C.c_int), ("J", C.c_double), ("solve_ms", C.c_double)]
 
 
 class sg_mc_stats(C.Structure):
@@ -90,6 +96,15 @@ def load():
     lib.mc_solve_batch.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double, C.c_int,
                                    vp, vp, vp, C.POINTER(sg_mc_stats), vp]
     lib.mc_solve_batch.restype = C.c_int
+    lib.sg_solve_slab_adjoint.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int,
+                                          C.POINTER(sg_solve_stats), vp]
+    lib.sg_solve_slab_adjoint.restype = C.c_int
+    lib.sg_adjoint_gradient.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(sg_adjoint_stats),
+                                        vp]
+    lib.sg_adjoint_gradient.restype = C.c_int
+    lib.sg_set_coefficient.argtypes = [vp, C.POINTER(sg_coeff)]
+    lib.sg_set_coefficient.restype = C.c_int
     lib.sg_autotune.argtypes = [vp, C.c_int]
     lib.sg_autotune.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]

@@ -83,6 +83,12 @@ cudaError_t apply_device_ctx(sg_ctx* c, const double* x, double* y, cudaStream_t
   return launch_apply(c->hp, c->ls, p, s);
 }
 
+cudaError_t apply_device_ctx_t(sg_ctx* c, const double* x, double* y, cudaStream_t s) {
+  ApplyParams p;
+  fill_apply_params(c->hp, c->ls, c->d_ctab, c->d_grow, c->d_gcol, c->d_gterm, c->d_gval, c->d_perm, x, y, 1, p);
+  return launch_apply(c->hp, c->ls, p, s);
+}
+
 // Plans the apply kernel and uploads the tables of a host problem into a new
 // context (used by sg_setup and by the Monte-Carlo sample batches).
 sg_status make_ctx(HostProblem&& hp, int precision, sg_ctx** out, std::string& msg) {
@@ -235,6 +241,42 @@ sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega) {
   return SG_OK;
 }
 
+sg_status sg_set_coefficient(sg_ctx* ctx, const sg_coeff* coef) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_set_coefficient: ctx is NULL");
+  sg::HostProblem& hp = ctx->hp;
+  std::vector<sg::Piece> pieces;
+  std::string msg;
+  sg_status st = sg::parse_pieces(coef, hp.M, hp.n_cells, pieces, msg);
+  if (st != SG_OK) return fail(st, "sg_set_coefficient: " + msg);
+  if (pieces.size() != hp.pieces.size()) return fail(SG_ERR_ARG, "sg_set_coefficient: number of pieces differs");
+  for (size_t i = 0; i < pieces.size(); ++i) {
+    if (pieces[i].mu != hp.pieces[i].mu) return fail(SG_ERR_ARG, "sg_set_coefficient: chaos index of a piece differs");
+    for (int d = 0; d < hp.dim; ++d) {
+      const int kd = pieces[i].kind[d];
+      if (kd != SG_F_ONE && kd != SG_F_SIN && kd != SG_F_POW) return fail(SG_ERR_ARG, "sg_set_coefficient: unknown factor kind");
+      if (kd == SG_F_POW && pieces[i].k[d] < 0) return fail(SG_ERR_ARG, "sg_set_coefficient: negative power");
+    }
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sg_set_coefficient: synchronize");
+  std::vector<sg::Piece> old = std::move(hp.pieces);
+  hp.pieces = std::move(pieces);
+  st = sg::fill_ctab(hp, msg);
+  if (st != SG_OK) {
+    hp.pieces = std::move(old);
+    sg::fill_ctab(hp, msg);
+    return fail(st, "sg_set_coefficient: " + msg);
+  }
+  e = cudaMemcpy(ctx->d_ctab, hp.ctab.data(), hp.ctab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_set_coefficient: upload");
+  if (ctx->mg) {
+    const int prec = ctx->mg->precision, nu = ctx->mg->nu;
+    const double omega = ctx->mg->omega;
+    return sg_mg_setup(ctx, prec, nu, omega);
+  }
+  return SG_OK;
+}
+
 sg_status sg_vcycle(sg_ctx* ctx, const double* r, double* z, sg_stream stream) {
   if (!ctx) return fail(SG_ERR_ARG, "sg_vcycle: ctx is NULL");
   if (!ctx->mg) return fail(SG_ERR_ARG, "sg_vcycle: call sg_mg_setup first");
@@ -261,6 +303,42 @@ sg_status sg_solve_slab(sg_ctx* ctx, int slab, const double* rhs, double* x, dou
   sg_status s = sg::fgmres(ctx, rhs, x, rtol, max_it, restart, st, reinterpret_cast<cudaStream_t>(stream), msg,
                            &apply_device);
   if (s != SG_OK) return fail(s, "sg_solve_slab: " + msg);
+  return SG_OK;
+}
+
+sg_status sg_solve_slab_adjoint(sg_ctx* ctx, int slab, const double* rhs, double* x, double rtol, int max_it,
+                                int restart, sg_solve_stats* st, sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: ctx is NULL");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: call sg_mg_setup first");
+  if (slab < 0 || slab >= ctx->hp.n_slabs) return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: slab out of range");
+  if (!rhs || !x) return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: null vector");
+  if (!(rtol > 0.0) || max_it < 1 || restart < 1 || restart > 200)
+    return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: rtol, max_it or restart out of range");
+  const long long n = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
+  if (rhs < x + n && x < rhs + n) return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: rhs and x overlap");
+  if (!is_device_ptr(rhs) || !is_device_ptr(x))
+    return fail(SG_ERR_ARG, "sg_solve_slab_adjoint: vectors must be device memory");
+  std::string msg;
+  sg_status s = sg::fgmres(ctx, rhs, x, rtol, max_it, restart, st, reinterpret_cast<cudaStream_t>(stream), msg,
+                           &sg::apply_device_ctx_t, 1);
+  if (s != SG_OK) return fail(s, "sg_solve_slab_adjoint: " + msg);
+  return SG_OK;
+}
+
+sg_status sg_adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int checkpoint_every, int cell_piece,
+                              double* J, double* grad_amp, double* grad_cell, sg_adjoint_stats* st,
+                              sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_adjoint_gradient: ctx is NULL");
+  if (!ctx->exact) return fail(SG_ERR_ARG, "sg_adjoint_gradient: call sg_set_exact first");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_adjoint_gradient: call sg_mg_setup first");
+  if (!(rtol > 0.0) || max_it < 1) return fail(SG_ERR_ARG, "sg_adjoint_gradient: rtol or max_it out of range");
+  if (checkpoint_every < 1) return fail(SG_ERR_ARG, "sg_adjoint_gradient: checkpoint_every must be >= 1");
+  if (cell_piece < -1 || cell_piece >= (int)ctx->hp.pieces.size())
+    return fail(SG_ERR_ARG, "sg_adjoint_gradient: cell_piece out of range");
+  std::string msg;
+  sg_status s = sg::adjoint_gradient(ctx, rtol, max_it, checkpoint_every, cell_piece, J, grad_amp, grad_cell, st,
+                                     reinterpret_cast<cudaStream_t>(stream), msg);
+  if (s != SG_OK) return fail(s, "sg_adjoint_gradient: " + msg);
   return SG_OK;
 }
 

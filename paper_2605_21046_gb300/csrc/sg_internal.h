@@ -81,6 +81,11 @@ sg_status build_host_problem_pieces(const sg_mesh* mesh, int k, int r, int n_sla
                                     int M, int p, const std::vector<Piece>& pieces,
                                     HostProblem& hp, std::string& msg);
 
+// Coefficient pieces of an sg_coeff (M-long indices, n_cells scales).
+sg_status parse_pieces(const sg_coeff* coef, int M, int64_t n_cells, std::vector<Piece>& pieces, std::string& msg);
+// hp.ctab from hp.pieces / hp.piece_term (mesh, degree and terms already set).
+sg_status fill_ctab(HostProblem& hp, std::string& msg);
+
 // ---------------------------------------------------------------- kernels
 struct ApplyParams {
   const void* x;          // double (FP64, DW) or float (F32) vectors
@@ -174,8 +179,8 @@ struct MG {
   int* d_cls = nullptr;
   std::vector<MGLevel> lv;
   cudaStream_t stream = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph_t[2] = {nullptr, nullptr};       // V-cycle of A (0) and of A^T (1)
+  cudaGraphExec_t exec_t[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
 };
 
@@ -185,8 +190,9 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
                    bool single_class = false);
 size_t krylov_bytes(long long N, int m);
 void mg_free(MG& mg);
-// z = P^{-1} r for one slab vector (double in, double out) on a stream.
-cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream);
+// z = P^{-1} r for one slab vector (double in, double out) on a stream; with
+// trans != 0 the V-cycle of the transposed blocks A_alpha^T.
+cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans = 0);
 
 }  // namespace sg
 
@@ -225,7 +231,17 @@ sg_status exact_errors(const HostProblem& hp, const ExactData& E, const double* 
 void set_last_error(const std::string& msg);
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
                  cudaStream_t s, std::string& msg,
-                 cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t));
+                 cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t), int trans = 0);
+cudaError_t apply_device_ctx_t(sg_ctx* c, const double* x, double* y, cudaStream_t s);
+// Value of a coefficient factor (SG_F_ONE / SIN / POW) at one coordinate.
+double factor_value(int kind, int k, double s);
+// y = y + (I (x) Tm (x) M_x) x on interior rows (y unchanged on Dirichlet rows);
+// Tm an N_t x N_t row-major time matrix.
+cudaError_t time_mass_apply(const HostProblem& hp, const LaunchShape& ls, const void* ctab, const int* zero_rows,
+                            const int* gcol, const int* gterm, const double* gval, const int* perm,
+                            const double* Tm, const double* x, double* y, cudaStream_t s);
+sg_status adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int K, int cell_piece, double* J_out,
+                           double* g_amp, double* g_cell, sg_adjoint_stats* st, cudaStream_t s, std::string& msg);
 }
 
 struct sg_ctx {

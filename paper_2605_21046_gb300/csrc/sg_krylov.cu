@@ -137,7 +137,7 @@ static cudaError_t norm2(const double* w, long long N, double* part, double* out
 
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
                  cudaStream_t s, std::string& msg,
-                 cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t)) {
+                 cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t), int trans) {
   const auto t0 = std::chrono::steady_clock::now();
   const long long N = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
   const size_t need = krylov_bytes(N, m);
@@ -203,7 +203,7 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
     for (int j = 0; j < m; ++j) {
       double* vj = ws.V + (long long)j * N;
       double* zj = ws.Z + (long long)j * N;
-      CK(mg_apply(*ctx->mg, vj, zj, s));
+      CK(mg_apply(*ctx->mg, vj, zj, s, trans));
       ++stats.prec_calls;
       CK(apply(ctx, zj, ws.w, s));
       ++stats.vmult_calls;

@@ -59,7 +59,7 @@ __global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long
 // Additive Vanka step: x += omega / mult * inv(patch) * r_patch for every
 // (cell, alpha).  One warp per (cell, 32 consecutive alpha): lanes share the
 // cell, so the patch inverse of a diagonal class is a broadcast load.
-template <typename T, int DIM, int K, int NT>
+template <typename T, int DIM, int K, int NT, bool TRANS>
 __global__ void mg_vanka(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv,
                          const int* __restrict__ cls, int n_xi, long long n_x, long long n_cells,
                          int cells0, int cells1, int nnx, int nny, int nnz, T omega) {
@@ -93,10 +93,16 @@ __global__ void mg_vanka(const T* __restrict__ r, T* __restrict__ x, const T* __
 #pragma unroll
     for (int a = 0; a < NKD; ++a) {
       if (!inner[a]) continue;
-      const T* row = M + (i * NKD + a) * NP;
       T z = T(0);
+      if constexpr (TRANS) {
+        // inverse of the transposed patch = transpose of the patch inverse
 #pragma unroll
-      for (int q = 0; q < NP; ++q) z += row[q] * rp[q];
+        for (int q = 0; q < NP; ++q) z += M[q * NP + i * NKD + a] * rp[q];
+      } else {
+        const T* row = M + (i * NKD + a) * NP;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) z += row[q] * rp[q];
+      }
       const long long g = node[a];
       const int gx = (int)(g % nnx), gy = (int)((g / nnx) % nny), gz = (int)(g / ((long long)nnx * nny));
       int mult = (gx % K == 0 ? 2 : 1) * (gy % K == 0 ? 2 : 1);
@@ -177,7 +183,7 @@ __global__ void mg_restrict(const T* __restrict__ rf, T* __restrict__ bc, int V,
 template <typename T>
 __global__ void mg_coarse(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv,
                           const int* __restrict__ cls, const long long* __restrict__ inner, int n_int,
-                          int n_t, long long n_x) {
+                          int n_t, long long n_x, int trans) {
   extern __shared__ __align__(16) unsigned char sm[];
   T* bs = reinterpret_cast<T*>(sm);
   const int alpha = blockIdx.x;
@@ -187,8 +193,12 @@ __global__ void mg_coarse(const T* __restrict__ b, T* __restrict__ x, const T* _
   const T* M = inv + (long long)cls[alpha] * n_int * n_int;
   for (int i = threadIdx.x; i < n_int; i += blockDim.x) {
     T s = T(0);
-    const T* row = M + (long long)i * n_int;
-    for (int q = 0; q < n_int; ++q) s += row[q] * bs[q];
+    if (trans) {
+      for (int q = 0; q < n_int; ++q) s += M[(long long)q * n_int + i] * bs[q];
+    } else {
+      const T* row = M + (long long)i * n_int;
+      for (int q = 0; q < n_int; ++q) s += row[q] * bs[q];
+    }
     x[base + inner[i]] = s;
   }
 }
@@ -523,15 +533,15 @@ std::vector<double> coarsen_scale(const std::vector<double>& s, const HostProble
 }
 
 template <typename T>
-cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s);
+cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans);
 
 // r = b - A x in one apply (residual mode: the init kernel writes b minus the
 // Dirichlet rows, the cell kernel subtracts).
 template <typename T>
-cudaError_t residual(MG& mg, int l, cudaStream_t s) {
+cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
   MGLevel& L = mg.lv[l];
   ApplyParams p;
-  fill_apply_params(L.hp, L.ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, 0, p);
+  fill_apply_params(L.hp, L.ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, trans, p);
   p.b = L.d_b;
   p.mode = kApplyResidual;
   return launch_apply(L.hp, L.ls, p, s);
@@ -553,20 +563,21 @@ __global__ void mg_first_residual(const T* __restrict__ b, T* __restrict__ r, lo
 }
 
 template <typename T, int DIM, int K, int NT>
-void launch_vanka(MG& mg, MGLevel& L, cudaStream_t s) {
+void launch_vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   const long long warps = L.hp.n_cells * ((L.hp.n_xi + 31) / 32);
   const int block = 128;
   const long long grid = (warps * 32 + block - 1) / block;
-  mg_vanka<T, DIM, K, NT><<<(unsigned)grid, block, 0, s>>>(
+  auto kern = trans ? &mg_vanka<T, DIM, K, NT, true> : &mg_vanka<T, DIM, K, NT, false>;
+  kern<<<(unsigned)grid, block, 0, s>>>(
       static_cast<const T*>(L.d_r), static_cast<T*>(L.d_x), static_cast<const T*>(L.d_inv), mg.d_cls, L.hp.n_xi,
       L.hp.n_x, L.hp.n_cells, L.hp.cells[0], L.hp.cells[1], L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], T(mg.omega));
 }
 
 template <typename T>
-bool vanka(MG& mg, MGLevel& L, cudaStream_t s) {
+bool vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   const int d = L.hp.dim, k = L.hp.k, t = L.hp.n_t;
 #define SG_V(D, KK, TT) \
-  if (d == D && k == KK && t == TT) { launch_vanka<T, D, KK, TT>(mg, L, s); return true; }
+  if (d == D && k == KK && t == TT) { launch_vanka<T, D, KK, TT>(mg, L, s, trans); return true; }
   SG_V(2, 1, 1) SG_V(2, 1, 2) SG_V(2, 1, 3) SG_V(2, 1, 4)
   SG_V(2, 2, 1) SG_V(2, 2, 2) SG_V(2, 2, 3) SG_V(2, 2, 4)
   SG_V(2, 3, 1) SG_V(2, 3, 2) SG_V(2, 3, 3) SG_V(2, 3, 4)
@@ -612,7 +623,7 @@ void restrict_to(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
+cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
   MGLevel& L = mg.lv[l];
   const int V = L.hp.n_xi * L.hp.n_t;
   const long long n = (long long)V * L.hp.n_x;
@@ -622,7 +633,8 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
     const size_t smem = (size_t)L.n_int * sizeof(T);
     mg_coarse<T><<<L.hp.n_xi, 256, smem, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
                                               static_cast<const T*>(L.d_inv), mg.d_cls,
-                                              reinterpret_cast<const long long*>(L.d_inner), L.n_int, L.hp.n_t, L.hp.n_x);
+                                              reinterpret_cast<const long long*>(L.d_inner), L.n_int, L.hp.n_t, L.hp.n_x,
+                                              trans);
     return cudaGetLastError();
   }
   cudaError_t e;
@@ -630,20 +642,20 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
     if (it == 0) {
       mg_first_residual<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_r), n,
                                                             L.hp.n_x, L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
-    } else if ((e = residual<T>(mg, l, s)) != cudaSuccess) {
+    } else if ((e = residual<T>(mg, l, s, trans)) != cudaSuccess) {
       return e;
     }
-    if (!vanka<T>(mg, L, s)) return cudaErrorInvalidValue;
+    if (!vanka<T>(mg, L, s, trans)) return cudaErrorInvalidValue;
   }
-  if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
+  if ((e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
   MGLevel& C = mg.lv[l + 1];
   if (C.hp.n_xi * C.hp.n_t != V) return cudaErrorInvalidValue;   // level buffers hold V vectors
   restrict_to<T>(L, C, V, s);
-  if ((e = issue_vcycle<T>(mg, l + 1, s)) != cudaSuccess) return e;
+  if ((e = issue_vcycle<T>(mg, l + 1, s, trans)) != cudaSuccess) return e;
   if (!prolong<T>(L, C, V, s)) return cudaErrorInvalidValue;
   for (int it = 0; it < mg.nu; ++it) {
-    if ((e = residual<T>(mg, l, s)) != cudaSuccess) return e;
-    if (!vanka<T>(mg, L, s)) return cudaErrorInvalidValue;
+    if ((e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
+    if (!vanka<T>(mg, L, s, trans)) return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -651,8 +663,12 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s) {
 }  // namespace
 
 void mg_free(MG& mg) {
-  if (mg.exec) cudaGraphExecDestroy(mg.exec);
-  if (mg.graph) cudaGraphDestroy(mg.graph);
+  for (int t = 0; t < 2; ++t) {
+    if (mg.exec_t[t]) cudaGraphExecDestroy(mg.exec_t[t]);
+    if (mg.graph_t[t]) cudaGraphDestroy(mg.graph_t[t]);
+    mg.exec_t[t] = nullptr;
+    mg.graph_t[t] = nullptr;
+  }
   if (mg.stream) cudaStreamDestroy(mg.stream);
   cudaFree(mg.d_cls);
   for (MGLevel& L : mg.lv) {
@@ -664,8 +680,6 @@ void mg_free(MG& mg) {
     }
   }
   mg.lv.clear();
-  mg.exec = nullptr;
-  mg.graph = nullptr;
   mg.stream = nullptr;
   mg.d_cls = nullptr;
 }
@@ -827,25 +841,26 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
   return SG_OK;
 }
 
-cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream) {
+cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans) {
   MGLevel& L0 = mg.lv[0];
   const long long n = (long long)L0.hp.n_xi * L0.hp.n_t * L0.hp.n_x;
   const bool f32 = mg.precision == kPrecF32;
+  const int t = trans ? 1 : 0;
   cudaError_t e;
-  if (!mg.exec) {
+  if (!mg.exec_t[t]) {
     if ((e = cudaStreamBeginCapture(mg.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-    cudaError_t ei = f32 ? issue_vcycle<float>(mg, 0, mg.stream) : issue_vcycle<double>(mg, 0, mg.stream);
-    e = cudaStreamEndCapture(mg.stream, &mg.graph);
+    cudaError_t ei = f32 ? issue_vcycle<float>(mg, 0, mg.stream, t) : issue_vcycle<double>(mg, 0, mg.stream, t);
+    e = cudaStreamEndCapture(mg.stream, &mg.graph_t[t]);
     if (ei != cudaSuccess) return ei;
     if (e != cudaSuccess) return e;
-    if ((e = cudaGraphInstantiate(&mg.exec, mg.graph, 0)) != cudaSuccess) return e;
+    if ((e = cudaGraphInstantiate(&mg.exec_t[t], mg.graph_t[t], 0)) != cudaSuccess) return e;
   }
   if (f32)
     mg_convert<double, float><<<grid_for(n, 256), 256, 0, stream>>>(r, static_cast<float*>(L0.d_b), n);
   else
     mg_convert<double, double><<<grid_for(n, 256), 256, 0, stream>>>(r, static_cast<double*>(L0.d_b), n);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cudaGraphLaunch(mg.exec, stream)) != cudaSuccess) return e;
+  if ((e = cudaGraphLaunch(mg.exec_t[t], stream)) != cudaSuccess) return e;
   if (f32)
     mg_convert<float, double><<<grid_for(n, 256), 256, 0, stream>>>(static_cast<const float*>(L0.d_x), z, n);
   else

@@ -176,7 +176,7 @@ double hermite_triple(int a, int b, int c) {
   return w[c];
 }
 
-static double factor_value(int kind, int k, double s) {
+double factor_value(int kind, int k, double s) {
   switch (kind) {
     case SG_F_ONE: return 1.0;
     case SG_F_SIN: return std::sin(k * M_PI * s);
@@ -196,7 +196,19 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
   if (M < 1 || M > 16) { msg = "invalid M"; return SG_ERR_ARG; }
   int64_t n_cells = 1;
   for (int d = 0; d < mesh->dim && d < 3; ++d) n_cells *= std::max(1, mesh->cells[d]);
-  std::vector<Piece> pieces(coef->n_pieces);
+  std::vector<Piece> pieces;
+  sg_status st = parse_pieces(coef, M, n_cells, pieces, msg);
+  if (st != SG_OK) return st;
+  return build_host_problem_pieces(mesh, k, r, n_slabs, T, M, p, pieces, hp, msg);
+}
+
+sg_status parse_pieces(const sg_coeff* coef, int M, int64_t n_cells, std::vector<Piece>& pieces, std::string& msg) {
+  if (!coef) { msg = "null coefficient"; return SG_ERR_ARG; }
+  if (coef->n_pieces < 1 || !coef->mu || !coef->amp || !coef->factor_kind || !coef->factor_k) {
+    msg = "coefficient needs at least one piece and all arrays";
+    return SG_ERR_ARG;
+  }
+  pieces.assign(coef->n_pieces, Piece());
   for (int pc = 0; pc < coef->n_pieces; ++pc) {
     Piece& q = pieces[pc];
     q.mu.assign(coef->mu + (size_t)pc * M, coef->mu + (size_t)(pc + 1) * M);
@@ -208,7 +220,7 @@ sg_status build_host_problem(const sg_mesh* mesh, int k, int r, int n_slabs, dou
     if (coef->cell_scale && coef->cell_scale[pc])
       q.scale.assign(coef->cell_scale[pc], coef->cell_scale[pc] + n_cells);
   }
-  return build_host_problem_pieces(mesh, k, r, n_slabs, T, M, p, pieces, hp, msg);
+  return SG_OK;
 }
 
 sg_status build_host_problem_pieces(const sg_mesh* mesh, int k, int r, int n_slabs, double T,
@@ -310,7 +322,16 @@ sg_status build_host_problem_pieces(const sg_mesh* mesh, int k, int r, int n_sla
       hp.Dhat[q * nq + n] = lagrange_deriv(g.x, n, g.x[q]);
       hp.dS[q * nq + n] = lagrange_deriv(gll, n, g.x[q]);
     }
+  return fill_ctab(hp, msg);
+}
+
+sg_status fill_ctab(HostProblem& hp, std::string& msg) {
   // coefficient values at the tensor Gauss points of every cell, times w_q |J|
+  const int nq = hp.k + 1;
+  Rule1D g = gauss_legendre(nq);
+  const std::vector<Piece>& pieces = hp.pieces;
+  const std::vector<int>& piece_term = hp.piece_term;
+  const int n_pieces = (int)pieces.size();
   const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
   double detJ = 1.0;
   for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];

@@ -60,6 +60,20 @@ def config_2d_q2_128(seed=128):
                 coef=linear_sine_coef(4, 2, 0.05, [(m, m) for m in range(1, 5)], a0_cells=a0))
 
 
+def config_adjoint_2d(cells=(4, 4), k=1, r=1, n_slabs=3, M=2, P=2, seed=None):
+    """A small coefficient-gradient case: a = a0(x) + 0.2 x^2 + 0.1 xi_1
+    sin(pi x) + 0.1 xi_2 sin(pi y) on the unit square, a0 a per-cell field
+    (all ones, or seeded in [0.8, 1.2] when ``seed`` is given); four pieces,
+    the first two on the mean term.  The manufactured forcing in strong form
+    is only defined for a smooth coefficient, hence the default of ones."""
+    n_cells = int(np.prod(cells))
+    a0 = np.ones(n_cells) if seed is None else np.random.default_rng(seed).uniform(0.8, 1.2, n_cells)
+    coef = linear_sine_coef(M, 2, 0.1, [(1, 0), (0, 1)] + [(1, 1)] * (M - 2), a0_cells=a0)
+    coef.insert(1, dict(mu=(0,) * M, amp=0.2, factors=[("pow", 2), ("one", 0)], cell_scale=None))
+    return dict(name=f"2d-q{k}-{cells[0]}x{cells[1]}-dG{r}-adjoint", dim=2, cells=tuple(cells), lo=(0.0, 0.0),
+                hi=(1.0, 1.0), k=k, r=r, n_slabs=n_slabs, T=1.0, M=M, P=P, coef=coef)
+
+
 def scaled(spec, cells, name=None):
     """The same problem on another mesh (per-cell fields are redrawn)."""
     s = dict(spec)

@@ -35,9 +35,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FLOP_PER_UNKNOWN = 166.0
 BYTES_PER_UNKNOWN = 16.0
 L2_BYTES = 135_528_448
-# dram__bytes_read.sum + dram__bytes_write.sum of one tile-kernel launch on this
-# workload (ncu capture summarised in profiles/); None once the kernel changes
-NCU_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP64 chunk-kernel launch on
+# this workload (ncu capture summarised in profiles/); None once the kernel changes
+NCU_TRAFFIC_BYTES = 19_879_168 + 0
 
 
 def workload():
@@ -352,6 +352,208 @@ def run_ours(args, world, rank, local):
     ctx.destroy()
 
 
+# ---------------------------------------------------------------- NEXT rows
+# ``--suite next`` measures the solver-side rows on their own workloads and
+# prints one JSON line per row: the mixed-precision 3D solve, batched
+# Monte-Carlo against SG on the same GPU, and the adjoint gradient.
+
+def exact_for(sg, M, q, dim, eta=0.35, T=(0.0, 1.0, 1.0)):
+    """Manufactured finite-chaos solution: c_alpha = eta^|alpha|,
+    Phi_alpha = prod_d sin(pi f x_d) with f = 1 + (alpha_{d mod M} mod 2),
+    T(t) polynomial; Lambda_q in the library's order."""
+    tiny = sg.sg_setup(dict(dim=2, cells=(2, 2), lo=(0.0, 0.0), hi=(1.0, 1.0)), 1, 0, 1, 1.0, M, q,
+                       [dict(mu=(0,) * M, amp=1.0, factors=[("one", 0), ("one", 0)])])
+    idx = sg.sg_get_multi_indices(tiny)
+    tiny.destroy()
+    c = [eta ** int(sum(a)) for a in idx]
+    freq = [[1 + int(a[d % M]) % 2 for d in range(dim)] for a in idx]
+    return {"q": q, "c": c, "freq": freq, "T": list(T)}
+
+
+def march(sg, torch, ctx, rtol, slabs=None):
+    """Slab marching with the manufactured right-hand sides; returns the last
+    slab, total device-synchronised wall ms and per-slab iteration counts."""
+    n = ctx.info["n_unknowns"]
+    slabs = ctx.info["n_slabs"] if slabs is None else slabs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rhs = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.zeros(n, dtype=torch.float64, device=dev)
+    u_prev = torch.zeros_like(u)
+    its = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(slabs):
+        sg.sg_rhs(ctx, s, u_prev if s else None, rhs)
+        st = sg.sg_solve_slab(ctx, s, rhs, u, rtol=rtol)
+        its.append(st["iterations"])
+        u_prev.copy_(u)
+    torch.cuda.synchronize()
+    return u, 1e3 * (time.perf_counter() - t0), its
+
+
+def next_mixed_precision(sg, torch, inputs):
+    """Mixed-precision solve on the 3D 32^3 Q2, M=3 / P=3 workload: FP64
+    V-cycle vs FP32 V-cycle (FP64 FGMRES, Arnoldi and residual), marching all
+    20 slabs to a 1e-8 relative residual per slab."""
+    spec = inputs.config_3d_q2_32()
+    exact = exact_for(sg, spec["M"], 2, 3)
+    out, ref = {}, None
+    for name, ap, mp in (("fp64", sg.SG_PREC_FP64, sg.SG_PREC_FP64),
+                         ("fp32_mg", sg.SG_PREC_FP64, sg.SG_PREC_FP32),
+                         ("fp32_mg_dw_apply", sg.SG_PREC_DW, sg.SG_PREC_FP32)):
+        ctx = sg.sg_setup_spec(spec, ap)
+        sg.sg_autotune(ctx, reps=3)
+        sg.sg_set_exact(ctx, exact)
+        t0 = time.perf_counter()
+        sg.sg_mg_setup(ctx, mp)
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        march(sg, torch, ctx, 1e-8, slabs=1)                     # warm-up: graphs, workspaces
+        u, ms, its = march(sg, torch, ctx, 1e-8)
+        err = sg.sg_qoi_errors(ctx, u, spec["n_slabs"] - 1)
+        if ref is None:
+            ref = u.clone()
+        diff = float((u - ref).abs().max() / ref.abs().max())
+        out[name] = {"march_ms": ms, "ms_per_slab": ms / spec["n_slabs"], "mg_setup_ms": setup_ms,
+                     "iterations_mean": sum(its) / len(its), "iterations_max": max(its),
+                     "max_rel_diff_vs_fp64": diff,
+                     "qoi_errors_T": err}
+        ctx.destroy()
+        del u
+        torch.cuda.empty_cache()
+    for k in out:
+        out[k]["time_ratio_vs_fp64"] = out[k]["march_ms"] / out["fp64"]["march_ms"]
+    return {"row": "mixed precision", "workload": spec["name"], "unknowns_per_slab": inputs.n_unknowns(spec),
+            "slabs": spec["n_slabs"], "rtol": 1e-8, "exact": "finite chaos q=2, eta=0.35, T(t)=t+t^2",
+            "splits": out}
+
+
+def next_mc_vs_sg(sg, torch, inputs, n_samples=4096, batch=256):
+    """Batched Monte-Carlo against SG on the same GPU: the coefficient of the
+    64x64 Q2 workload, dG(1), 50 slabs to t = 1; half the samples on 64x64,
+    half on 128x128; errors of the mean and variance at t = 1 against the
+    manufactured solution's exact statistics."""
+    import numpy as np
+    base = dict(inputs.config_2d_q2_64(), n_slabs=50)
+    exact = exact_for(sg, 4, 2, 2)
+    xi = np.random.default_rng(4096).standard_normal((n_samples, 4))
+    half = n_samples // 2
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = {}
+    for mesh, sl in (("64x64", slice(0, half)), ("128x128", slice(half, n_samples))):
+        spec = dict(base, cells=(64, 64) if mesh == "64x64" else (128, 128))
+        # Monte-Carlo
+        ctx = sg.sg_setup_spec(dict(spec, P=0))
+        sg.sg_set_exact(ctx, exact)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mean, var, _, st = sg.mc_solve_batch(ctx, xi[sl], batch=batch, mg_precision=sg.SG_PREC_FP32, rtol=1e-8)
+        torch.cuda.synchronize()
+        mc_ms = 1e3 * (time.perf_counter() - t0)
+        e_mc = sg.sg_stat_errors(ctx, mean, var, 1.0)
+        ctx.destroy()
+        # stochastic Galerkin, P = 3 (35 modes), FP32 V-cycle
+        ctx = sg.sg_setup_spec(spec)
+        sg.sg_autotune(ctx, reps=3)
+        sg.sg_set_exact(ctx, exact)
+        sg.sg_mg_setup(ctx, sg.SG_PREC_FP32)
+        march(sg, torch, ctx, 1e-8, slabs=1)
+        u, sg_ms, its = march(sg, torch, ctx, 1e-8)
+        m = torch.empty(ctx.info["n_x"], dtype=torch.float64, device=dev)
+        v = torch.empty_like(m)
+        sg.sg_moments(ctx, u, ctx.info["n_t"] - 1, m, v)
+        e_sg = sg.sg_stat_errors(ctx, m, v, 1.0)
+        ctx.destroy()
+        rows[mesh] = {"mc": {"samples": int(sl.stop - sl.start), "batch": batch, "ms": mc_ms,
+                             "fgmres_iterations_total": st["total_iterations"],
+                             "error_mean_L2": e_mc["mean"], "error_var_L2": e_mc["var"]},
+                      "sg": {"chaos_modes": 35, "ms": sg_ms, "iterations_mean": sum(its) / len(its),
+                             "error_mean_L2": e_sg["mean"], "error_var_L2": e_sg["var"]},
+                      "sg_faster": sg_ms < mc_ms,
+                      "sg_more_accurate": e_sg["mean"] < e_mc["mean"] and e_sg["var"] < e_mc["var"]}
+        torch.cuda.empty_cache()
+    return {"row": "batched Monte-Carlo vs SG", "slabs": 50, "samples": n_samples,
+            "xi": "default_rng(4096).standard_normal((4096, 4))", "rtol": 1e-8, "meshes": rows}
+
+
+def next_adjoint(sg, torch, inputs, fd_rel_step=1e-6):
+    """Adjoint gradient on the 128x128 Q2, M=4 / P=4 workload (70 modes,
+    50 slabs): J = E ||u(T)||^2, dJ/d(sigma_m) and dJ/d(a0 per cell),
+    checkpoints every 10 slabs; central differences for sigma_1 and one cell."""
+    import numpy as np
+    spec = inputs.config_2d_q2_128()
+    exact = exact_for(sg, 4, 2, 2)
+    ctx = sg.sg_setup_spec(spec)
+    sg.sg_autotune(ctx, reps=3)
+    sg.sg_set_exact(ctx, exact)
+    sg.sg_mg_setup(ctx, sg.SG_PREC_FP32)
+    rtol = 1e-11
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, g_amp, g_cell, st = sg.sg_adjoint_gradient(ctx, rtol=rtol, checkpoint_every=10, cell_piece=0)
+    grad_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    J_fwd = sg.sg_adjoint_gradient(ctx, rtol=rtol, checkpoint_every=10, gradient=False)[0]
+    fwd_ms = 1e3 * (time.perf_counter() - t0)
+    coef = [dict(p) for p in spec["coef"]]
+    fd = {}
+    # sigma_1 (piece 1) and the a0 value of the centre cell (piece 0)
+    c_mid = (spec["cells"][1] // 2) * spec["cells"][0] + spec["cells"][0] // 2
+    for name, kind in (("sigma_1", 1), (f"a0_cell_{c_mid}", 0)):
+        vals = []
+        for sgn in (1.0, -1.0):
+            pc = [dict(p) for p in coef]
+            if kind == 1:
+                h = fd_rel_step * pc[1]["amp"]
+                pc[1]["amp"] = pc[1]["amp"] + sgn * h
+            else:
+                cs = np.array(pc[0]["cell_scale"], dtype=np.float64)
+                h = fd_rel_step * cs[c_mid]
+                cs[c_mid] += sgn * h
+                pc[0]["cell_scale"] = cs
+            sg.sg_set_coefficient(ctx, pc)
+            vals.append(sg.sg_adjoint_gradient(ctx, rtol=rtol, checkpoint_every=10, gradient=False)[0])
+        fdv = (vals[0] - vals[1]) / (2 * h)
+        adj = float(g_amp[1]) if kind == 1 else float(g_cell[c_mid])
+        fd[name] = {"adjoint": adj, "central_difference": fdv, "rel_diff": abs(adj - fdv) / abs(fdv)}
+    sg.sg_set_coefficient(ctx, coef)
+    ctx.destroy()
+    return {"row": "adjoint gradient", "workload": spec["name"], "unknowns_per_slab": inputs.n_unknowns(spec),
+            "slabs": spec["n_slabs"], "checkpoint_every": 10, "rtol": rtol, "mg": "fp32 V-cycle, fp64 FGMRES",
+            "J": J, "J_forward_only": J_fwd, "grad_ms": grad_ms, "forward_only_ms": fwd_ms,
+            "grad_over_forward": grad_ms / fwd_ms, "forward_solves": st["forward_solves"],
+            "adjoint_solves": st["adjoint_solves"], "max_iterations": st["max_iterations"],
+            "grad_sigma": [float(v) for v in g_amp[1:]], "grad_a0_norm": float(np.linalg.norm(g_cell)),
+            "fd_relative_step": fd_rel_step, "fd_checks": fd}
+
+
+def run_next(args, world, rank, local):
+    import torch
+    import paper_2605_21046_gb300 as sg
+    from paper_2605_21046_gb300 import build, inputs
+    build.build()
+    torch.cuda.set_device(torch.device("cuda", local))
+    if rank != 0:
+        return
+    rows = [s.strip() for s in args.rows.split(",")]
+    for row in rows:
+        t0 = time.perf_counter()
+        try:
+            if row == "mixed":
+                out = next_mixed_precision(sg, torch, inputs)
+            elif row == "mc":
+                out = next_mc_vs_sg(sg, torch, inputs, n_samples=args.mc_samples)
+            elif row == "adjoint":
+                out = next_adjoint(sg, torch, inputs)
+            else:
+                raise ValueError(row)
+        except sg.SGError as ex:
+            out = {"row": row, "error": str(ex)}
+            torch.cuda.empty_cache()
+        out.update({"suite": "next", "impl": "ours", "wall_s": time.perf_counter() - t0,
+                    "gpu": torch.cuda.get_device_name()})
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,11 +565,17 @@ def main():
     ap.add_argument("--no-dw", action="store_true", help="skip the double-word variant")
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--suite", choices=["apply", "next"], default="apply",
+                    help="apply: the headline line; next: one line per solver-side row")
+    ap.add_argument("--rows", default="mixed,mc,adjoint", help="rows of --suite next")
+    ap.add_argument("--mc-samples", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.suite == "next":
+        run_next(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -278,7 +278,8 @@ sg_status sg_solve_slab_adjoint(sg_ctx* ctx, int slab, const double* rhs, double
  *   J                 HOST double out (may be NULL)
  *   grad_amp          HOST n_pieces doubles out (may be NULL)
  *   grad_cell         HOST n_cells doubles out (NULL allowed; ignored if
- *                     cell_piece < 0)
+ *                     cell_piece < 0).  With grad_amp and grad_cell both
+ *                     NULL only the forward sweep runs (J alone).
  *   st                statistics out (may be NULL)
  * Needs sg_set_exact and sg_mg_setup; the Dirichlet data of the manufactured
  * solution are zero, so J covers all nodes.  At most 16 coefficient terms.
@@ -352,6 +353,15 @@ sg_status sg_moments(sg_ctx* ctx, const double* u, int time_node, double* mean, 
  * solution; err: HOST array of 3 doubles (mean, variance, full).  Needs
  * sg_set_exact.  Synchronous (evaluated on the host, post-processing). */
 sg_status sg_qoi_errors(sg_ctx* ctx, const double* u, int slab, double* err);
+
+/* sg_stat_errors - L2(D) errors of a nodal mean field and a nodal variance
+ * field (Q_k functions on the context's mesh, e.g. the output of sg_moments or
+ * of mc_solve_batch) against the exact mean and variance of the manufactured
+ * solution at time t (eqs. qoi-mean-chaos / qoi-variance-chaos applied to the
+ * exact chaos coefficients).  mean, var: DEVICE n_x doubles; err: HOST array
+ * of 2 doubles (mean, variance).  (k+4)^d Gauss points per cell.  Needs
+ * sg_set_exact.  Synchronous (host post-processing). */
+sg_status sg_stat_errors(sg_ctx* ctx, const double* mean, const double* var, double t, double* err);
 
 /* mc_solve_batch - Monte-Carlo estimate of the mean and variance at t = T
  * (Sec. 5: the pathwise problem and its slab system eq. mc-slab-system, the

@@ -235,21 +235,24 @@ def sg_solve_slab_adjoint(ctx, slab, rhs, x, rtol=1e-8, max_it=500, restart=30, 
     return out
 
 
-def sg_adjoint_gradient(ctx, rtol=1e-10, max_it=500, checkpoint_every=10, cell_piece=-1, stream=None):
+def sg_adjoint_gradient(ctx, rtol=1e-10, max_it=500, checkpoint_every=10, cell_piece=-1, stream=None,
+                        gradient=True):
     """J = E ||u_h(T)||^2 of the marched manufactured problem and its gradient
     with respect to every piece amplitude and (cell_piece >= 0) the per-cell
-    scale of one piece.  Returns (J, grad_amp, grad_cell or None, stats)."""
+    scale of one piece.  Returns (J, grad_amp, grad_cell or None, stats);
+    ``gradient=False`` runs the forward sweep only (grads None)."""
     n_pieces = ctx.n_pieces
-    g_amp = np.zeros(max(n_pieces, 1), dtype=np.float64)
-    g_cell = np.zeros(ctx.info["n_cells"], dtype=np.float64) if cell_piece >= 0 else None
+    g_amp = np.zeros(max(n_pieces, 1), dtype=np.float64) if gradient else None
+    g_cell = np.zeros(ctx.info["n_cells"], dtype=np.float64) if (cell_piece >= 0 and gradient) else None
     J = C.c_double(0.0)
     st = _abi.sg_adjoint_stats()
     _check(_abi.load().sg_adjoint_gradient(
         ctx.handle, float(rtol), int(max_it), int(checkpoint_every), int(cell_piece), C.byref(J),
-        g_amp.ctypes.data_as(C.POINTER(C.c_double)),
+        g_amp.ctypes.data_as(C.POINTER(C.c_double)) if g_amp is not None else None,
         g_cell.ctypes.data_as(C.POINTER(C.c_double)) if g_cell is not None else None,
         C.byref(st), C.c_void_p(_stream_handle(stream))), "sg_adjoint_gradient")
-    return J.value, g_amp[:n_pieces], g_cell, {name: getattr(st, name) for name, _ in _abi.sg_adjoint_stats._fields_}
+    stats = {name: getattr(st, name) for name, _ in _abi.sg_adjoint_stats._fields_}
+    return J.value, (g_amp[:n_pieces] if g_amp is not None else None), g_cell, stats
 
 
 def sg_set_coefficient(ctx, coef):
@@ -360,6 +363,23 @@ def sg_qoi_errors(ctx, u, slab):
     err = (C.c_double * 3)()
     _check(_abi.load().sg_qoi_errors(ctx.handle, C.c_void_p(u.data_ptr()), int(slab), err), "sg_qoi_errors")
     return {"mean": err[0], "var": err[1], "full": err[2]}
+
+
+def sg_stat_errors(ctx, mean, var, t):
+    """L2(D) errors (mean, variance) of nodal fields against the manufactured
+    solution's exact statistics at time t."""
+    _check_vec_n(ctx, mean, var)
+    err = (C.c_double * 2)()
+    _check(_abi.load().sg_stat_errors(ctx.handle, C.c_void_p(mean.data_ptr()), C.c_void_p(var.data_ptr()),
+                                      float(t), err), "sg_stat_errors")
+    return {"mean": err[0], "var": err[1]}
+
+
+def _check_vec_n(ctx, *ts):
+    n = ctx.info["n_x"]
+    for t in ts:
+        if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.numel() == n and t.is_contiguous()):
+            raise ValueError(f"wants contiguous float64 CUDA tensors of {n} elements")
 
 
 def mc_solve_batch(ctx, xi, batch=256, mg_precision=SG_PREC_FP32, rtol=1e-8, max_it=500, keep_paths=False,

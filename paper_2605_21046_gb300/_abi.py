@@ -15,7 +15,8 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_destroy", "sg_status_string", "sg_last_error", "sg_mg_setup", "sg_vcycle",
                    "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
                    "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch",
-                   "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient"])
+                   "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient",
+                   "sg_stat_errors"])
 
 
 class sg_mesh(C.Structure):
@@ -105,6 +106,8 @@ def load():
     lib.sg_adjoint_gradient.restype = C.c_int
     lib.sg_set_coefficient.argtypes = [vp, C.POINTER(sg_coeff)]
     lib.sg_set_coefficient.restype = C.c_int
+    lib.sg_stat_errors.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_double)]
+    lib.sg_stat_errors.restype = C.c_int
     lib.sg_autotune.argtypes = [vp, C.c_int]
     lib.sg_autotune.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]

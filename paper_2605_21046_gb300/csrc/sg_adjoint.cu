@@ -380,7 +380,9 @@ sg_status adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int K, int cell
   int n_sm = 152;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, 0);
   const int bgrid = (int)std::min<long long>((long long)n_sm * 2, hp.n_cells);
-  for (int seg = n_ck - 1; seg >= 0 && e == cudaSuccess && status == SG_OK; --seg) {
+  // J alone (no gradient asked): no backward sweep
+  const bool want_grad = g_amp || (g_cell && cell_piece >= 0);
+  for (int seg = n_ck - 1; want_grad && seg >= 0 && e == cudaSuccess && status == SG_OK; --seg) {
     const int s0 = seg * K, s1 = std::min(N, s0 + K);
     // recompute the segment's forward states into d_seg[0 .. s1 - s0) (the
     // last segment is still there from the forward sweep)

@@ -1,6 +1,7 @@
 // The extern "C" entry points of libsg declared in include/sg.h.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -460,6 +461,19 @@ sg_status sg_qoi_errors(sg_ctx* ctx, const double* u, int slab, double* err) {
   std::string msg;
   sg_status st = sg::exact_errors(ctx->hp, *ctx->exact, u, slab, err, msg);
   if (st != SG_OK) return fail(st, "sg_qoi_errors: " + msg);
+  return SG_OK;
+}
+
+sg_status sg_stat_errors(sg_ctx* ctx, const double* mean, const double* var, double t, double* err) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_stat_errors: ctx is NULL");
+  if (!ctx->exact) return fail(SG_ERR_ARG, "sg_stat_errors: call sg_set_exact first");
+  if (!mean || !var || !is_device_ptr(mean) || !is_device_ptr(var) || !err)
+    return fail(SG_ERR_ARG, "sg_stat_errors: bad pointer");
+  if (!(t >= 0.0) || !std::isfinite(t)) return fail(SG_ERR_ARG, "sg_stat_errors: t out of range");
+  cudaDeviceSynchronize();
+  std::string msg;
+  sg_status st = sg::stat_errors(ctx->hp, *ctx->exact, mean, var, t, err, msg);
+  if (st != SG_OK) return fail(st, "sg_stat_errors: " + msg);
   return SG_OK;
 }
 

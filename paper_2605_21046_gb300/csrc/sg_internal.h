@@ -227,6 +227,8 @@ cudaError_t exact_rhs(const HostProblem& hp, const LaunchShape& ls, ExactData& E
 cudaError_t moments(const HostProblem& hp, const double* u, int node, double* mean, double* var, cudaStream_t s);
 sg_status exact_errors(const HostProblem& hp, const ExactData& E, const double* u_dev, int slab, double err[3],
                        std::string& msg);
+sg_status stat_errors(const HostProblem& hp, const ExactData& E, const double* mean_dev, const double* var_dev,
+                      double t, double err[2], std::string& msg);
 // Records the message sg_last_error() returns on this thread.
 void set_last_error(const std::string& msg);
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,

@@ -402,4 +402,73 @@ sg_status exact_errors(const HostProblem& hp, const ExactData& E, const double* 
   return SG_OK;
 }
 
+sg_status stat_errors(const HostProblem& hp, const ExactData& E, const double* mean_dev, const double* var_dev,
+                      double t, double err[2], std::string& msg) {
+  std::vector<double> Mh(hp.n_x), Vh(hp.n_x);
+  cudaError_t e = cudaMemcpy(Mh.data(), mean_dev, hp.n_x * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(Vh.data(), var_dev, hp.n_x * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { msg = cudaGetErrorString(e); return SG_ERR_CUDA; }
+  const double Tt = poly(E.t_coef, t);
+  const int nq_modes = (int)E.c.size();
+  const int n = hp.k + 1, nqs = hp.k + 4;
+  const int nkd = hp.dim == 2 ? n * n : n * n * n;
+  const int nqd = hp.dim == 2 ? nqs * nqs : nqs * nqs * nqs;
+  Rule1D g = gauss_legendre(nqs);
+  std::vector<double> gll = lobatto_nodes(hp.k);
+  std::vector<double> S1((size_t)nqs * n);
+  for (int qq = 0; qq < nqs; ++qq)
+    for (int j = 0; j < n; ++j) S1[qq * n + j] = lagrange(gll, j, g.x[qq]);
+  double detJ = 1.0;
+  for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];
+  int zero_q = -1;
+  for (int j = 0; j < nq_modes; ++j) {
+    bool z = true;
+    for (int m = 0; m < hp.M; ++m) z = z && E.idx_q[(size_t)j * hp.M + m] == 0;
+    if (z) zero_q = j;
+  }
+  double e_mean = 0.0, e_var = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : e_mean, e_var)
+  for (long long cell = 0; cell < hp.n_cells; ++cell) {
+    const int cc[3] = {(int)(cell % hp.cells[0]), (int)((cell / hp.cells[0]) % hp.cells[1]),
+                       (int)(cell / ((long long)hp.cells[0] * hp.cells[1]))};
+    long long gidx[64];
+    for (int a = 0; a < nkd; ++a) {
+      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+      long long gi = 0, stride = 1;
+      for (int d = 0; d < hp.dim; ++d) {
+        gi += (long long)(cc[d] * hp.k + ai[d]) * stride;
+        stride *= hp.nn[d];
+      }
+      gidx[a] = gi;
+    }
+    for (int qd = 0; qd < nqd; ++qd) {
+      const int qi[3] = {qd % nqs, (qd / nqs) % nqs, qd / (nqs * nqs)};
+      double x[3] = {0, 0, 0}, w = detJ;
+      for (int d = 0; d < hp.dim; ++d) {
+        x[d] = hp.lo[d] + (cc[d] + g.x[qi[d]]) * hp.h[d];
+        w *= g.w[qi[d]];
+      }
+      double mh = 0.0, vh = 0.0;
+      for (int a = 0; a < nkd; ++a) {
+        const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
+        double v = 1.0;
+        for (int d = 0; d < hp.dim; ++d) v *= S1[qi[d] * n + ai[d]];
+        mh += v * Mh[gidx[a]];
+        vh += v * Vh[gidx[a]];
+      }
+      double m_ex = 0.0, v_ex = 0.0;
+      for (int j = 0; j < nq_modes; ++j) {
+        const double ph = Tt * E.c[j] * phi_val(hp, &E.freq[(size_t)j * 3], x, nullptr);
+        if (j == zero_q) m_ex = ph;
+        else v_ex += ph * ph;
+      }
+      e_mean += w * (mh - m_ex) * (mh - m_ex);
+      e_var += w * (vh - v_ex) * (vh - v_ex);
+    }
+  }
+  err[0] = std::sqrt(e_mean);
+  err[1] = std::sqrt(e_var);
+  return SG_OK;
+}
+
 }  // namespace sg

@@ -91,6 +91,11 @@ def test_checkpoint_spacing_does_not_change_the_result(cuda):
         assert np.abs(g2 - g).max() <= 1e-10 * np.abs(g).max()
         assert np.abs(c2 - c).max() <= 1e-10 * np.abs(c).max()
     assert out[0][3]["checkpoints"] == 6 and out[3][3]["checkpoints"] == 0
+    ctx = _ctx(spec, exact)
+    J1, g1, c1, st1 = sg.sg_adjoint_gradient(ctx, rtol=1e-13, checkpoint_every=3, cell_piece=2, gradient=False)
+    ctx.destroy()
+    assert g1 is None and c1 is None and st1["adjoint_solves"] == 0 and st1["forward_solves"] == 7
+    assert abs(J1 - J) <= 1e-11 * J
 
 
 def test_set_coefficient_keeps_the_load_vector(cuda):

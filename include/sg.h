@@ -77,9 +77,13 @@ enum { SG_F_ONE = 0, SG_F_SIN = 1, SG_F_POW = 2 };
  *                 significant bits.  Inputs and outputs stay double.  Inputs
  *                 with magnitude below 2^-74 keep only 24 significant bits.
  *                 Meets the 1e-12 relative apply tolerance of the FP64 path.
- *   SG_PREC_FP32  native single precision; accepted by sg_mg_setup only (the
- *                 multigrid preconditioner inside the FP64 outer FGMRES). */
-enum { SG_PREC_FP64 = 0, SG_PREC_DW = 1, SG_PREC_FP32 = 2 };
+ *   SG_PREC_FP32  native single precision; accepted by sg_mg_setup and
+ *                 mc_solve_batch only (the multigrid preconditioner inside the
+ *                 FP64 outer FGMRES).
+ *   SG_PREC_BF16  as SG_PREC_FP32, with the Vanka patch inverses stored in
+ *                 bfloat16 (rounded to nearest from FP32) and applied in FP32:
+ *                 half the factor bytes of the FP32 V-cycle. */
+enum { SG_PREC_FP64 = 0, SG_PREC_DW = 1, SG_PREC_FP32 = 2, SG_PREC_BF16 = 3 };
 
 /* Uniform Cartesian mesh of [lo, hi] (dim = 2 or 3; entries beyond dim are
  * ignored).  cells[d] >= 1 cells in direction d. */
@@ -207,8 +211,9 @@ sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_h
  * counts are even and > 2; the coarsest block is inverted densely (at most
  * 2048 interior unknowns per mode, else SG_ERR_UNSUPPORTED).  Vanka patches
  * are one cell's interior nodes x all time nodes, inverted exactly.
- *   mg_precision  SG_PREC_FP64 or SG_PREC_FP32 (vectors, patch inverses,
- *                 transfers and coarse solve; the outer solver stays FP64)
+ *   mg_precision  SG_PREC_FP64, SG_PREC_FP32 (vectors, patch inverses,
+ *                 transfers and coarse solve; the outer solver stays FP64) or
+ *                 SG_PREC_BF16 (FP32 with bfloat16-stored patch inverses)
  *   nu            smoothing steps before and after the coarse correction (>= 1)
  *   omega         Vanka damping (0 < omega <= 1)
  * Allocates device memory owned by the context (replaces an earlier set-up).
@@ -374,7 +379,7 @@ sg_status sg_stat_errors(sg_ctx* ctx, const double* mean, const double* var, dou
  * the batch to rtol with a mean-operator V-cycle as preconditioner.
  *   xi        HOST n_samples x M standard-normal samples
  *   batch     samples per batch, 1..512
- *   mg_precision  SG_PREC_FP64 or SG_PREC_FP32 V-cycle
+ *   mg_precision  SG_PREC_FP64, SG_PREC_FP32 or SG_PREC_BF16 V-cycle
  *   mean_T, var_T  DEVICE n_x doubles out: nodal sample mean and unbiased
  *             sample variance of u(x, T)
  *   u_T       DEVICE n_samples x N_t x n_x doubles out (last slab of every

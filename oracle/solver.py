@@ -74,12 +74,24 @@ def diagonal_classes(G):
     return keys, cls.reshape(-1)
 
 
+def round_bf16(a):
+    """Each value rounded to float32, then to the nearest bfloat16 (ties to
+    even): the 16 high bits of the float32 pattern after adding 0x7FFF plus
+    the lowest kept bit.  Finite inputs only."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(a))
+
+
 class Level:
     """One multigrid level: the block operators A_alpha (one per diagonal
     class), their Vanka patch inverses, and the prolongation from the next
-    coarser level."""
+    coarser level.  ``factor_round`` (e.g. ``round_bf16``) is applied to the
+    patch inverses after they are computed (the coarsest solve is exact)."""
 
-    def __init__(self, spec, At, Bt, keys, coarsest):
+    def __init__(self, spec, At, Bt, keys, coarsest, factor_round=None):
+        self.factor_round = factor_round
         self.mesh = space_fe.Mesh(spec["dim"], spec["cells"], spec["lo"], spec["hi"], spec["k"])
         self.bmask = self.mesh.boundary_mask()
         self.n_t = At.shape[0]
@@ -115,7 +127,8 @@ class Level:
         for A in self.A:
             inv = []
             for dofs in self.patches:
-                inv.append(np.linalg.inv(A[dofs][:, dofs].toarray()) if dofs.size else np.zeros((0, 0)))
+                m = np.linalg.inv(A[dofs][:, dofs].toarray()) if dofs.size else np.zeros((0, 0))
+                inv.append(self.factor_round(m) if self.factor_round is not None else m)
             self.patch_inv.append(inv)
 
     def smooth(self, cls, x, b):
@@ -171,11 +184,11 @@ class Multigrid:
     """Block-Jacobi (in alpha) preconditioner: one V-cycle of the diagonal
     block A_alpha for every chaos mode and both time nodes at once."""
 
-    def __init__(self, problem):
+    def __init__(self, problem, factor_round=None):
         self.p = problem
         specs = coarse_specs(problem.spec)
         self.keys, self.cls = diagonal_classes(problem.G)
-        self.levels = [Level(s, problem.At, problem.Bt, self.keys, i == len(specs) - 1)
+        self.levels = [Level(s, problem.At, problem.Bt, self.keys, i == len(specs) - 1, factor_round)
                        for i, s in enumerate(specs)]
         self.P = [prolongation(self.levels[i], self.levels[i + 1]) for i in range(len(self.levels) - 1)]
 

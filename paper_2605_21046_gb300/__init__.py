@@ -16,9 +16,10 @@ import numpy as np
 
 from . import _abi
 
-SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = _abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32
+SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32, SG_PREC_BF16 = (_abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32,
+                                                      _abi.SG_PREC_BF16)
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}

@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(PKG, "libsg.so")
 SG_OK, SG_ERR_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 SG_ERR_NOT_CONVERGED, SG_ERR_NONFINITE, SG_ERR_TIMEOUT = 5, 6, 7
 SG_F_ONE, SG_F_SIN, SG_F_POW = 0, 1, 2
-SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32 = 0, 1, 2
+SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32, SG_PREC_BF16 = 0, 1, 2, 3
 
 # every symbol include/sg.h declares
 EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_get_multi_indices",

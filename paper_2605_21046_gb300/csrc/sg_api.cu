@@ -220,8 +220,8 @@ sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_h
 
 sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega) {
   if (!ctx) return fail(SG_ERR_ARG, "sg_mg_setup: ctx is NULL");
-  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32)
-    return fail(SG_ERR_UNSUPPORTED, "sg_mg_setup: precision must be SG_PREC_FP64 or SG_PREC_FP32");
+  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32 && mg_precision != SG_PREC_BF16)
+    return fail(SG_ERR_UNSUPPORTED, "sg_mg_setup: precision must be SG_PREC_FP64, SG_PREC_FP32 or SG_PREC_BF16");
   if (nu < 1 || nu > 16 || !(omega > 0.0 && omega <= 1.0)) return fail(SG_ERR_ARG, "sg_mg_setup: nu or omega out of range");
   cudaDeviceSynchronize();
   if (ctx->mg) {
@@ -271,7 +271,7 @@ sg_status sg_set_coefficient(sg_ctx* ctx, const sg_coeff* coef) {
   e = cudaMemcpy(ctx->d_ctab, hp.ctab.data(), hp.ctab.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "sg_set_coefficient: upload");
   if (ctx->mg) {
-    const int prec = ctx->mg->precision, nu = ctx->mg->nu;
+    const int prec = ctx->mg->requested, nu = ctx->mg->nu;
     const double omega = ctx->mg->omega;
     return sg_mg_setup(ctx, prec, nu, omega);
   }
@@ -483,8 +483,8 @@ sg_status mc_solve_batch(sg_ctx* ctx, int n_samples, const double* xi, int batch
   if (!ctx->exact) return fail(SG_ERR_ARG, "mc_solve_batch: call sg_set_exact first");
   if (n_samples < 1 || !xi) return fail(SG_ERR_ARG, "mc_solve_batch: no samples");
   if (batch < 1 || batch > 512) return fail(SG_ERR_ARG, "mc_solve_batch: batch must be 1..512");
-  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32)
-    return fail(SG_ERR_ARG, "mc_solve_batch: mg_precision must be SG_PREC_FP64 or SG_PREC_FP32");
+  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32 && mg_precision != SG_PREC_BF16)
+    return fail(SG_ERR_ARG, "mc_solve_batch: mg_precision must be SG_PREC_FP64, SG_PREC_FP32 or SG_PREC_BF16");
   if (!(rtol > 0.0) || max_it < 1) return fail(SG_ERR_ARG, "mc_solve_batch: rtol or max_it out of range");
   if (!mean_T || !var_T || !is_device_ptr(mean_T) || !is_device_ptr(var_T) || mean_T == var_T)
     return fail(SG_ERR_ARG, "mc_solve_batch: mean_T and var_T must be distinct device vectors");

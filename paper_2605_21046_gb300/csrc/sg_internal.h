@@ -155,7 +155,9 @@ struct MGLevel {
   int* d_gterm = nullptr;
   double* d_gval = nullptr;
   int* d_perm = nullptr;
-  void* d_inv = nullptr;     // [class][cell][np][np] patch inverses, or coarsest [class][n_int][n_int]
+  void* d_inv = nullptr;     // [class][cell][np][pitch] patch inverses (pitch = np rounded up to 8;
+                             //  bf16 when MG::bf16), or coarsest [class][n_int][n_int]
+  int vanka_chunk = 0;       // cells per Vanka chunk
   int* d_inner = nullptr;    // coarsest: dof offset (i * n_x + node) of every interior dof
   void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
   void* d_b = nullptr;
@@ -171,7 +173,12 @@ struct MGLevel {
 };
 
 struct MG {
-  int precision = SG_PREC_FP64;   // SG_PREC_FP64 or kPrecF32
+  int precision = SG_PREC_FP64;   // vector precision: SG_PREC_FP64 or kPrecF32
+  int requested = SG_PREC_FP64;   // as passed to mg_build (SG_PREC_BF16 included)
+  bool bf16 = false;              // patch inverses stored in bf16 (FP32 vectors)
+  int n_blk = 0;                  // Vanka mode blocks (modes of one class)
+  int* d_blk_cls = nullptr;
+  int* d_blk_alpha = nullptr;
   int nu = 2;
   double omega = 0.7;
   int n_classes = 0;

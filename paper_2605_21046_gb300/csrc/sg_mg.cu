@@ -17,6 +17,7 @@
 // Dirichlet rows and columns removed), restriction P^T.  Coarsest level:
 // dense inverse of the interior block.  Dirichlet rows are the identity on
 // every level.  The whole V-cycle is captured once into a CUDA graph.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include "sg_internal.h"
 
@@ -57,58 +59,147 @@ __global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long
 }
 
 // Additive Vanka step: x += omega / mult * inv(patch) * r_patch for every
-// (cell, alpha).  One warp per (cell, 32 consecutive alpha): lanes share the
-// cell, so the patch inverse of a diagonal class is a broadcast load.
-template <typename T, int DIM, int K, int NT, bool TRANS>
-__global__ void mg_vanka(const T* __restrict__ r, T* __restrict__ x, const T* __restrict__ inv,
-                         const int* __restrict__ cls, int n_xi, long long n_x, long long n_cells,
-                         int cells0, int cells1, int nnx, int nny, int nnz, T omega) {
+// (cell, alpha), patch = the cell's nodes x all time nodes (Dirichlet rows
+// skipped), mult = number of cells that hold the node.
+//
+// A CTA takes a chunk of C cells that are consecutive in x and shares their
+// nodes: it gathers r on the chunk's node grid for all V vectors into shared
+// memory (coalesced along x), computes every patch product from there, sums
+// the corrections of neighbouring cells in shared memory, and writes x once:
+// a plain update for nodes that only this chunk holds, an atomic add for the
+// chunk's outer nodes.  One thread owns one patch row rho of one cell for a
+// block of up to VB modes of one diagonal class (modes are pre-sorted into
+// such blocks), so the inverse row is read once per block and the patch
+// values are shared-memory broadcasts.  Inverses are stored [class][cell][NP]
+// [NPP] in W (double, float or bf16; NPP = NP rounded up to 8).
+constexpr int kVankaVB = 8;
+
+template <typename T>
+struct VankaParams {
+  const T* r;
+  T* x;
+  const void* inv;
+  const int* blk_cls;       // [n_blk] class of every mode block
+  const int* blk_alpha;     // [n_blk][kVankaVB] modes, -1 padded
+  int n_blk, n_xi, chunk, npp;
+  long long n_x, n_cells;
+  int cells[3], nn[3];
+  T omega;
+};
+
+template <typename W>
+__device__ __forceinline__ float to_f(W w) { return (float)w; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
+
+template <typename T, typename W>
+__device__ __forceinline__ T wval(const W* p) { return (T)to_f<W>(*p); }
+template <>
+__device__ __forceinline__ double wval<double, double>(const double* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float wval<float, float>(const float* p) { return __ldg(p); }
+
+template <typename T, typename W, int DIM, int K, int NT, bool TRANS>
+__global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
   constexpr int N = K + 1;
   constexpr int NKD = DIM == 2 ? N * N : N * N * N;
   constexpr int NP = NT * NKD;
-  const int lane = threadIdx.x & 31;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int chunks = (n_xi + 31) / 32;
-  const long long cell = warp / chunks;
-  if (cell >= n_cells) return;
-  const int alpha = (int)(warp % chunks) * 32 + lane;
-  if (alpha >= n_xi) return;
-  const int cx = (int)(cell % cells0), cy = (int)((cell / cells0) % cells1), cz = (int)(cell / ((long long)cells0 * cells1));
-  long long node[NKD];
-  bool inner[NKD];
-  T rp[NP];
-#pragma unroll
-  for (int a = 0; a < NKD; ++a) {
-    const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
-    bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
-    if (DIM == 3) in = in && gz > 0 && gz < nnz - 1;
-    inner[a] = in;
-    node[a] = ((long long)gz * nny + gy) * nnx + gx;
-#pragma unroll
-    for (int i = 0; i < NT; ++i) rp[i * NKD + a] = in ? r[(long long)(alpha * NT + i) * n_x + node[a]] : T(0);
-  }
-  const T* M = inv + ((long long)cls[alpha] * n_cells + cell) * NP * NP;
-#pragma unroll
-  for (int i = 0; i < NT; ++i)
-#pragma unroll
-    for (int a = 0; a < NKD; ++a) {
-      if (!inner[a]) continue;
-      T z = T(0);
-      if constexpr (TRANS) {
-        // inverse of the transposed patch = transpose of the patch inverse
-#pragma unroll
-        for (int q = 0; q < NP; ++q) z += M[q * NP + i * NKD + a] * rp[q];
-      } else {
-        const T* row = M + (i * NKD + a) * NP;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) z += row[q] * rp[q];
+  constexpr int VB = kVankaVB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int V = p.n_xi * NT, C = p.chunk;
+  const int LX = C * K + 1;                         // chunk nodes along x
+  constexpr int LYZ = DIM == 2 ? N : N * N;         // nodes across y (and z)
+  const int LN = LX * LYZ;
+  T* Rl = reinterpret_cast<T*>(smem_raw);           // [V][LN]
+  T* Zc = Rl + (size_t)V * LN;                      // [V][LN]
+  const W* inv = static_cast<const W*>(p.inv);
+  const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
+  const int cpr = (p.cells[0] + C - 1) / C;         // chunks per row of cells
+  const long long n_chunks = (long long)cpr * p.cells[1] * p.cells[2];
+  for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const int cx0 = (int)(ch % cpr) * C;
+    const long long row = ch / cpr;
+    const int cy = (int)(row % p.cells[1]), cz = (int)(row / p.cells[1]);
+    const int nc = min(C, p.cells[0] - cx0);
+    const int lxn = nc * K + 1;
+    __syncthreads();
+    // gather r on the chunk's node grid; clear the corrections
+    for (int idx = tid; idx < V * LN; idx += nthr) {
+      const int v = idx / LN, ln = idx - v * LN;
+      const int lx = ln % LX, lyz = ln / LX;
+      T val = T(0);
+      if (lx < lxn) {
+        const int gx = cx0 * K + lx, gy = cy * K + lyz % N, gz = DIM == 3 ? cz * K + lyz / N : 0;
+        bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+        if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
+        if (in) val = p.r[(long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx];
       }
-      const long long g = node[a];
-      const int gx = (int)(g % nnx), gy = (int)((g / nnx) % nny), gz = (int)(g / ((long long)nnx * nny));
-      int mult = (gx % K == 0 ? 2 : 1) * (gy % K == 0 ? 2 : 1);
-      if (DIM == 3) mult *= (gz % K == 0 ? 2 : 1);
-      atomicAdd(x + (long long)(alpha * NT + i) * n_x + g, omega * z / T(mult));
+      Rl[idx] = val;
+      Zc[idx] = T(0);
     }
+    __syncthreads();
+    // patch rows
+    const int items = nc * NP * p.n_blk;
+    for (int it = tid; it < items; it += nthr) {
+      const int rho = it % NP;
+      const int cb = it / NP;
+      const int c = cb % nc, b = cb / nc;
+      const int i = rho / NKD, a = rho - i * NKD;
+      const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
+      const int gx = (cx0 + c) * K + ax, gy = cy * K + ay, gz = DIM == 3 ? cz * K + az : 0;
+      bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+      if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
+      if (!in) continue;
+      const long long cell = ((long long)cz * p.cells[1] + cy) * p.cells[0] + cx0 + c;
+      const W* M = inv + ((long long)p.blk_cls[b] * p.n_cells + cell) * NP * p.npp;
+      int al[VB];
+#pragma unroll
+      for (int u = 0; u < VB; ++u) al[u] = p.blk_alpha[b * VB + u];
+      T acc[VB];
+#pragma unroll
+      for (int u = 0; u < VB; ++u) acc[u] = T(0);
+      const int lbase = c * K;                       // local x of the cell's first node
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const int iq = q / NKD, aq = q - iq * NKD;
+        const int ln = (lbase + aq % N) + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
+        const T w = TRANS ? wval<T, W>(M + (size_t)q * p.npp + rho) : wval<T, W>(M + (size_t)rho * p.npp + q);
+        const T* rq = Rl + (size_t)iq * LN + ln;
+#pragma unroll
+        for (int u = 0; u < VB; ++u)
+          if (al[u] >= 0) acc[u] += w * rq[(size_t)al[u] * NT * LN];
+      }
+      const int mult = (gx % K == 0 ? 2 : 1) * (gy % K == 0 ? 2 : 1) * (DIM == 3 && gz % K == 0 ? 2 : 1);
+      const T sc = p.omega / T(mult);
+      const int lna = (lbase + ax) + LX * (ay + (DIM == 3 ? N * az : 0));
+#pragma unroll
+      for (int u = 0; u < VB; ++u)
+        if (al[u] >= 0) atomicAdd(&Zc[(size_t)(al[u] * NT + i) * LN + lna], sc * acc[u]);
+    }
+    __syncthreads();
+    // write x: chunk-private nodes directly, shared outer nodes atomically
+    for (int idx = tid; idx < V * LN; idx += nthr) {
+      const int v = idx / LN, ln = idx - v * LN;
+      const int lx = ln % LX, lyz = ln / LX;
+      if (lx >= lxn) continue;
+      const int ly = lyz % N, lz = DIM == 3 ? lyz / N : 0;
+      const int gx = cx0 * K + lx, gy = cy * K + ly, gz = DIM == 3 ? cz * K + lz : 0;
+      bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+      if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
+      if (!in) continue;
+      const T val = Zc[idx];
+      T* dst = p.x + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx;
+      const bool priv = lx > 0 && lx < lxn - 1 && ly > 0 && ly < K && (DIM == 2 || (lz > 0 && lz < K));
+      if (priv) *dst += val;
+      else atomicAdd(dst, val);
+    }
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
 }
 
 // x_fine += P e_coarse: gather over the (k+1)^d nodes of the coarse cell that
@@ -330,13 +421,17 @@ bool node_interior(const HostProblem& hp, const int g[3]) {
   return true;
 }
 
-// Vanka patch inverses of one level and class: [cell][np][np].
+// Row pitch of the stored patch inverses: np rounded up to 8 values (16-byte
+// rows for bf16, float and double).
+int vanka_row_pitch(int np) { return (np + 7) / 8 * 8; }
+
+// Vanka patch inverses of one level and class: [cell][np][pitch].
 bool patch_inverses(const HostProblem& hp, const ElementData& e, const std::vector<double>& diag,
                     std::vector<double>& out) {
-  const int n = hp.k + 1, nkd = e.nkd, nt = hp.n_t, np = nt * nkd;
+  const int n = hp.k + 1, nkd = e.nkd, nt = hp.n_t, np = nt * nkd, npp = vanka_row_pitch(np);
   std::vector<std::vector<double>> Kc(hp.n_cells);
   for (long long c = 0; c < hp.n_cells; ++c) element_stiffness(hp, e, diag, c, Kc[c]);
-  out.assign((size_t)hp.n_cells * np * np, 0.0);
+  out.assign((size_t)hp.n_cells * np * npp, 0.0);
   bool ok = true;
 #pragma omp parallel for schedule(dynamic, 64) reduction(&& : ok)
   for (long long c = 0; c < hp.n_cells; ++c) {
@@ -393,7 +488,9 @@ bool patch_inverses(const HostProblem& hp, const ElementData& e, const std::vect
           }
       }
     if (!invert(P, np)) ok = false;
-    std::copy(P.begin(), P.end(), out.begin() + (size_t)c * np * np);
+    for (int row = 0; row < np; ++row)
+      std::copy(P.begin() + (size_t)row * np, P.begin() + (size_t)(row + 1) * np,
+                out.begin() + ((size_t)c * np + row) * npp);
   }
   return ok;
 }
@@ -491,6 +588,23 @@ cudaError_t upload_values(void** dst, const std::vector<double>& src, int precis
   return upload_vec(reinterpret_cast<double**>(dst), src);
 }
 
+// bf16 copy of src (rounded to float, then to the nearest bf16 on the device).
+cudaError_t upload_bf16(void** dst, const std::vector<double>& src) {
+  float* tmp = nullptr;
+  std::vector<float> f(src.begin(), src.end());
+  cudaError_t e = upload_vec(&tmp, f);
+  if (e == cudaSuccess) e = cudaMalloc(dst, std::max<size_t>(1, f.size()) * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) {
+    const long long n = (long long)f.size();
+    k_to_bf16<<<(int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096)), 256>>>(
+        tmp, static_cast<__nv_bfloat16*>(*dst), n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  cudaFree(tmp);
+  return e;
+}
+
 // The diagonal (block-Jacobi) coupling table: row alpha keeps its own column.
 void diagonal_table(const HostProblem& fine, GTable& g, std::vector<std::vector<double>>& diag_of_row) {
   diag_of_row.assign(fine.n_xi, std::vector<double>(fine.n_terms, 0.0));
@@ -562,28 +676,101 @@ __global__ void mg_first_residual(const T* __restrict__ b, T* __restrict__ r, lo
   }
 }
 
+// Cells per Vanka chunk: up to 8, within the shared-memory budget.
+int vanka_chunk(const MGLevel& L, size_t value_bytes, size_t budget) {
+  const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
+  const size_t V = (size_t)L.hp.n_xi * L.hp.n_t;
+  int best = 0;
+  for (int c = 1; c <= std::min(8, L.hp.cells[0]); ++c)
+    if (2 * V * (size_t)(c * L.hp.k + 1) * lyz * value_bytes <= budget) best = c;
+  return best;
+}
+
+size_t vanka_smem(const MGLevel& L, int chunk, size_t value_bytes) {
+  const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
+  return 2 * (size_t)L.hp.n_xi * L.hp.n_t * (size_t)(chunk * L.hp.k + 1) * lyz * value_bytes;
+}
+
+template <typename T, typename W, int DIM, int K, int NT>
+cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
+  VankaParams<T> p;
+  p.r = static_cast<const T*>(L.d_r);
+  p.x = static_cast<T*>(L.d_x);
+  p.inv = L.d_inv;
+  p.blk_cls = mg.d_blk_cls;
+  p.blk_alpha = mg.d_blk_alpha;
+  p.n_blk = mg.n_blk;
+  p.n_xi = L.hp.n_xi;
+  p.chunk = L.vanka_chunk;
+  p.npp = vanka_row_pitch(L.np);
+  p.n_x = L.hp.n_x;
+  p.n_cells = L.hp.n_cells;
+  for (int d = 0; d < 3; ++d) {
+    p.cells[d] = L.hp.cells[d];
+    p.nn[d] = L.hp.nn[d];
+  }
+  p.omega = T(mg.omega);
+  const size_t smem = vanka_smem(L, L.vanka_chunk, sizeof(T));
+  const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
+  const long long chunks = (long long)cpr * L.hp.cells[1] * L.hp.cells[2];
+  const int grid = (int)std::min<long long>(chunks, 152LL * 8);
+  auto kern = trans ? &mg_vanka<T, W, DIM, K, NT, true> : &mg_vanka<T, W, DIM, K, NT, false>;
+  kern<<<grid, 256, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Allows the Vanka kernels of one shape the opt-in shared-memory maximum
+// (called at set-up, outside any stream capture).
+template <typename T, typename W, int DIM, int K, int NT>
+cudaError_t prepare_vanka_w() {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaFuncSetAttribute(&mg_vanka<T, W, DIM, K, NT, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(&mg_vanka<T, W, DIM, K, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return e;
+}
+
+cudaError_t prepare_vanka(int dim, int k, int nt, bool f32, bool bf16) {
+#define SG_PV(D, KK, TT)                                                           \
+  if (dim == D && k == KK && nt == TT) {                                           \
+    if (!f32) return prepare_vanka_w<double, double, D, KK, TT>();                 \
+    if (bf16) return prepare_vanka_w<float, __nv_bfloat16, D, KK, TT>();           \
+    return prepare_vanka_w<float, float, D, KK, TT>();                             \
+  }
+  SG_PV(2, 1, 1) SG_PV(2, 1, 2) SG_PV(2, 1, 3) SG_PV(2, 1, 4)
+  SG_PV(2, 2, 1) SG_PV(2, 2, 2) SG_PV(2, 2, 3) SG_PV(2, 2, 4)
+  SG_PV(2, 3, 1) SG_PV(2, 3, 2) SG_PV(2, 3, 3) SG_PV(2, 3, 4)
+  SG_PV(3, 1, 1) SG_PV(3, 1, 2) SG_PV(3, 2, 1) SG_PV(3, 2, 2)
+#undef SG_PV
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, int DIM, int K, int NT>
-void launch_vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
-  const long long warps = L.hp.n_cells * ((L.hp.n_xi + 31) / 32);
-  const int block = 128;
-  const long long grid = (warps * 32 + block - 1) / block;
-  auto kern = trans ? &mg_vanka<T, DIM, K, NT, true> : &mg_vanka<T, DIM, K, NT, false>;
-  kern<<<(unsigned)grid, block, 0, s>>>(
-      static_cast<const T*>(L.d_r), static_cast<T*>(L.d_x), static_cast<const T*>(L.d_inv), mg.d_cls, L.hp.n_xi,
-      L.hp.n_x, L.hp.n_cells, L.hp.cells[0], L.hp.cells[1], L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], T(mg.omega));
+cudaError_t launch_vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (mg.bf16) return launch_vanka_w<T, __nv_bfloat16, DIM, K, NT>(mg, L, s, trans);
+  }
+  return launch_vanka_w<T, T, DIM, K, NT>(mg, L, s, trans);
 }
 
 template <typename T>
 bool vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   const int d = L.hp.dim, k = L.hp.k, t = L.hp.n_t;
 #define SG_V(D, KK, TT) \
-  if (d == D && k == KK && t == TT) { launch_vanka<T, D, KK, TT>(mg, L, s, trans); return true; }
+  if (d == D && k == KK && t == TT) return launch_vanka<T, D, KK, TT>(mg, L, s, trans) == cudaSuccess;
   SG_V(2, 1, 1) SG_V(2, 1, 2) SG_V(2, 1, 3) SG_V(2, 1, 4)
   SG_V(2, 2, 1) SG_V(2, 2, 2) SG_V(2, 2, 3) SG_V(2, 2, 4)
   SG_V(2, 3, 1) SG_V(2, 3, 2) SG_V(2, 3, 3) SG_V(2, 3, 4)
   SG_V(3, 1, 1) SG_V(3, 1, 2) SG_V(3, 2, 1) SG_V(3, 2, 2)
 #undef SG_V
   return false;
+}
+
+bool vk_launch(MG& mg, MGLevel& L, cudaStream_t s) {
+  return mg.precision == kPrecF32 ? vanka<float>(mg, L, s, 0) : vanka<double>(mg, L, s, 0);
 }
 
 template <typename T>
@@ -662,6 +849,49 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
 
 }  // namespace
 
+// Picks the cells per Vanka chunk of every smoothed level by timing one sweep
+// for each candidate (1, 2, 4, 8 cells, within the shared-memory budget) on
+// the level's own buffers; keeps the fastest.
+static cudaError_t tune_vanka(MG& mg) {
+  const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  for (MGLevel& L : mg.lv) {
+    if (L.coarsest || e != cudaSuccess) continue;
+    const int max_c = L.vanka_chunk;
+    const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
+    if ((e = cudaMemsetAsync(L.d_r, 0, n * vb, mg.stream)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
+    int best = max_c;
+    float best_ms = 1e30f;
+    std::vector<int> cand;
+    for (int c = 1; c <= max_c; c *= 2) cand.push_back(c);
+    if (cand.back() != max_c) cand.push_back(max_c);
+    for (int c : cand) {
+      if (e != cudaSuccess) break;
+      L.vanka_chunk = c;
+      float ms = 0.0f;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(a, mg.stream);
+        const bool ok = vk_launch(mg, L, mg.stream);
+        if (!ok) e = cudaErrorInvalidValue;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    L.vanka_chunk = best;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return e;
+}
+
 void mg_free(MG& mg) {
   for (int t = 0; t < 2; ++t) {
     if (mg.exec_t[t]) cudaGraphExecDestroy(mg.exec_t[t]);
@@ -671,6 +901,9 @@ void mg_free(MG& mg) {
   }
   if (mg.stream) cudaStreamDestroy(mg.stream);
   cudaFree(mg.d_cls);
+  cudaFree(mg.d_blk_cls);
+  cudaFree(mg.d_blk_alpha);
+  mg.d_blk_cls = mg.d_blk_alpha = nullptr;
   for (MGLevel& L : mg.lv) {
     cudaFree(L.d_ctab); cudaFree(L.d_grow); cudaFree(L.d_gcol); cudaFree(L.d_gterm); cudaFree(L.d_gval);
     cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner);
@@ -687,6 +920,9 @@ void mg_free(MG& mg) {
 sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg,
                    bool single_class) {
   const auto t0 = std::chrono::steady_clock::now();
+  mg.requested = precision;
+  mg.bf16 = precision == SG_PREC_BF16;
+  if (mg.bf16) precision = kPrecF32;          // FP32 vectors, bf16-stored patch inverses
   mg.precision = precision;
   mg.nu = nu;
   mg.omega = omega;
@@ -716,6 +952,18 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     std::fill(mg.cls.begin(), mg.cls.end(), 0);
   }
   mg.n_classes = (int)class_diag.size();
+  // Vanka mode blocks: the modes of one class, kVankaVB at a time
+  std::vector<int> blk_cls, blk_alpha;
+  for (int c = 0; c < mg.n_classes; ++c) {
+    std::vector<int> modes;
+    for (int a = 0; a < fine.n_xi; ++a)
+      if (mg.cls[a] == c) modes.push_back(a);
+    for (size_t i = 0; i < modes.size(); i += kVankaVB) {
+      blk_cls.push_back(c);
+      for (int u = 0; u < kVankaVB; ++u) blk_alpha.push_back(i + u < modes.size() ? modes[i + u] : -1);
+    }
+  }
+  mg.n_blk = (int)blk_cls.size();
   // level problems
   std::vector<HostProblem> hps;
   hps.push_back(fine);
@@ -794,7 +1042,22 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
         inv.insert(inv.end(), pi.begin(), pi.end());
       }
     }
-    if ((e = upload_values(&L.d_inv, inv, precision)) != cudaSuccess) break;
+    if (!L.coarsest && mg.bf16) e = upload_bf16(&L.d_inv, inv);
+    else e = upload_values(&L.d_inv, inv, precision);
+    if (e != cudaSuccess) break;
+    if (!L.coarsest) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const size_t vb = precision == kPrecF32 ? 4 : 8;
+      L.vanka_chunk = vanka_chunk(L, vb, 100 * 1024);
+      if (L.vanka_chunk == 0) L.vanka_chunk = vanka_chunk(L, vb, (size_t)optin - 1024);
+      if (L.vanka_chunk == 0) {
+        msg = "Vanka smoother: one cell with all rows does not fit in shared memory (fewer samples per batch)";
+        return SG_ERR_UNSUPPORTED;
+      }
+      if ((e = prepare_vanka(L.hp.dim, L.hp.k, L.hp.n_t, precision == kPrecF32, mg.bf16)) != cudaSuccess) break;
+    }
     // level apply tables (coefficient stays double; vectors use the MG precision)
     if ((e = upload_vec(reinterpret_cast<double**>(&L.d_ctab), L.hp.ctab)) != cudaSuccess) break;
     if ((e = upload_vec(&L.d_grow, L.hp.g.row)) != cudaSuccess) break;
@@ -832,7 +1095,10 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     }
   }
   if (e == cudaSuccess) e = upload_vec(&mg.d_cls, mg.cls);
+  if (e == cudaSuccess) e = upload_vec(&mg.d_blk_cls, blk_cls);
+  if (e == cudaSuccess) e = upload_vec(&mg.d_blk_alpha, blk_alpha);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = tune_vanka(mg);
   if (e != cudaSuccess) {
     msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;

@@ -110,3 +110,38 @@ def test_fgmres_matches_direct_solve():
         assert res <= 1e-10
         assert np.abs(x.reshape(p.shape) - xd).max() <= 1e-8 * np.abs(xd).max()
         assert its < 30
+
+
+def test_round_bf16_rounds_to_nearest_even():
+    """Hand-made cases at 1.0 (bf16 spacing 2^-7 there), then agreement with
+    torch's own float32 -> bfloat16 conversion on random values."""
+    torch = pytest.importorskip("torch")
+    h = 2.0 ** -8
+    vals = np.array([1.0, 1.0 + h, 1.0 + 3 * h, 1.0 + h + 2.0 ** -20, -(1.0 + 3 * h), 1.0 - 2.0 ** -9, 0.0])
+    want = np.array([1.0, 1.0, 1.0 + 4 * h, 1.0 + 2 * h, -(1.0 + 4 * h), 1.0, 0.0])
+    assert np.array_equal(solver.round_bf16(vals), want)
+    x = np.random.default_rng(5).standard_normal(10000) * np.exp(np.random.default_rng(6).uniform(-20, 20, 10000))
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(solver.round_bf16(x), ref)
+
+
+def test_vcycle_with_bf16_factors_still_contracts():
+    """The V-cycle with bf16-rounded Vanka inverses remains a contraction for
+    the block operator (error reduction per cycle well below 1), close to the
+    exact-factor cycle's."""
+    spec = spec2((16, 16), k=2)
+    p = operator.SGProblem(spec)
+    rates = []
+    for fr in (None, solver.round_bf16):
+        mg = solver.Multigrid(p, factor_round=fr)
+        L = mg.levels[0]
+        A = L.A[0]
+        e = np.random.default_rng(3).standard_normal(A.shape[0])
+        e[np.tile(L.bmask, L.n_t)] = 0.0
+        for _ in range(3):
+            e = e - mg.vcycle_block(0, A @ e)
+        n0 = np.linalg.norm(e)
+        e = e - mg.vcycle_block(0, A @ e)
+        rates.append(np.linalg.norm(e) / n0)
+    assert rates[0] < 0.2 and rates[1] < 0.3
+    assert abs(rates[1] - rates[0]) < 0.1

@@ -2,7 +2,9 @@
 solve (sg_solve_slab) with the oracle (oracle/solver.py), through the C ABI.
 
 sg_vcycle is a fixed linear map: the GPU result is compared element by element
-with the oracle's V-cycle (FP64 levels: 1e-10 relative; FP32 levels: 1e-4).
+with the oracle's V-cycle (FP64 levels: 1e-10 relative; FP32 levels: 1e-4;
+FP32 levels with bf16-stored Vanka inverses: 1e-4 against the oracle's V-cycle
+whose inverses are rounded to bf16 in the same way).
 sg_solve_slab is checked by the property the benchmark spec fixes for solves: the
 true residual ||b - A x|| / ||b||, evaluated by the oracle's operator, is at
 most the requested tolerance (1e-8 at scale, 1e-10 on the small case), and the
@@ -42,7 +44,7 @@ VCYCLE_CASES = {
     "3d-q1-4x4x4": spec3((4, 4, 4), k=1),
     "3d-q2-4x4x4": spec3((4, 4, 4), k=2, M=1, P=1),
 }
-MG_PREC = {"fp64": (sg.SG_PREC_FP64, 1e-10), "fp32": (sg.SG_PREC_FP32, 1e-4)}
+MG_PREC = {"fp64": (sg.SG_PREC_FP64, 1e-10), "fp32": (sg.SG_PREC_FP32, 1e-4), "bf16": (sg.SG_PREC_BF16, 1e-4)}
 
 
 def _rel(a, b):
@@ -55,7 +57,8 @@ def test_vcycle_matches_oracle(cuda, name, prec):
     torch = cuda
     spec = VCYCLE_CASES[name]
     p = operator.SGProblem(spec)
-    mg = solver.Multigrid(p)
+    # bf16: the oracle's V-cycle with its Vanka inverses rounded the same way
+    mg = solver.Multigrid(p, factor_round=solver.round_bf16 if prec == "bf16" else None)
     r = np.random.default_rng(4).uniform(-1, 1, p.shape)
     want = mg.apply(r).reshape(-1)
     ctx = sg.sg_setup_spec(spec)

@@ -381,7 +381,6 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
   for (int c : chunks) {
     if (e != cudaSuccess) break;
     for (int t : thread_opts) {
-      if (t < ctx->hp.n_xi) continue;
       sg::LaunchShape ls;
       std::string msg;
       if (sg::plan_apply_shape(ctx->hp, c, t, ls, msg) != SG_OK) continue;

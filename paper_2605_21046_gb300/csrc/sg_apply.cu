@@ -20,9 +20,11 @@
 //            cost nothing);
 //   phase 2  per (cell, Gauss point, alpha): the time-node mass coupling
 //            w_q sum_j A_t[i][j] u[alpha,j] and the sparse chaos contraction
-//            sum_(beta,mu) G_mu[alpha][beta] a_mu(x_q) grad u[beta,i];
-//            chaos rows are visited in order of their entry count so that the
-//            lanes of a warp loop the same number of times;
+//            sum_(beta,mu) G_mu[alpha][beta] a_mu(x_q) grad u[beta,i]; the
+//            lanes of a warp take consecutive points of ONE chaos row, so the
+//            coupling loop never diverges and its entries are broadcast loads
+//            (rounds of up to 32 points, results held in registers until every
+//            read of the round's points is done);
 //   phase 3  per (cell, vector): the transposed sum factorisation back to
 //            the cell's nodes;
 //   phase 4  per (cell, vector, node): scale by tau*Bhat_ii and add into y
@@ -81,11 +83,11 @@ size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz,
   const size_t V = (size_t)n_xi * n_t;
   size_t vals = (size_t)chunk * V * (1 + dim) * nqd      // Qs
                 + (size_t)chunk * n_terms * nqd          // Cs
-                + nnz                                    // Gv
                 + nqd * n_t * n_t                        // Amq
                 + n_t + 3;                               // Tb, Rt
-  size_t ints = (n_xi + 1) + 2 * (size_t)nnz + n_xi;     // Gr, Gc, Gt, Pm
-  return ((vals * value_bytes + 7) / 8) * 8 + ints * sizeof(int);
+  size_t ints = (n_xi + 1) + n_xi;                       // Gr, Pm
+  // values, then 16-byte packed coupling entries at a 16-byte boundary, then ints
+  return ((vals * value_bytes + 15) / 16) * 16 + 16 * (size_t)nnz + ints * sizeof(int);
 }
 
 template <int K>
@@ -131,8 +133,10 @@ int max_apply_chunk(const HostProblem& hp, size_t budget) {
   return chunk;
 }
 
-// Launch shape for a given chunk and thread count (0 = defaults).  Phase 2
-// runs whole (cell, point) groups of n_xi threads, so threads >= n_xi.
+// Launch shape for a given chunk and thread count (0 = defaults).  A phase-2
+// round holds at least one point of every chaos row (at most kmax items per
+// thread), so kmax * threads >= n_xi; threads stay within the kernel's launch
+// bounds.
 sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, LaunchShape& ls, std::string& msg) {
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) {
@@ -170,11 +174,22 @@ sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, Launch
     chunk = (int)std::min<long long>(chunk, std::max<long long>(1, (cells_per_sm + 1) / 2));
   }
   if (chunk > max1) { msg = "chunk does not fit in shared memory"; return SG_ERR_ARG; }
-  if (threads <= 0) {
-    const int groups = std::max(1, 256 / hp.n_xi);
-    threads = ((groups * hp.n_xi + 31) / 32) * 32;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) {
+    cudaGetLastError();
+    msg = "apply kernel attributes unavailable";
+    return SG_ERR_CUDA;
   }
-  if (threads < hp.n_xi || threads > 512 || threads % 32) { msg = "invalid thread count"; return SG_ERR_ARG; }
+  // a phase-2 round needs one point of every chaos row: kmax * threads >= n_xi
+  const int kmax = 18 / (hp.n_t * (1 + hp.dim)) < 1 ? 1 : std::min(3, 18 / (hp.n_t * (1 + hp.dim)));
+  if (threads <= 0) {
+    threads = 256;
+    while (threads * kmax < hp.n_xi && threads + 128 <= fa.maxThreadsPerBlock) threads += 128;
+  }
+  if (threads * kmax < hp.n_xi || threads > fa.maxThreadsPerBlock || threads % 32 || threads < 32) {
+    msg = "invalid thread count";
+    return SG_ERR_ARG;
+  }
   ls.chunk = chunk;
   ls.threads = threads;
   ls.smem = apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, chunk, vb);

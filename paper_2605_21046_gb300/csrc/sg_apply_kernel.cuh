@@ -199,9 +199,34 @@ __device__ __forceinline__ void backward_cell(typename A::T* q) {
   }
 }
 
+// One coupling entry of a chaos row, packed for a single 16-byte shared load:
+// the offset of column beta's vectors in a cell's value block, the offset of
+// the entry's coefficient term in a cell's coefficient block, and G.
+template <class T>
+struct alignas(16) CoupleEntry {
+  int off;
+  int tq;
+  T g;
+};
+
+// Phase-2 items held per thread (their results live in registers until the
+// round's barrier), and the launch bounds: the 2D shapes with at most two
+// time nodes and degree <= 2 run two 384-thread CTAs per SM within 80
+// registers.
+__host__ __device__ constexpr int chunk_kmax(int dim, int nt) {
+  return 18 / (nt * (1 + dim)) < 1 ? 1 : (18 / (nt * (1 + dim)) > 3 ? 3 : 18 / (nt * (1 + dim)));
+}
+template <int DIM, int K, int NT>
+struct ChunkBounds {
+  static constexpr bool tight = DIM == 2 && K <= 2 && NT <= 2;
+  static constexpr int threads = tight ? 384 : 512;
+  static constexpr int blocks = tight ? 2 : 1;
+};
+
 // The persistent chunk kernel (design notes in sg_apply.cu).
 template <class A, int DIM, int K, int NT>
-__global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p) {
+__global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<DIM, K, NT>::blocks)
+    sg_apply_chunk_kernel(const ApplyParams p) {
   using T = typename A::T;
   using Sh = Shape<DIM, K>;
   constexpr int NQD = Sh::NQD, NKD = Sh::NKD, NC = Sh::NC, N = Sh::N;
@@ -214,21 +239,22 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
   const int n_xi = p.n_xi, V = n_xi * NT, C = p.chunk;
 
   T* Qs = reinterpret_cast<T*>(smem_raw);                       // [C][V][NC][NQD]
-  // the 8-byte tables follow the value arrays at an 8-byte boundary
   T* Cs = Qs + (size_t)C * V * SLOT;                            // [C][term][NQD]
-  T* Gv = Cs + (size_t)C * p.n_terms * NQD;                     // [nnz]
-  T* Amq = Gv + p.nnz;                                          // [NQD][NT][NT]
+  T* Amq = Cs + (size_t)C * p.n_terms * NQD;                    // [NQD][NT][NT]
   T* Tb = Amq + NQD * NT * NT;                                  // [NT]
   T* Rt = Tb + NT;                                              // [3] (h_0/h_d)^2
-  int* Gr = reinterpret_cast<int*>(Rt + 3);                     // [n_xi+1]
-  int* Gc = Gr + n_xi + 1;                                      // [nnz]
-  int* Gt = Gc + p.nnz;                                         // [nnz]
-  int* Pm = Gt + p.nnz;                                         // [n_xi]
+  // the packed coupling entries follow at a 16-byte boundary
+  CoupleEntry<T>* Ge = reinterpret_cast<CoupleEntry<T>*>(
+      (reinterpret_cast<uintptr_t>(Rt + 3) + 15) & ~static_cast<uintptr_t>(15));   // [nnz]
+  int* Gr = reinterpret_cast<int*>(Ge + p.nnz);                 // [n_xi+1]
+  int* Pm = Gr + n_xi + 1;                                      // [n_xi]
 
   for (int e = tid; e < p.nnz; e += nthr) {
-    Gv[e] = A::in(p.g_val[e]);
-    Gc[e] = p.g_col[e];
-    Gt[e] = p.g_term[e];
+    CoupleEntry<T> ce;
+    ce.off = p.g_col[e] * NT * SLOT;
+    ce.tq = p.g_term[e] * NQD;
+    ce.g = A::in(p.g_val[e]);
+    Ge[e] = ce;
   }
   for (int e = tid; e <= n_xi; e += nthr) Gr[e] = p.g_row[e];
   for (int e = tid; e < n_xi; e += nthr) Pm[e] = p.perm[e];
@@ -274,61 +300,80 @@ __global__ void __launch_bounds__(512) sg_apply_chunk_kernel(const ApplyParams p
     }
     __syncthreads();
     // ---------------------------------------------------------- phase 2
+    // Rounds of PB Gauss points: the items of a round are (chaos row, point)
+    // pairs, consecutive threads taking consecutive points of one row, so a
+    // warp follows a single row (no divergence in the coupling loop, one
+    // broadcast load per entry).  A thread holds up to KMAX items' results in
+    // registers; every read of a round's points precedes its writes (one
+    // barrier), and rounds touch disjoint points.
     {
-      const int gpr = nthr / n_xi;               // (cell, point) groups per round
-      const int gl = tid / n_xi;
-      const int a = Pm[tid - gl * n_xi];
-      const int ngroups = nc * NQD;
-      for (int g0 = 0; g0 < ngroups; g0 += gpr) {
-        const int g = g0 + gl;
-        const bool act = gl < gpr && g < ngroups;
-        const int c = act ? g / NQD : 0;
-        const int q = act ? g - c * NQD : 0;
-        T out[NT][NC];
-        if (act) {
-          const T* base = Qs + (size_t)c * V * SLOT + q;
-          T uv[NT];
+      constexpr int KMAX = chunk_kmax(DIM, NT);
+      const int PB = min(32, max(1, (KMAX * nthr) / n_xi));
+      const int npts = nc * NQD;
+      for (int p0 = 0; p0 < npts; p0 += PB) {
+        const int pb = min(PB, npts - p0);
+        const int items = n_xi * pb;
+        T out[KMAX][NT][NC];
+        int a_of[KMAX], c_of[KMAX], q_of[KMAX];
 #pragma unroll
-          for (int j = 0; j < NT; ++j) uv[j] = base[(size_t)(a * NT + j) * SLOT];
-          const T* am = Amq + q * NT * NT;
+        for (int kk = 0; kk < KMAX; ++kk) {
+          const int it = tid + kk * nthr;
+          a_of[kk] = -1;
+          c_of[kk] = q_of[kk] = 0;
+          if (it < items) {
+            const int slot = it / pb, pt = p0 + (it - slot * pb);
+            const int a = Pm[slot];
+            const int c = pt / NQD, q = pt - c * NQD;
+            a_of[kk] = a;
+            c_of[kk] = c;
+            q_of[kk] = q;
+            const T* base = Qs + (size_t)c * V * SLOT + q;
+            T uv[NT];
 #pragma unroll
-          for (int i = 0; i < NT; ++i) {
-            T s = A::mul(am[i * NT], uv[0]);
+            for (int j = 0; j < NT; ++j) uv[j] = base[(size_t)(a * NT + j) * SLOT];
+            const T* am = Amq + q * NT * NT;
 #pragma unroll
-            for (int j = 1; j < NT; ++j) A::fma(am[i * NT + j], uv[j], s);
-            out[i][0] = A::fin(s);
+            for (int i = 0; i < NT; ++i) {
+              T s = A::mul(am[i * NT], uv[0]);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) out[i][1 + d] = A::zero();
-          }
-          const T* cq = Cs + (size_t)c * p.n_terms * NQD + q;
-          const int e_end = Gr[a + 1];
-          for (int e = Gr[a]; e < e_end; ++e) {
-            const T w = A::fin(A::mul(Gv[e], cq[Gt[e] * NQD]));
-            const T* gb = base + (size_t)(Gc[e] * NT) * SLOT;
+              for (int j = 1; j < NT; ++j) A::fma(am[i * NT + j], uv[j], s);
+              out[kk][i][0] = A::fin(s);
+#pragma unroll
+              for (int d = 0; d < DIM; ++d) out[kk][i][1 + d] = A::zero();
+            }
+            const T* cq = Cs + (size_t)c * p.n_terms * NQD + q;
+            const int e_end = Gr[a + 1];
+            for (int e = Gr[a]; e < e_end; ++e) {
+              const CoupleEntry<T> ce = Ge[e];
+              const T w = A::fin(A::mul(ce.g, cq[ce.tq]));
+              const T* gb = base + ce.off;
+#pragma unroll
+              for (int i = 0; i < NT; ++i)
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) A::fma(w, gb[(size_t)i * SLOT + (1 + d) * NQD], out[kk][i][1 + d]);
+            }
 #pragma unroll
             for (int i = 0; i < NT; ++i)
 #pragma unroll
-              for (int d = 0; d < DIM; ++d) A::fma(w, gb[(size_t)i * SLOT + (1 + d) * NQD], out[i][1 + d]);
+              for (int d = 0; d < DIM; ++d) {
+                if (p.aniso && d > 0) out[kk][i][1 + d] = A::mul(A::fin(out[kk][i][1 + d]), Rt[d]);
+                out[kk][i][1 + d] = A::fin(out[kk][i][1 + d]);
+              }
           }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KMAX; ++kk) {
+          if (a_of[kk] < 0) continue;
+          T* base = Qs + (size_t)c_of[kk] * V * SLOT + q_of[kk];
 #pragma unroll
           for (int i = 0; i < NT; ++i)
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-              if (p.aniso && d > 0) out[i][1 + d] = A::mul(A::fin(out[i][1 + d]), Rt[d]);
-              out[i][1 + d] = A::fin(out[i][1 + d]);
-            }
+            for (int cc = 0; cc < NC; ++cc) base[(size_t)(a_of[kk] * NT + i) * SLOT + cc * NQD] = out[kk][i][cc];
         }
-        __syncthreads();
-        if (act) {
-          T* base = Qs + (size_t)c * V * SLOT + q;
-#pragma unroll
-          for (int i = 0; i < NT; ++i)
-#pragma unroll
-            for (int cc = 0; cc < NC; ++cc) base[(size_t)(a * NT + i) * SLOT + cc * NQD] = out[i][cc];
-        }
-        __syncthreads();
       }
     }
+    __syncthreads();
     // ---------------------------------------------------------- phase 3
     for (int it = tid; it < nc * V; it += nthr) backward_cell<A, DIM, K>(Qs + (size_t)it * SLOT);
     __syncthreads();

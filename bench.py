@@ -37,7 +37,7 @@ BYTES_PER_UNKNOWN = 16.0
 L2_BYTES = 135_528_448
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 chunk-kernel launch on
 # this workload (ncu capture summarised in profiles/); None once the kernel changes
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = 19_901_696 + 0
 
 
 def workload():
@@ -196,9 +196,11 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_clocks, local):
+def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_clocks, local, profile_range=False):
     """Device time of `steps` applies over rotating buffers; returns
-    (elapsed_ms max over ranks, mean per-launch seconds, clocks)."""
+    (elapsed_ms max over ranks, mean per-launch seconds, clocks).  With
+    profile_range the timed launches are bracketed by cudaProfilerStart/Stop
+    (for ncu --profile-from-start off)."""
     R = len(X)
     for s in range(warmup):
         sg.sg_apply(ctx, 0, X[s % R], Y[s % R], False, stream)
@@ -209,6 +211,8 @@ def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_cloc
         torch.cuda.synchronize()
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
+        if profile_range:
+            torch.cuda.profiler.start()
         t_start.record(stream)
         for s in range(steps):
             ev[s][0].record(stream)
@@ -216,6 +220,8 @@ def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_cloc
             ev[s][1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
+        if profile_range:
+            torch.cuda.profiler.stop()
         barrier(world)
     clocks = clk.summary() if sample_clocks else None
     elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), world)
@@ -231,6 +237,7 @@ def measure_solve(sg, torch, spec, dev, reps=3, autotune=True):
     out, ref = {}, None
     for name, apply_prec, mg_prec in (("fp64", sg.SG_PREC_FP64, sg.SG_PREC_FP64),
                                       ("fp32_mg", sg.SG_PREC_FP64, sg.SG_PREC_FP32),
+                                      ("bf16_factors_mg", sg.SG_PREC_FP64, sg.SG_PREC_BF16),
                                       ("fp32_mg_dw_apply", sg.SG_PREC_DW, sg.SG_PREC_FP32)):
         ctx = sg.sg_setup_spec(spec, apply_prec)
         if autotune:
@@ -278,7 +285,7 @@ def run_ours(args, world, rank, local):
     Y = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(R)]
     stream = torch.cuda.current_stream(dev)
     elapsed_ms, t_launch, clocks = time_applies(sg, torch, ctx, X, Y, args.steps, args.warmup, stream,
-                                                world, True, local)
+                                                world, True, local, profile_range=args.profile_range)
     value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
     assert torch.isfinite(Y[0]).all()
     y64 = Y[0].clone()
@@ -393,14 +400,16 @@ def march(sg, torch, ctx, rtol, slabs=None):
 
 def next_mixed_precision(sg, torch, inputs):
     """Mixed-precision solve on the 3D 32^3 Q2, M=3 / P=3 workload: FP64
-    V-cycle vs FP32 V-cycle (FP64 FGMRES, Arnoldi and residual), marching all
-    20 slabs to a 1e-8 relative residual per slab."""
+    V-cycle vs FP32 V-cycle vs FP32 V-cycle with bf16-stored Vanka factors
+    (FP64 FGMRES, Arnoldi and residual), marching all 20 slabs to a 1e-8
+    relative residual per slab."""
     spec = inputs.config_3d_q2_32()
     exact = exact_for(sg, spec["M"], 2, 3)
     out, ref = {}, None
     for name, ap, mp in (("fp64", sg.SG_PREC_FP64, sg.SG_PREC_FP64),
                          ("fp32_mg", sg.SG_PREC_FP64, sg.SG_PREC_FP32),
-                         ("fp32_mg_dw_apply", sg.SG_PREC_DW, sg.SG_PREC_FP32)):
+                         ("bf16_factors_mg", sg.SG_PREC_FP64, sg.SG_PREC_BF16),
+                         ("bf16_factors_mg_dw_apply", sg.SG_PREC_DW, sg.SG_PREC_BF16)):
         ctx = sg.sg_setup_spec(spec, ap)
         sg.sg_autotune(ctx, reps=3)
         sg.sg_set_exact(ctx, exact)
@@ -565,6 +574,8 @@ def main():
     ap.add_argument("--no-dw", action="store_true", help="skip the double-word variant")
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed FP64 applies with cudaProfilerStart/Stop")
     ap.add_argument("--suite", choices=["apply", "next"], default="apply",
                     help="apply: the headline line; next: one line per solver-side row")
     ap.add_argument("--rows", default="mixed,mc,adjoint", help="rows of --suite next")

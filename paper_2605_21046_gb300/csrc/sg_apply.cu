@@ -57,23 +57,22 @@ void* select_kernel_f32(int dim, int k, int n_t);
 // elsewhere) for a plain apply, b minus that for a residual, b for an
 // accumulation (y == b allowed there).
 template <typename IO>
-__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* y, const IO* b, int mode,
-                                 long long n_total, long long n_x, int nnx, int nny, int nnz,
-                                 int dim) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long m = idx % n_x;
-    int ix = (int)(m % nnx);
-    int iy = (int)((m / nnx) % nny);
-    int iz = (int)(m / ((long long)nnx * nny));
-    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
-    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
+__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* y, const IO* b, int mode, int n_x, int nnx,
+                                 int nny, int nnz, int dim) {
+  // blockIdx.y picks the vector; 32-bit node arithmetic within it
+  const long long off = (long long)blockIdx.y * n_x;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
+    const long long idx = off + m;
     if (mode == kApplyAccumulate) {
       y[idx] = b[idx];
-    } else {
-      const IO v = bd ? x[idx] : IO(0);
-      y[idx] = mode == kApplyResidual ? b[idx] - v : v;
+      continue;
     }
+    const int ix = m % nnx, r = m / nnx;
+    const int iy = r % nny, iz = r / nny;
+    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
+    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
+    const IO v = bd ? x[idx] : IO(0);
+    y[idx] = mode == kApplyResidual ? b[idx] - v : v;
   }
 }
 
@@ -259,15 +258,17 @@ void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void*
 
 cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const ApplyParams& prm,
                          cudaStream_t stream) {
-  const long long n_total = (long long)hp.n_xi * hp.n_t * hp.n_x;
-  int ib = 256;
-  long long ig = std::min<long long>((n_total + ib - 1) / ib, 152LL * 16);
+  const int V = hp.n_xi * hp.n_t;
+  const int ib = 256;
+  const dim3 ig((unsigned)std::max<long long>(1, std::min<long long>((hp.n_x + ib - 1) / ib, 64)), (unsigned)V);
   if (hp.precision == kPrecF32)
-    sg_init_y_kernel<float><<<(int)ig, ib, 0, stream>>>(static_cast<const float*>(prm.x), static_cast<float*>(prm.y),
-                                                        static_cast<const float*>(prm.b), prm.mode, n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+    sg_init_y_kernel<float><<<ig, ib, 0, stream>>>(static_cast<const float*>(prm.x), static_cast<float*>(prm.y),
+                                                   static_cast<const float*>(prm.b), prm.mode, (int)hp.n_x, hp.nn[0],
+                                                   hp.nn[1], hp.nn[2], hp.dim);
   else
-    sg_init_y_kernel<double><<<(int)ig, ib, 0, stream>>>(static_cast<const double*>(prm.x), static_cast<double*>(prm.y),
-                                                         static_cast<const double*>(prm.b), prm.mode, n_total, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+    sg_init_y_kernel<double><<<ig, ib, 0, stream>>>(static_cast<const double*>(prm.x), static_cast<double*>(prm.y),
+                                                    static_cast<const double*>(prm.b), prm.mode, (int)hp.n_x, hp.nn[0],
+                                                    hp.nn[1], hp.nn[2], hp.dim);
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<ApplyParams*>(&prm)};

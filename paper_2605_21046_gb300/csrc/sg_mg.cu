@@ -849,6 +849,57 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
 
 }  // namespace
 
+// Picks the launch shape (cells per chunk x threads) of every smoothed level's
+// residual apply by timing it on the level's own buffers (levels of at least
+// 256 cells; smaller ones keep the default).
+static cudaError_t tune_level_applies(MG& mg) {
+  const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  for (MGLevel& L : mg.lv) {
+    if (L.coarsest || L.hp.n_cells < 256 || e != cudaSuccess) continue;
+    const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
+    if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(L.d_b, 0, n * vb, mg.stream)) != cudaSuccess) break;
+    const int max1 = max_apply_chunk(L.hp, (size_t)optin - 1024);
+    std::vector<int> chunks;
+    for (int c = max1; c >= 1; c = c > 1 ? (c + 1) / 2 - (c == 2) : 0) chunks.push_back(c);
+    LaunchShape best = L.ls;
+    float best_ms = 1e30f;
+    for (int c : chunks) {
+      for (int t : {128, 256, 384, 512}) {
+        if (e != cudaSuccess) break;
+        LaunchShape ls;
+        std::string msg;
+        if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
+        ApplyParams p;
+        fill_apply_params(L.hp, ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, 0, p);
+        p.b = L.d_b;
+        p.mode = kApplyResidual;
+        e = launch_apply(L.hp, ls, p, mg.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_apply(L.hp, ls, p, mg.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = ls;
+        }
+      }
+    }
+    L.ls = best;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return e;
+}
+
 // Picks the cells per Vanka chunk of every smoothed level by timing one sweep
 // for each candidate (1, 2, 4, 8 cells, within the shared-memory budget) on
 // the level's own buffers; keeps the fastest.
@@ -1098,6 +1149,7 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_cls, blk_cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_alpha, blk_alpha);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = tune_level_applies(mg);
   if (e == cudaSuccess) e = tune_vanka(mg);
   if (e != cudaSuccess) {
     msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);

@@ -253,7 +253,10 @@ sg_status build_host_problem_pieces(const sg_mesh* mesh, int k, int r, int n_sla
   hp.idx = chaos_indices(M, p);
   hp.n_xi = (int)(hp.idx.size() / M);
   hp.n_t = r + 1;
-  if ((long long)hp.n_xi * hp.n_t * hp.n_x > (1LL << 40)) { msg = "problem too large"; return SG_ERR_ARG; }
+  if ((long long)hp.n_xi * hp.n_t * hp.n_x > (1LL << 40) || hp.n_x >= (1LL << 31) || hp.n_cells >= (1LL << 31)) {
+    msg = "problem too large";
+    return SG_ERR_ARG;
+  }
   // active coefficient terms (first appearance order)
   hp.mus.clear();
   const int n_pieces = (int)pieces.size();

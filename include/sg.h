@@ -374,22 +374,38 @@ sg_status sg_stat_errors(sg_ctx* ctx, const double* mean, const double* var, dou
  * mc-variance-estimator-unbiased; Algorithm 1).  For every sample xi_s the
  * deterministic heat equation with a(x, xi_s) = sum_mu a_mu(x) Psi_mu(xi_s) and
  * the manufactured forcing f(x, t, xi_s) of sg_set_exact is marched over all
- * slabs of the context (same mesh, Q_k and dG(r)).  `batch` samples are solved
- * together: one apply launch covers the whole batch, FGMRES(30) iterates on
- * the batch to rtol with a mean-operator V-cycle as preconditioner.
+ * slabs of the context (same mesh, Q_k and dG(r)).  All samples form one
+ * block-diagonal system per slab: one Monte-Carlo apply launch covers every
+ * sample (in tiles of `batch` samples), FGMRES(10) iterates on the whole
+ * system to rtol with a graph-captured mean-operator V-cycle as
+ * preconditioner.  Samples are split into groups solved one after another
+ * only when the device memory cannot hold them at once.
  *   xi        HOST n_samples x M standard-normal samples
- *   batch     samples per batch, 1..512
+ *   batch     samples per tile of the apply launch, 1..512 (reduced to fit
+ *             shared memory)
  *   mg_precision  SG_PREC_FP64, SG_PREC_FP32 or SG_PREC_BF16 V-cycle
  *   mean_T, var_T  DEVICE n_x doubles out: nodal sample mean and unbiased
  *             sample variance of u(x, T)
  *   u_T       DEVICE n_samples x N_t x n_x doubles out (last slab of every
  *             sample), or NULL
- *   st        statistics out (may be NULL)
- * Needs sg_set_exact.  Allocates and frees per-batch device workspaces.
+ *   st        statistics out (may be NULL; batches = sample groups)
+ * Needs sg_set_exact.  Allocates and frees its device workspaces.
  * Synchronous. */
 sg_status mc_solve_batch(sg_ctx* ctx, int n_samples, const double* xi, int batch, int mg_precision,
                          double rtol, int max_it, double* mean_T, double* var_T, double* u_T,
                          sg_mc_stats* st, sg_stream stream);
+
+/* mc_solve_meshes - mc_solve_batch for samples on several meshes at once
+ * (up to 4 contexts of the same dimension, degrees, slabs, T and coefficient
+ * terms; mesh sizes may differ): the samples of every mesh join ONE system
+ * per slab, ONE apply launch covers every (mesh, sample tile, cell) unit, and
+ * each mesh keeps its own mean-operator V-cycle.  Per mesh p: ctxs[p],
+ * n_samples[p], xi[p] (HOST n_samples[p] x M), mean_T[p], var_T[p] (DEVICE
+ * n_x[p] doubles out), u_T[p] (DEVICE or NULL; u_T itself may be NULL).
+ * Other arguments and behaviour as mc_solve_batch.  Synchronous. */
+sg_status mc_solve_meshes(int n_meshes, sg_ctx* const* ctxs, const int* n_samples, const double* const* xi,
+                          int tile, int mg_precision, double rtol, int max_it, double* const* mean_T,
+                          double* const* var_T, double* const* u_T, sg_mc_stats* st, sg_stream stream);
 
 /* sg_get_info - sizes and launch shape of a context (host struct out). */
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out);

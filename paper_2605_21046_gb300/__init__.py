@@ -403,6 +403,32 @@ def mc_solve_batch(ctx, xi, batch=256, mg_precision=SG_PREC_FP32, rtol=1e-8, max
     return mean, var, u_T, {name: getattr(st, name) for name, _ in _abi.sg_mc_stats._fields_}
 
 
+def mc_solve_meshes(ctxs, xis, tile=64, mg_precision=SG_PREC_FP32, rtol=1e-8, max_it=500, keep_paths=False,
+                    stream=None):
+    """Monte-Carlo on several meshes in one system per slab: ``ctxs`` and
+    ``xis`` (numpy n_samples_p x M arrays) per mesh.  Returns
+    (means, vars, paths or None per mesh, stats)."""
+    import torch
+    P = len(ctxs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xs = [np.ascontiguousarray(x, dtype=np.float64) for x in xis]
+    means = [torch.empty(c.info["n_x"], dtype=torch.float64, device=dev) for c in ctxs]
+    vars_ = [torch.empty(c.info["n_x"], dtype=torch.float64, device=dev) for c in ctxs]
+    paths = [torch.empty(x.shape[0] * c.info["n_t"] * c.info["n_x"], dtype=torch.float64, device=dev)
+             for c, x in zip(ctxs, xs)] if keep_paths else None
+    vp = C.c_void_p
+    h = (vp * P)(*[c.handle.value for c in ctxs])
+    ns = (C.c_int * P)(*[x.shape[0] for x in xs])
+    xp = (C.POINTER(C.c_double) * P)(*[x.ctypes.data_as(C.POINTER(C.c_double)) for x in xs])
+    mp = (vp * P)(*[t.data_ptr() for t in means])
+    vv = (vp * P)(*[t.data_ptr() for t in vars_])
+    up = (vp * P)(*[t.data_ptr() for t in paths]) if paths is not None else None
+    st = _abi.sg_mc_stats()
+    _check(_abi.load().mc_solve_meshes(P, h, ns, xp, int(tile), int(mg_precision), float(rtol), int(max_it), mp, vv,
+                                       up, C.byref(st), C.c_void_p(_stream_handle(stream))), "mc_solve_meshes")
+    return means, vars_, paths, {name: getattr(st, name) for name, _ in _abi.sg_mc_stats._fields_}
+
+
 def sg_autotune(ctx, reps=10):
     """Pick the fastest apply launch shape for this context (sg_autotune)."""
     _check(_abi.load().sg_autotune(ctx.handle, int(reps)), "sg_autotune")

@@ -16,7 +16,7 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
                    "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch",
                    "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient",
-                   "sg_stat_errors"])
+                   "sg_stat_errors", "mc_solve_meshes"])
 
 
 class sg_mesh(C.Structure):
@@ -106,6 +106,10 @@ def load():
     lib.sg_adjoint_gradient.restype = C.c_int
     lib.sg_set_coefficient.argtypes = [vp, C.POINTER(sg_coeff)]
     lib.sg_set_coefficient.restype = C.c_int
+    lib.mc_solve_meshes.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(C.POINTER(C.c_double)),
+                                    C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(vp), C.POINTER(vp),
+                                    C.POINTER(vp), C.POINTER(sg_mc_stats), vp]
+    lib.mc_solve_meshes.restype = C.c_int
     lib.sg_stat_errors.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_double)]
     lib.sg_stat_errors.restype = C.c_int
     lib.sg_autotune.argtypes = [vp, C.c_int]

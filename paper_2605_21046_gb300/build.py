@@ -15,7 +15,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_apply_f64.cu", "sg_apply_dw.cu", "sg_apply_f32.cu", "sg_mg.cu",
-           "sg_krylov.cu", "sg_noalloc.cu", "sg_manufactured.cu", "sg_mc.cu", "sg_adjoint.cu", "sg_api.cu"]
+           "sg_krylov.cu", "sg_noalloc.cu", "sg_manufactured.cu", "sg_mc.cu", "sg_mc_apply.cu", "sg_adjoint.cu", "sg_api.cu"]
 
 
 def _nvcc():

@@ -495,6 +495,39 @@ sg_status mc_solve_batch(sg_ctx* ctx, int n_samples, const double* xi, int batch
   return SG_OK;
 }
 
+sg_status mc_solve_meshes(int n_meshes, sg_ctx* const* ctxs, const int* n_samples, const double* const* xi, int tile,
+                          int mg_precision, double rtol, int max_it, double* const* mean_T, double* const* var_T,
+                          double* const* u_T, sg_mc_stats* st, sg_stream stream) {
+  if (n_meshes < 1 || n_meshes > sg::kMcMaxProb || !ctxs || !n_samples || !xi || !mean_T || !var_T)
+    return fail(SG_ERR_ARG, "mc_solve_meshes: 1 to 4 meshes with their samples and outputs");
+  if (tile < 1 || tile > 512) return fail(SG_ERR_ARG, "mc_solve_meshes: tile must be 1..512");
+  if (mg_precision != SG_PREC_FP64 && mg_precision != SG_PREC_FP32 && mg_precision != SG_PREC_BF16)
+    return fail(SG_ERR_ARG, "mc_solve_meshes: mg_precision must be SG_PREC_FP64, SG_PREC_FP32 or SG_PREC_BF16");
+  if (!(rtol > 0.0) || max_it < 1) return fail(SG_ERR_ARG, "mc_solve_meshes: rtol or max_it out of range");
+  std::vector<sg_ctx*> cs;
+  std::vector<int> ns;
+  std::vector<const double*> xs;
+  std::vector<double*> mean, var, ut;
+  for (int p = 0; p < n_meshes; ++p) {
+    if (!ctxs[p] || !ctxs[p]->exact) return fail(SG_ERR_ARG, "mc_solve_meshes: every context needs sg_set_exact");
+    if (n_samples[p] < 1 || !xi[p]) return fail(SG_ERR_ARG, "mc_solve_meshes: no samples for a mesh");
+    if (!mean_T[p] || !var_T[p] || !is_device_ptr(mean_T[p]) || !is_device_ptr(var_T[p]) || mean_T[p] == var_T[p])
+      return fail(SG_ERR_ARG, "mc_solve_meshes: mean_T and var_T must be distinct device vectors");
+    if (u_T && u_T[p] && !is_device_ptr(u_T[p])) return fail(SG_ERR_ARG, "mc_solve_meshes: u_T must be device memory");
+    cs.push_back(ctxs[p]);
+    ns.push_back(n_samples[p]);
+    xs.push_back(xi[p]);
+    mean.push_back(mean_T[p]);
+    var.push_back(var_T[p]);
+    ut.push_back(u_T ? u_T[p] : nullptr);
+  }
+  std::string msg;
+  sg_status s = sg::mc_solve_meshes(cs, ns, xs, tile, mg_precision, rtol, max_it, mean, var, ut, st,
+                                    reinterpret_cast<cudaStream_t>(stream), msg);
+  if (s != SG_OK) return fail(s, "mc_solve_meshes: " + msg);
+  return SG_OK;
+}
+
 sg_status sg_get_info(const sg_ctx* ctx, sg_info* out) {
   if (!ctx || !out) return fail(SG_ERR_ARG, "sg_get_info: null argument");
   const sg::HostProblem& hp = ctx->hp;

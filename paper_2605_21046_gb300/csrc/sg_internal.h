@@ -2,6 +2,7 @@
 // tables and the kernel parameter block.  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -139,6 +140,40 @@ cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const App
 // Kernel attribute set-up (max dynamic shared memory).
 cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t smem);
 
+// ---------------------------------------------------------------- Monte-Carlo apply
+// One pathwise problem family of a Monte-Carlo apply launch: S samples of the
+// deterministic slab operator A_t (x) M + B_t (x) K[a(., xi_s)] on one mesh.
+constexpr int kMcMaxProb = 4;
+struct McProblem {
+  const void* x;             // S x N_t x n_x input (IO type of the arithmetic)
+  void* y;                   // output
+  const void* b;             // right-hand side of the residual / accumulate modes
+  const double* ctab;        // [cell][term][NQD]: w_q |J| a_t(x_q) / h_0^2
+  const double* wgt;         // [S][n_terms]: Psi_t(xi_s)
+  const double* amq;         // [NQD][N_t][N_t]: w_q |J| T[i][j] / (tau Bhat_ii)
+  long long n_x;
+  long long unit0;           // first work unit (cell x sample tile) of this problem
+  int n_cells, S, ts, tiles;
+  int nn[3], cells[3];
+  int aniso;
+  double ratio[3];
+};
+struct McParams {
+  McProblem pr[kMcMaxProb];
+  int n_prob, n_terms, chunk, mode, mass_only;
+  long long units;
+  double tb[kMaxNT];
+};
+// Shared memory of the Monte-Carlo apply for a chunk of cells and a sample tile.
+size_t mc_smem_bytes(int dim, int k, int n_t, int ts, int n_terms, int chunk, int value_bytes);
+// w_q |J| T[i][j] / (tau Bhat_ii) for one mesh (T = A_hat, its transpose, or C_t).
+void mc_amq(const HostProblem& hp, const std::vector<double>& T, std::vector<double>& amq);
+// Launches the init kernels of every problem and one Monte-Carlo apply.
+cudaError_t launch_mc_apply(int precision, int dim, int k, int n_t, const McParams& p, int grid, int threads,
+                            size_t smem, cudaStream_t s);
+// Kernel attribute set-up for the Monte-Carlo apply of one shape.
+cudaError_t prepare_mc_kernel(int precision, int dim, int k, int n_t);
+
 // Precision of the apply kernels used inside the multigrid preconditioner.
 constexpr int kPrecF32 = SG_PREC_FP32;
 
@@ -155,6 +190,9 @@ struct MGLevel {
   int* d_gterm = nullptr;
   double* d_gval = nullptr;
   int* d_perm = nullptr;
+  double* d_amq = nullptr;   // Monte-Carlo levels: the time-mass table of the level
+  int mc_chunk = 0, mc_grid = 0, mc_threads = 256;
+  size_t mc_smem = 0;
   void* d_inv = nullptr;     // [class][cell][np][pitch] patch inverses (pitch = np rounded up to 8;
                              //  bf16 when MG::bf16), or coarsest [class][n_int][n_int]
   int vanka_chunk = 0;       // cells per Vanka chunk
@@ -177,6 +215,10 @@ struct MG {
   int requested = SG_PREC_FP64;   // as passed to mg_build (SG_PREC_BF16 included)
   bool bf16 = false;              // patch inverses stored in bf16 (FP32 vectors)
   int n_blk = 0;                  // Vanka mode blocks (modes of one class)
+  int vanka_tile = 0;             // modes per Vanka tile (all of them unless Monte-Carlo)
+  bool mc = false;                // rows are Monte-Carlo samples: residuals by the MC apply
+  int mc_ts = 0;                  // samples per tile of the MC apply
+  double* d_wgt = nullptr;        // [S][n_terms] Psi_t(xi_s)
   int* d_blk_cls = nullptr;
   int* d_blk_alpha = nullptr;
   int nu = 2;
@@ -195,6 +237,11 @@ struct MG {
 // term (used for Monte-Carlo sample batches, whose rows all differ).
 sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega, MG& mg, std::string& msg,
                    bool single_class = false);
+// The mean-operator V-cycle of a Monte-Carlo system whose rows are samples
+// (weights [S][n_terms]): level residuals use the Monte-Carlo apply with ts
+// samples per tile, the Vanka smoother works in tiles of vanka_tile samples.
+sg_status mg_build_mc(const HostProblem& fine, int precision, int nu, double omega, const std::vector<double>& wgt,
+                      int ts, MG& mg, std::string& msg);
 size_t krylov_bytes(long long N, int m);
 void mg_free(MG& mg);
 // z = P^{-1} r for one slab vector (double in, double out) on a stream; with
@@ -222,6 +269,10 @@ struct ExactData {
   double* d_tpk = nullptr;           // 2 * kMaxNT slab scalars
   int* d_zero_rows = nullptr;        // empty coupling table of the transfer apply
 };
+sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector<int>& n_samples,
+                          const std::vector<const double*>& xis, int tile, int mg_precision, double rtol, int max_it,
+                          const std::vector<double*>& mean_T, const std::vector<double*>& var_T,
+                          const std::vector<double*>& u_T, sg_mc_stats* st, cudaStream_t stream, std::string& msg);
 sg_status mc_solve(sg_ctx* parent, int n_samples, const double* xi, int batch, int mg_precision, double rtol,
                    int max_it, double* mean_T, double* var_T, double* u_T, sg_mc_stats* st, cudaStream_t stream,
                    std::string& msg);
@@ -231,6 +282,10 @@ void exact_free(ExactData* e);
 cudaError_t exact_rhs(const HostProblem& hp, const LaunchShape& ls, ExactData& E, const void* ctab, const int* gcol,
                       const int* gterm, const double* gval, const int* perm, int slab, const double* u_prev,
                       double* rhs, cudaStream_t s);
+// rhs += (I (x) C_t (x) M_x) u_prev (nothing on the first slab or without u_prev).
+cudaError_t exact_transfer(const HostProblem& hp, const LaunchShape& ls, ExactData& E, const void* ctab,
+                           const int* gcol, const int* gterm, const double* gval, const int* perm, int slab,
+                           const double* u_prev, double* rhs, cudaStream_t s);
 cudaError_t moments(const HostProblem& hp, const double* u, int node, double* mean, double* var, cudaStream_t s);
 sg_status exact_errors(const HostProblem& hp, const ExactData& E, const double* u_dev, int slab, double err[3],
                        std::string& msg);
@@ -242,6 +297,13 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
                  cudaStream_t s, std::string& msg,
                  cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t), int trans = 0);
 cudaError_t apply_device_ctx_t(sg_ctx* c, const double* x, double* y, cudaStream_t s);
+// Restarted right-preconditioned FGMRES on N unknowns with caller-given apply
+// and preconditioner (both on stream s); workspace of krylov_bytes(N, m).
+sg_status fgmres_core(long long N, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
+                      cudaStream_t s, std::string& msg, const std::function<cudaError_t(const double*, double*)>& apply,
+                      const std::function<cudaError_t(const double*, double*)>& prec, double* workspace);
+// rhs = F^(n) (+ B_0 on slab 0) for hp.n_xi rows of E's load tables (no transfer term).
+cudaError_t exact_rhs_load(const HostProblem& hp, ExactData& E, int slab, double* rhs, cudaStream_t s);
 // Value of a coefficient factor (SG_F_ONE / SIN / POW) at one coordinate.
 double factor_value(int kind, int k, double s);
 // y = y + (I (x) Tm (x) M_x) x on interior rows (y unchanged on Dirichlet rows);

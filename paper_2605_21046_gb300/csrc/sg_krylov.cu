@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -138,7 +139,6 @@ static cudaError_t norm2(const double* w, long long N, double* part, double* out
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
                  cudaStream_t s, std::string& msg,
                  cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t), int trans) {
-  const auto t0 = std::chrono::steady_clock::now();
   const long long N = (long long)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
   const size_t need = krylov_bytes(N, m);
   if (!ctx->d_krylov || ctx->krylov_bytes < need) {
@@ -148,7 +148,19 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
     if (e != cudaSuccess) { msg = "FGMRES workspace allocation failed"; ctx->krylov_bytes = 0; return SG_ERR_OOM; }
     ctx->krylov_bytes = need;
   }
-  Ws ws = carve(ctx->d_krylov, N, m);
+  MG* mg = ctx->mg;
+  sg_status r = fgmres_core(
+      N, b, x, rtol, max_it, m, st, s, msg, [&](const double* in, double* out) { return apply(ctx, in, out, s); },
+      [&](const double* in, double* out) { return mg_apply(*mg, in, out, s, trans); }, ctx->d_krylov);
+  if (st) st->mg_setup_ms = mg ? mg->setup_ms : 0.0;
+  return r;
+}
+
+sg_status fgmres_core(long long N, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
+                      cudaStream_t s, std::string& msg, const std::function<cudaError_t(const double*, double*)>& apply,
+                      const std::function<cudaError_t(const double*, double*)>& prec, double* workspace) {
+  const auto t0 = std::chrono::steady_clock::now();
+  Ws ws = carve(workspace, N, m);
   sg_solve_stats stats;
   std::memset(&stats, 0, sizeof(stats));
   cudaError_t e;
@@ -174,7 +186,7 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
   }
   // r = b - A x
   auto true_residual = [&](double& beta) -> cudaError_t {
-    cudaError_t ee = apply(ctx, x, ws.r, s);
+    cudaError_t ee = apply(x, ws.r);
     if (ee != cudaSuccess) return ee;
     ++stats.vmult_calls;
     k_sub_from<<<grid_n(N), 256, 0, s>>>(b, ws.r, N);
@@ -203,9 +215,9 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
     for (int j = 0; j < m; ++j) {
       double* vj = ws.V + (long long)j * N;
       double* zj = ws.Z + (long long)j * N;
-      CK(mg_apply(*ctx->mg, vj, zj, s, trans));
+      CK(prec(vj, zj));
       ++stats.prec_calls;
-      CK(apply(ctx, zj, ws.w, s));
+      CK(apply(zj, ws.w));
       ++stats.vmult_calls;
       // CGS2
       CK(multidot(ws.w, ws.V, j + 1, N, ws.part, ws.h, s));
@@ -257,7 +269,6 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
   }
   stats.rel_residual = beta / bnorm;
   stats.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  stats.mg_setup_ms = ctx->mg ? ctx->mg->setup_ms : 0.0;
   if (st) *st = stats;
 #undef CK
   return status;

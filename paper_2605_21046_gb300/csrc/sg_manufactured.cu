@@ -255,6 +255,12 @@ sg_status exact_build(const HostProblem& hp, int q, const double* c, const int* 
 cudaError_t exact_rhs(const HostProblem& hp, const LaunchShape& ls, ExactData& E, const void* ctab, const int* gcol,
                       const int* gterm, const double* gval, const int* perm, int slab, const double* u_prev,
                       double* rhs, cudaStream_t s) {
+  cudaError_t e = exact_rhs_load(hp, E, slab, rhs, s);
+  if (e != cudaSuccess) return e;
+  return exact_transfer(hp, ls, E, ctab, gcol, gterm, gval, perm, slab, u_prev, rhs, s);
+}
+
+cudaError_t exact_rhs_load(const HostProblem& hp, ExactData& E, int slab, double* rhs, cudaStream_t s) {
   const int nt = hp.n_t;
   const std::vector<double> nodes = radau_right_nodes(hp.r);
   const int ng = hp.r + (int)E.t_coef.size() + 2;
@@ -277,7 +283,14 @@ cudaError_t exact_rhs(const HostProblem& hp, const LaunchShape& ls, ExactData& E
   if (e != cudaSuccess) return e;
   const long long total = (long long)hp.n_xi * nt * hp.n_x;
   k_rhs_combine<<<grid_of(total), 256, 0, s>>>(E.d_P, E.d_K, rhs, hp.n_xi, nt, hp.n_x, E.d_tpk, E.d_tpk + kMaxNT);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t exact_transfer(const HostProblem& hp, const LaunchShape& ls, ExactData& E, const void* ctab,
+                           const int* gcol, const int* gterm, const double* gval, const int* perm, int slab,
+                           const double* u_prev, double* rhs, cudaStream_t s) {
+  const int nt = hp.n_t;
+  const std::vector<double> nodes = radau_right_nodes(hp.r);
   if (slab == 0 || !u_prev) return cudaSuccess;
   // transfer: rhs += (I (x) C_t (x) M_x) u_prev, C_t[i][j] = v_i(t_{n-1}^+) v_j^{prev}(t_{n-1}^-)
   ApplyParams p;

@@ -3,18 +3,20 @@
 // mc-slab-system, the estimators eqs. mc-mean-estimator and
 // mc-variance-estimator-unbiased, and Algorithm 1).
 //
-// A batch of S samples is solved as one block-diagonal system: every sample is
-// a row of the coupling table with the single diagonal entry
-//     sum_mu Psi_mu(xi_s) a_mu(x)  =  a(x, xi_s),
-// so the apply kernel evaluates all S pathwise operators in one launch, the
-// right-hand side of sample s is the manufactured forcing f(x, t, xi_s) (its
-// load vector is combined on the device from spatial tables per distinct
-// spatial factor of the exact solution), and FGMRES iterates on the batch.
-// The preconditioner is one V-cycle of the mean operator (its residuals use
-// the true sampled operators, its Vanka patches and coarse solve the mean
-// block): per-sample patch inverses would cost samples x cells x patch^2.
-// At t = T the batch mean and sum of squared deviations are merged into the
-// running estimators with Chan's pairwise update (FP64, on the device).
+// All samples of all meshes of a call form ONE block-diagonal system per
+// slab: the Monte-Carlo apply (sg_mc_apply.cu) evaluates every pathwise
+// operator A(xi_s) = A_t (x) M + B_t (x) K[a(., xi_s)] of every mesh in one
+// launch over a queue of (mesh, sample tile, cell) units, the right-hand side
+// of sample s is the manufactured forcing f(x, t, xi_s) (its load vector is
+// combined on the device from spatial tables per distinct spatial factor of
+// the exact solution), and one FGMRES iterates on the whole system.  The
+// preconditioner is, per mesh, one graph-captured V-cycle of the mean operator
+// (its residuals use the true sampled operators, its Vanka patches and coarse
+// solve the mean block): per-sample patch inverses would cost samples x cells
+// x patch^2.  When the device memory cannot hold every sample at once, the
+// samples are split into groups solved one after the other.  At t = T each
+// group's mean and sum of squared deviations are merged into the running
+// estimators with Chan's pairwise update (FP64, on the device).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -208,143 +210,322 @@ void spatial_tables(const HostProblem& hp, const std::vector<std::vector<int>>& 
 
 }  // namespace
 
-sg_status mc_solve(sg_ctx* parent, int n_samples, const double* xi, int batch, int mg_precision, double rtol,
-                   int max_it, double* mean_T, double* var_T, double* u_T, sg_mc_stats* st, cudaStream_t stream,
-                   std::string& msg) {
+namespace {
+
+// One mesh of a Monte-Carlo solve: its samples of the current group, the
+// batch problem (rows = samples), per-sample load tables, the mean-operator
+// V-cycle and the time-mass tables of the apply.
+struct McMesh {
+  sg_ctx* parent = nullptr;
+  int S_total = 0, S = 0, s_begin = 0;
+  const double* xi = nullptr;          // host, S_total x M
+  std::vector<int> group;              // exact-solution mode -> spatial group
+  int ng = 0;
+  double *d_Pg = nullptr, *d_Kg = nullptr;
+  HostProblem hp;
+  ExactData* E = nullptr;
+  MG* mg = nullptr;
+  double *d_wgt = nullptr, *d_amqA = nullptr, *d_amqC = nullptr;
+  long long off = 0, n = 0;
+  double n_done = 0.0;
+};
+
+void free_group(McMesh& m) {
+  if (m.mg) {
+    mg_free(*m.mg);
+    delete m.mg;
+    m.mg = nullptr;
+  }
+  if (m.E) {
+    cudaFree(m.E->d_P);
+    cudaFree(m.E->d_K);
+    cudaFree(m.E->d_tpk);
+    cudaFree(m.E->d_zero_rows);
+    delete m.E;
+    m.E = nullptr;
+  }
+  cudaFree(m.d_wgt);
+  m.d_wgt = nullptr;
+}
+
+}  // namespace
+
+sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector<int>& n_samples,
+                          const std::vector<const double*>& xis, int tile, int mg_precision, double rtol, int max_it,
+                          const std::vector<double*>& mean_T, const std::vector<double*>& var_T,
+                          const std::vector<double*>& u_T, sg_mc_stats* st, cudaStream_t stream, std::string& msg) {
   const auto t0 = std::chrono::steady_clock::now();
-  const HostProblem& ph = parent->hp;
-  const ExactData& ex = *parent->exact;
-  const int M = ph.M, nt = ph.n_t, nq = (int)ex.c.size();
-  // distinct spatial factors of the exact solution
-  std::map<std::vector<int>, int> gid;
-  std::vector<std::vector<int>> gfreq;
-  std::vector<int> group(nq);
-  for (int a = 0; a < nq; ++a) {
-    std::vector<int> f(ex.freq.begin() + 3 * a, ex.freq.begin() + 3 * a + 3);
-    auto it = gid.find(f);
-    if (it == gid.end()) {
-      group[a] = (int)gfreq.size();
-      gid[f] = group[a];
-      gfreq.push_back(f);
-    } else {
-      group[a] = it->second;
+  const int P = (int)parents.size();
+  if (P < 1 || P > kMcMaxProb) { msg = "1 to 4 meshes"; return SG_ERR_ARG; }
+  const HostProblem& h0 = parents[0]->hp;
+  for (int p = 1; p < P; ++p) {
+    const HostProblem& h = parents[p]->hp;
+    if (h.dim != h0.dim || h.k != h0.k || h.r != h0.r || h.n_slabs != h0.n_slabs || h.T != h0.T ||
+        h.n_terms != h0.n_terms || h.M != h0.M) {
+      msg = "meshes of one Monte-Carlo solve need the same dimension, degrees, slabs, T and coefficient terms";
+      return SG_ERR_ARG;
     }
   }
-  const int ng = (int)gfreq.size();
-  std::vector<double> Pg, Kg;
-  spatial_tables(ph, gfreq, Pg, Kg);
-  double *d_Pg = nullptr, *d_Kg = nullptr, *d_wP = nullptr, *d_wK = nullptr;
-  cudaError_t e = cudaMalloc(&d_Pg, Pg.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&d_Kg, Kg.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemcpy(d_Pg, Pg.data(), Pg.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_Kg, Kg.data(), Kg.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&d_wP, (size_t)batch * ng * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&d_wK, (size_t)batch * ph.n_terms * ng * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemsetAsync(mean_T, 0, ph.n_x * sizeof(double), stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(var_T, 0, ph.n_x * sizeof(double), stream);
+  const int nt = h0.n_t, M = h0.M, nterm = h0.n_terms;
+  std::vector<McMesh> ms(P);
+  cudaError_t e = cudaSuccess;
+  sg_status status = SG_OK;
   sg_mc_stats stats;
   std::memset(&stats, 0, sizeof(stats));
-  stats.n_samples = n_samples;
-  sg_status status = SG_OK;
-  double n_done = 0.0;
-  for (int b0 = 0; b0 < n_samples && e == cudaSuccess && status == SG_OK; b0 += batch) {
-    const int S = std::min(batch, n_samples - b0);
-    // the batch problem: rows = samples, diagonal coupling Psi_mu(xi_s)
-    HostProblem hp = ph;
-    hp.n_xi = S;
-    hp.idx.assign((size_t)S * M, 0);
-    hp.g.row.assign(S + 1, 0);
-    hp.g.col.clear();
-    hp.g.term.clear();
-    hp.g.val.clear();
-    std::vector<double> wP((size_t)S * ng, 0.0), wK((size_t)S * ph.n_terms * ng, 0.0);
-    for (int s = 0; s < S; ++s) {
-      const double* xs = xi + (size_t)(b0 + s) * M;
-      std::vector<double> psi_mu(ph.n_terms);
-      for (int t = 0; t < ph.n_terms; ++t) {
-        psi_mu[t] = Psi(ph.mus[t].data(), xs, M);
-        if (psi_mu[t] != 0.0) {
-          hp.g.col.push_back(s);
-          hp.g.term.push_back(t);
-          hp.g.val.push_back(psi_mu[t]);
+  for (int p = 0; p < P; ++p) {
+    McMesh& m = ms[p];
+    m.parent = parents[p];
+    m.S_total = n_samples[p];
+    m.xi = xis[p];
+    stats.n_samples += m.S_total;
+    const ExactData& ex = *m.parent->exact;
+    const int nq = (int)ex.c.size();
+    std::map<std::vector<int>, int> gid;
+    std::vector<std::vector<int>> gfreq;
+    m.group.assign(nq, 0);
+    for (int a = 0; a < nq; ++a) {
+      std::vector<int> f(ex.freq.begin() + 3 * a, ex.freq.begin() + 3 * a + 3);
+      auto it = gid.find(f);
+      if (it == gid.end()) {
+        m.group[a] = (int)gfreq.size();
+        gid[f] = m.group[a];
+        gfreq.push_back(f);
+      } else {
+        m.group[a] = it->second;
+      }
+    }
+    m.ng = (int)gfreq.size();
+    std::vector<double> Pg, Kg, amqA, amqC;
+    spatial_tables(m.parent->hp, gfreq, Pg, Kg);
+    if (e == cudaSuccess) e = cudaMalloc(&m.d_Pg, Pg.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&m.d_Kg, Kg.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_Pg, Pg.data(), Pg.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_Kg, Kg.data(), Kg.size() * sizeof(double), cudaMemcpyHostToDevice);
+    // time-mass tables of the apply (A_hat) and of the transfer (C_t)
+    const HostProblem& h = m.parent->hp;
+    const std::vector<double> nodes = radau_right_nodes(h.r);
+    std::vector<double> Ct((size_t)nt * nt);
+    for (int i = 0; i < nt; ++i)
+      for (int j = 0; j < nt; ++j) Ct[(size_t)i * nt + j] = lagrange(nodes, i, 0.0) * lagrange(nodes, j, 1.0);
+    mc_amq(h, h.A_hat, amqA);
+    mc_amq(h, Ct, amqC);
+    if (e == cudaSuccess) e = cudaMalloc(&m.d_amqA, amqA.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&m.d_amqC, amqC.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_amqA, amqA.data(), amqA.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m.d_amqC, amqC.data(), amqC.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mean_T[p], 0, h.n_x * sizeof(double), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(var_T[p], 0, h.n_x * sizeof(double), stream);
+  }
+  // sample tile of the apply: the largest <= tile whose chunk of 2 cells fits
+  int ts = std::max(1, tile);
+  while (ts > 1 && mc_smem_bytes(h0.dim, h0.k, nt, ts, nterm, 2, 8) > 100 * 1024) ts = (ts + 1) / 2;
+  int chunk = 1;
+  for (int c = 1; c <= 8; ++c)
+    if (mc_smem_bytes(h0.dim, h0.k, nt, ts, nterm, c, 8) <= 100 * 1024) chunk = c;
+  const size_t smem = mc_smem_bytes(h0.dim, h0.k, nt, ts, nterm, chunk, 8);
+  if (e == cudaSuccess) e = prepare_mc_kernel(SG_PREC_FP64, h0.dim, h0.k, nt);
+  // sample groups: all samples in one system unless the device memory says otherwise
+  const int m_restart = 10;
+  double vec_bytes = 0.0;
+  for (int p = 0; p < P; ++p) vec_bytes += (double)ms[p].S_total * nt * ms[p].parent->hp.n_x * sizeof(double);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const double need = vec_bytes * (2 * m_restart + 3 + 2 + 3);
+  const int groups = std::max(1, (int)std::ceil(need / (0.7 * (double)free_b)));
+  const int mgp = mg_precision;
+  double* d_krylov = nullptr;
+  double *U = nullptr, *RHS = nullptr;
+  for (int gi = 0; gi < groups && e == cudaSuccess && status == SG_OK; ++gi) {
+    long long N = 0;
+    for (int p = 0; p < P && e == cudaSuccess && status == SG_OK; ++p) {
+      McMesh& m = ms[p];
+      const HostProblem& ph = m.parent->hp;
+      m.s_begin = (int)((long long)m.S_total * gi / groups);
+      m.S = (int)((long long)m.S_total * (gi + 1) / groups) - m.s_begin;
+      m.off = N;
+      m.n = (long long)m.S * nt * ph.n_x;
+      N += m.n;
+      if (m.S == 0) continue;
+      // the batch problem: rows = samples, diagonal coupling Psi_mu(xi_s)
+      m.hp = ph;
+      m.hp.n_xi = m.S;
+      m.hp.idx.assign((size_t)m.S * M, 0);
+      m.hp.g.row.assign(m.S + 1, 0);
+      m.hp.g.col.clear();
+      m.hp.g.term.clear();
+      m.hp.g.val.clear();
+      m.hp.perm.resize(m.S);
+      const ExactData& ex = *m.parent->exact;
+      const int nq = (int)ex.c.size();
+      std::vector<double> wgt((size_t)m.S * nterm), wP((size_t)m.S * m.ng, 0.0), wK((size_t)m.S * nterm * m.ng, 0.0);
+      for (int s = 0; s < m.S; ++s) {
+        const double* xs = m.xi + (size_t)(m.s_begin + s) * M;
+        for (int t = 0; t < nterm; ++t) {
+          wgt[(size_t)s * nterm + t] = Psi(ph.mus[t].data(), xs, M);
+          if (wgt[(size_t)s * nterm + t] != 0.0) {
+            m.hp.g.col.push_back(s);
+            m.hp.g.term.push_back(t);
+            m.hp.g.val.push_back(wgt[(size_t)s * nterm + t]);
+          }
+        }
+        m.hp.g.row[s + 1] = (int)m.hp.g.col.size();
+        m.hp.perm[s] = s;
+        for (int a = 0; a < nq; ++a) {
+          const double w = ex.c[a] * Psi(&ex.idx_q[(size_t)a * M], xs, M);
+          wP[(size_t)s * m.ng + m.group[a]] += w;
+          for (int t = 0; t < nterm; ++t)
+            wK[((size_t)s * nterm + t) * m.ng + m.group[a]] += wgt[(size_t)s * nterm + t] * w;
         }
       }
-      hp.g.row[s + 1] = (int)hp.g.col.size();
-      for (int a = 0; a < nq; ++a) {
-        const double w = ex.c[a] * Psi(&ex.idx_q[(size_t)a * M], xs, M);
-        wP[(size_t)s * ng + group[a]] += w;
-        for (int t = 0; t < ph.n_terms; ++t) wK[((size_t)s * ph.n_terms + t) * ng + group[a]] += psi_mu[t] * w;
-      }
-    }
-    hp.perm.resize(S);
-    for (int s = 0; s < S; ++s) hp.perm[s] = s;
-    sg_ctx* bc = nullptr;
-    status = make_ctx(std::move(hp), parent->hp.precision, &bc, msg);
-    if (status != SG_OK) break;
-    bc->mg = new MG();
-    status = mg_build(bc->hp, mg_precision, 2, 0.7, *bc->mg, msg, true);
-    if (status == SG_OK) {
-      ExactData* E = new ExactData(*parent->exact);
-      E->d_P = E->d_K = E->d_tpk = nullptr;
-      E->d_zero_rows = nullptr;
-      bc->exact = E;
-      const long long N = (long long)S * nt * ph.n_x;
-      e = cudaMalloc(&E->d_P, (size_t)S * ph.n_x * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&E->d_K, (size_t)S * ph.n_x * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&E->d_tpk, 2 * kMaxNT * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&E->d_zero_rows, (S + 1) * sizeof(int));
-      if (e == cudaSuccess) e = cudaMemsetAsync(E->d_zero_rows, 0, (S + 1) * sizeof(int), stream);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(d_wP, wP.data(), wP.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(d_wK, wK.data(), wK.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
+      // per-sample load tables
+      m.E = new ExactData(ex);
+      m.E->d_P = m.E->d_K = m.E->d_tpk = nullptr;
+      m.E->d_zero_rows = nullptr;
+      double *d_wP = nullptr, *d_wK = nullptr;
+      e = cudaMalloc(&m.E->d_P, (size_t)m.S * ph.n_x * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&m.E->d_K, (size_t)m.S * ph.n_x * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&m.E->d_tpk, 2 * kMaxNT * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&d_wP, wP.size() * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&d_wK, wK.size() * sizeof(double));
+      if (e == cudaSuccess) e = cudaMemcpy(d_wP, wP.data(), wP.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d_wK, wK.data(), wK.size() * sizeof(double), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) {
-        k_mc_combine<<<grid_n((long long)S * ph.n_x), 256, 0, stream>>>(d_Pg, d_Kg, d_wP, d_wK, S, ng, ph.n_terms,
-                                                                         ph.n_x, E->d_P, E->d_K);
+        k_mc_combine<<<grid_n((long long)m.S * ph.n_x), 256, 0, stream>>>(m.d_Pg, m.d_Kg, d_wP, d_wK, m.S, m.ng, nterm,
+                                                                           ph.n_x, m.E->d_P, m.E->d_K);
         e = cudaGetLastError();
-      }
-      double *u = nullptr, *rhs = nullptr;
-      if (e == cudaSuccess) e = cudaMalloc(&u, N * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&rhs, N * sizeof(double));
-      if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, N * sizeof(double), stream);
-      for (int n = 0; n < ph.n_slabs && e == cudaSuccess && status == SG_OK; ++n) {
-        e = exact_rhs(bc->hp, bc->ls, *E, bc->d_ctab, bc->d_gcol, bc->d_gterm, bc->d_gval, bc->d_perm, n,
-                      n > 0 ? u : nullptr, rhs, stream);
-        if (e != cudaSuccess) break;
-        sg_solve_stats ss;
-        status = fgmres(bc, rhs, u, rtol, max_it, 30, &ss, stream, msg, &apply_device_ctx);
-        stats.total_iterations += ss.iterations;
-        stats.max_slab_iterations = std::max(stats.max_slab_iterations, ss.iterations);
-        stats.max_rel_residual = std::max(stats.max_rel_residual, ss.rel_residual);
-      }
-      if (e == cudaSuccess && status == SG_OK) {
-        k_mc_merge<<<grid_n(ph.n_x), 256, 0, stream>>>(u, S, nt, nt - 1, ph.n_x, n_done, mean_T, var_T);
-        e = cudaGetLastError();
-        if (e == cudaSuccess && u_T)
-          e = cudaMemcpyAsync(u_T + (size_t)b0 * nt * ph.n_x, u, N * sizeof(double), cudaMemcpyDeviceToDevice, stream);
-        n_done += S;
       }
       if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-      cudaFree(u);
-      cudaFree(rhs);
+      cudaFree(d_wP);
+      cudaFree(d_wK);
+      if (e == cudaSuccess) e = cudaMalloc(&m.d_wgt, wgt.size() * sizeof(double));
+      if (e == cudaSuccess) e = cudaMemcpy(m.d_wgt, wgt.data(), wgt.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) break;
+      // mean-operator V-cycle over all samples of the group
+      m.mg = new MG();
+      status = mg_build_mc(m.hp, mgp, 2, 0.7, wgt, std::min(ts, 32), *m.mg, msg);
     }
-    ++stats.batches;
-    destroy_ctx(bc);
-  }
-  if (e == cudaSuccess && status == SG_OK) {
-    k_mc_finish<<<grid_n(ph.n_x), 256, 0, stream>>>(var_T, ph.n_x, n_done);
-    e = cudaGetLastError();
+    if (e != cudaSuccess || status != SG_OK) break;
+    // one system for every mesh of the group
+    cudaFree(U);
+    cudaFree(RHS);
+    cudaFree(d_krylov);
+    U = RHS = d_krylov = nullptr;
+    e = cudaMalloc(&U, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&RHS, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&d_krylov), krylov_bytes(N, m_restart));
+    if (e == cudaSuccess) e = cudaMemsetAsync(U, 0, N * sizeof(double), stream);
+    if (e != cudaSuccess) break;
+    McParams base;
+    std::memset(&base, 0, sizeof(base));
+    long long units = 0;
+    for (int p = 0; p < P; ++p) {
+      McMesh& m = ms[p];
+      if (m.S == 0) continue;
+      McProblem& pr = base.pr[base.n_prob++];
+      const HostProblem& ph = m.parent->hp;
+      pr.ctab = m.parent->d_ctab;
+      pr.wgt = m.d_wgt;
+      pr.n_x = ph.n_x;
+      pr.unit0 = units;
+      pr.n_cells = (int)ph.n_cells;
+      pr.S = m.S;
+      pr.ts = std::min(ts, m.S);
+      pr.tiles = (m.S + pr.ts - 1) / pr.ts;
+      for (int d = 0; d < 3; ++d) {
+        pr.nn[d] = ph.nn[d];
+        pr.cells[d] = ph.cells[d];
+        pr.ratio[d] = d < ph.dim ? (ph.h[0] * ph.h[0]) / (ph.h[d] * ph.h[d]) : 0.0;
+      }
+      pr.aniso = 0;
+      for (int d = 1; d < ph.dim; ++d) pr.aniso |= ph.h[d] != ph.h[0];
+      units += (long long)pr.tiles * pr.n_cells;
+    }
+    base.n_terms = nterm;
+    base.chunk = chunk;
+    base.units = units;
+    for (int i = 0; i < nt; ++i) base.tb[i] = h0.tau * h0.B_hat[i * nt + i];
+    const int grid = (int)std::max<long long>(1, std::min<long long>(units / chunk, 152LL * 2));
+    auto mc_launch = [&](const double* x, double* y, const double* b, int mode, bool transfer) -> cudaError_t {
+      McParams q = base;
+      q.mode = mode;
+      q.mass_only = transfer ? 1 : 0;
+      int j = 0;
+      for (int p = 0; p < P; ++p) {
+        McMesh& m = ms[p];
+        if (m.S == 0) continue;
+        q.pr[j].x = x + m.off;
+        q.pr[j].y = y + m.off;
+        q.pr[j].b = b ? b + m.off : nullptr;
+        q.pr[j].amq = transfer ? m.d_amqC : m.d_amqA;
+        ++j;
+      }
+      return launch_mc_apply(SG_PREC_FP64, h0.dim, h0.k, nt, q, grid, 256, smem, stream);
+    };
+    auto apply = [&](const double* in, double* out) { return mc_launch(in, out, nullptr, kApplyPlain, false); };
+    auto prec = [&](const double* in, double* out) -> cudaError_t {
+      for (int p = 0; p < P; ++p) {
+        McMesh& m = ms[p];
+        if (m.S == 0) continue;
+        cudaError_t ee = mg_apply(*m.mg, in + m.off, out + m.off, stream, 0);
+        if (ee != cudaSuccess) return ee;
+      }
+      return cudaSuccess;
+    };
+    for (int n = 0; n < h0.n_slabs && e == cudaSuccess && status == SG_OK; ++n) {
+      for (int p = 0; p < P && e == cudaSuccess; ++p)
+        if (ms[p].S > 0) e = exact_rhs_load(ms[p].hp, *ms[p].E, n, RHS + ms[p].off, stream);
+      if (e == cudaSuccess && n > 0) e = mc_launch(U, RHS, RHS, kApplyAccumulate, true);
+      if (e != cudaSuccess) break;
+      sg_solve_stats ss;
+      status = fgmres_core(N, RHS, U, rtol, max_it, m_restart, &ss, stream, msg, apply, prec, d_krylov);
+      stats.total_iterations += ss.iterations;
+      stats.max_slab_iterations = std::max(stats.max_slab_iterations, ss.iterations);
+      stats.max_rel_residual = std::max(stats.max_rel_residual, ss.rel_residual);
+    }
+    for (int p = 0; p < P && e == cudaSuccess && status == SG_OK; ++p) {
+      McMesh& m = ms[p];
+      if (m.S == 0) continue;
+      const long long nx = m.parent->hp.n_x;
+      k_mc_merge<<<grid_n(nx), 256, 0, stream>>>(U + m.off, m.S, nt, nt - 1, nx, m.n_done, mean_T[p], var_T[p]);
+      e = cudaGetLastError();
+      if (e == cudaSuccess && u_T[p])
+        e = cudaMemcpyAsync(u_T[p] + (size_t)m.s_begin * nt * nx, U + m.off, m.n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, stream);
+      m.n_done += m.S;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    for (McMesh& m : ms) free_group(m);
+    ++stats.batches;
   }
-  cudaFree(d_Pg);
-  cudaFree(d_Kg);
-  cudaFree(d_wP);
-  cudaFree(d_wK);
+  for (int p = 0; p < P && e == cudaSuccess && status == SG_OK; ++p) {
+    k_mc_finish<<<grid_n(ms[p].parent->hp.n_x), 256, 0, stream>>>(var_T[p], ms[p].parent->hp.n_x, ms[p].n_done);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  for (McMesh& m : ms) {
+    free_group(m);
+    cudaFree(m.d_Pg);
+    cudaFree(m.d_Kg);
+    cudaFree(m.d_amqA);
+    cudaFree(m.d_amqC);
+  }
+  cudaFree(U);
+  cudaFree(RHS);
+  cudaFree(d_krylov);
   stats.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = stats;
   if (e != cudaSuccess) {
-    msg = std::string("Monte-Carlo batch: ") + cudaGetErrorString(e);
+    msg = std::string("Monte-Carlo solve: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
   }
   return status;
+}
+
+sg_status mc_solve(sg_ctx* parent, int n_samples, const double* xi, int batch, int mg_precision, double rtol,
+                   int max_it, double* mean_T, double* var_T, double* u_T, sg_mc_stats* st, cudaStream_t stream,
+                   std::string& msg) {
+  return mc_solve_meshes({parent}, {n_samples}, {xi}, batch, mg_precision, rtol, max_it, {mean_T}, {var_T}, {u_T}, st,
+                         stream, msg);
 }
 
 }  // namespace sg

@@ -1,0 +1,245 @@
+// The Monte-Carlo apply: y = A(xi_s) x_s for every sample s of one or more
+// meshes in ONE launch (paper, Sec. 5: the pathwise slab system eq.
+// mc-slab-system, A(xi) = A_t (x) M_x + B_t (x) K[a(., xi)] with
+// a(x, xi) = sum_mu a_mu(x) Psi_mu(xi), eq. coeff_expansion).
+//
+// The work is a queue of units (problem, sample tile, cell): persistent CTAs
+// take even contiguous ranges of it and walk them in chunks of cells of one
+// problem and tile.  A chunk stages the tile's vectors of its cells in shared
+// memory and runs the phases of the SG cell kernel (gather, sum-factorised
+// interpolation, point work, transposed sum factorisation, atomic scatter),
+// with a point kernel that needs no chaos coupling: at a Gauss point the
+// sample's coefficient is sum_t Psi_t(xi_s) a_t(x_q), times the gradients of
+// its own vectors, plus the time-node mass coupling.  Samples never couple, so
+// any number of them (and several meshes of one shape) share a launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sg_apply_kernel.cuh"
+
+namespace sg {
+
+namespace {
+
+template <typename IO>
+__global__ void mc_init_y(const IO* __restrict__ x, IO* y, const IO* b, int mode, int n_x, int nnx, int nny,
+                          int nnz, int dim) {
+  const long long off = (long long)blockIdx.y * n_x;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
+    const long long idx = off + m;
+    if (mode == kApplyAccumulate) {
+      y[idx] = b[idx];
+      continue;
+    }
+    const int ix = m % nnx, r = m / nnx;
+    const int iy = r % nny, iz = r / nny;
+    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
+    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
+    const IO v = bd ? x[idx] : IO(0);
+    y[idx] = mode == kApplyResidual ? b[idx] - v : v;
+  }
+}
+
+template <class A, int DIM, int K, int NT>
+__global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
+  using T = typename A::T;
+  using IO = typename A::IO;
+  using Sh = Shape<DIM, K>;
+  constexpr int NQD = Sh::NQD, NKD = Sh::NKD, NC = Sh::NC, N = Sh::N;
+  constexpr int SLOT = NC * NQD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int C = p.chunk, nterm = p.n_terms;
+  int ts_max = 0;
+  for (int q = 0; q < p.n_prob; ++q) ts_max = max(ts_max, p.pr[q].ts);
+  T* Qs = reinterpret_cast<T*>(smem_raw);                       // [C][ts*NT][SLOT]
+  T* Cs = Qs + (size_t)C * ts_max * NT * SLOT;                  // [C][term][NQD]
+  T* Wt = Cs + (size_t)C * nterm * NQD;                         // [ts][term]
+  T* Amq = Wt + (size_t)ts_max * nterm;                         // [NQD][NT][NT]
+  const long long u_begin = (long long)blockIdx.x * p.units / gridDim.x;
+  const long long u_end = (long long)(blockIdx.x + 1) * p.units / gridDim.x;
+  int cur_prob = -1, cur_tile = -1;
+  for (long long u = u_begin; u < u_end;) {
+    int pi = 0;
+    while (pi + 1 < p.n_prob && u >= p.pr[pi + 1].unit0) ++pi;
+    const McProblem& P = p.pr[pi];
+    const long long lu = u - P.unit0;
+    const int tile = (int)(lu / P.n_cells);
+    const int cell0 = (int)(lu - (long long)tile * P.n_cells);
+    const int nc = (int)min((long long)min(C, P.n_cells - cell0), u_end - u);
+    const int s0 = tile * P.ts, ns = min(P.ts, P.S - s0);
+    const int VT = ns * NT;
+    const IO* __restrict__ xin = static_cast<const IO*>(P.x);
+    IO* __restrict__ yout = static_cast<IO*>(P.y);
+    const int nnx = P.nn[0], nny = P.nn[1], nnz_ = P.nn[2];
+    __syncthreads();   // the previous chunk is done with shared memory
+    if (pi != cur_prob || tile != cur_tile) {
+      for (int e = tid; e < ns * nterm; e += nthr) Wt[e] = A::in(P.wgt[(size_t)s0 * nterm + e]);
+      if (pi != cur_prob)
+        for (int e = tid; e < NQD * NT * NT; e += nthr) Amq[e] = A::in(P.amq[e]);
+      cur_prob = pi;
+      cur_tile = tile;
+    }
+    // phase 0: gather
+    for (int idx = tid; idx < nc * nterm * NQD; idx += nthr)
+      Cs[idx] = A::in(P.ctab[(size_t)cell0 * nterm * NQD + idx]);
+    for (int idx = tid; idx < nc * VT * NKD; idx += nthr) {
+      const int a = idx % NKD;
+      const int cv = idx / NKD;
+      const int v = cv % VT, c = cv / VT;
+      const int gc = cell0 + c;
+      const int cx = gc % P.cells[0], cy = (gc / P.cells[0]) % P.cells[1], cz = gc / (P.cells[0] * P.cells[1]);
+      const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
+      bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+      if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
+      T val = A::zero();
+      if (interior) val = A::in(xin[(long long)(s0 * NT + v) * P.n_x + ((long long)gz * nny + gy) * nnx + gx]);
+      Qs[(size_t)cv * SLOT + a] = val;
+    }
+    __syncthreads();
+    // phase 1: values and reference gradients at the Gauss points
+    for (int it = tid; it < nc * VT; it += nthr) {
+      T* q = Qs + (size_t)it * SLOT;
+      T uv[NKD];
+#pragma unroll
+      for (int a = 0; a < NKD; ++a) uv[a] = q[a];
+      forward_cell<A, DIM, K>(uv, q);
+    }
+    __syncthreads();
+    // phase 2: per (cell, point, sample): mass coupling and a(x_q, xi_s) grad u
+    for (int it = tid; it < nc * NQD * ns; it += nthr) {
+      const int q = it % NQD;
+      const int rest = it / NQD;
+      const int sl = rest % ns, c = rest / ns;
+      T* base = Qs + ((size_t)c * VT + (size_t)sl * NT) * SLOT + q;
+      T uv[NT], out[NT][NC];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) uv[j] = base[(size_t)j * SLOT];
+      const T* am = Amq + q * NT * NT;
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        T sacc = A::mul(am[i * NT], uv[0]);
+#pragma unroll
+        for (int j = 1; j < NT; ++j) A::fma(am[i * NT + j], uv[j], sacc);
+        out[i][0] = A::fin(sacc);
+      }
+      if (p.mass_only) {
+#pragma unroll
+        for (int i = 0; i < NT; ++i)
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) out[i][1 + d] = A::zero();
+      } else {
+        const T* cq = Cs + (size_t)c * nterm * NQD + q;
+        T acoef = A::mul(Wt[sl * nterm], cq[0]);
+        for (int t = 1; t < nterm; ++t) A::fma(Wt[sl * nterm + t], cq[t * NQD], acoef);
+        acoef = A::fin(acoef);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          T ad = acoef;
+          if (P.aniso && d > 0) ad = A::fin(A::mul(acoef, A::in(P.ratio[d])));
+#pragma unroll
+          for (int i = 0; i < NT; ++i) out[i][1 + d] = A::fin(A::mul(ad, base[(size_t)i * SLOT + (1 + d) * NQD]));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NT; ++i)
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) base[(size_t)i * SLOT + cc * NQD] = out[i][cc];
+    }
+    __syncthreads();
+    // phase 3: back to the nodes
+    for (int it = tid; it < nc * VT; it += nthr) backward_cell<A, DIM, K>(Qs + (size_t)it * SLOT);
+    __syncthreads();
+    // phase 4: scale by tau Bhat_ii and add into y
+    for (int idx = tid; idx < nc * VT * NKD; idx += nthr) {
+      const int a = idx % NKD;
+      const int cv = idx / NKD;
+      const int v = cv % VT, c = cv / VT;
+      const int gc = cell0 + c;
+      const int cx = gc % P.cells[0], cy = (gc / P.cells[0]) % P.cells[1], cz = gc / (P.cells[0] * P.cells[1]);
+      const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
+      bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
+      if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
+      if (interior) {
+        T val = A::mul(A::in(p.tb[v % NT]), Qs[(size_t)cv * SLOT + a]);
+        if (p.mode == kApplyResidual) val = A::neg(val);
+        A::add_out(yout + (long long)(s0 * NT + v) * P.n_x + ((long long)gz * nny + gy) * nnx + gx, val);
+      }
+    }
+    u += nc;
+  }
+}
+
+void* select_mc(int precision, int dim, int k, int n_t) {
+#define SG_M(D, KK, TT)                                                                              \
+  if (dim == D && k == KK && n_t == TT)                                                              \
+    return precision == kPrecF32 ? reinterpret_cast<void*>(&mc_apply_kernel<F32, D, KK, TT>)         \
+                                 : reinterpret_cast<void*>(&mc_apply_kernel<F64, D, KK, TT>);
+  SG_M(2, 1, 1) SG_M(2, 1, 2) SG_M(2, 1, 3) SG_M(2, 1, 4)
+  SG_M(2, 2, 1) SG_M(2, 2, 2) SG_M(2, 2, 3) SG_M(2, 2, 4)
+  SG_M(2, 3, 1) SG_M(2, 3, 2) SG_M(2, 3, 3) SG_M(2, 3, 4)
+  SG_M(3, 1, 1) SG_M(3, 1, 2) SG_M(3, 2, 1) SG_M(3, 2, 2)
+#undef SG_M
+  return nullptr;
+}
+
+}  // namespace
+
+size_t mc_smem_bytes(int dim, int k, int n_t, int ts, int n_terms, int chunk, int value_bytes) {
+  const size_t nqd = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
+  const size_t vals = (size_t)chunk * ts * n_t * (1 + dim) * nqd + (size_t)chunk * n_terms * nqd +
+                      (size_t)ts * n_terms + nqd * n_t * n_t;
+  return vals * value_bytes;
+}
+
+void mc_amq(const HostProblem& hp, const std::vector<double>& Tm, std::vector<double>& amq) {
+  const int nq = hp.k + 1, nqd = hp.dim == 2 ? nq * nq : nq * nq * nq, nt = hp.n_t;
+  double detJ = 1.0;
+  for (int d = 0; d < hp.dim; ++d) detJ *= hp.h[d];
+  amq.assign((size_t)nqd * nt * nt, 0.0);
+  for (int qd = 0; qd < nqd; ++qd) {
+    const int qi[3] = {qd % nq, (qd / nq) % nq, qd / (nq * nq)};
+    double w = detJ;
+    for (int d = 0; d < hp.dim; ++d) w *= hp.wq[qi[d]];
+    for (int i = 0; i < nt; ++i) {
+      const double tb = hp.tau * hp.B_hat[i * nt + i];
+      for (int j = 0; j < nt; ++j) amq[((size_t)qd * nt + i) * nt + j] = w * Tm[(size_t)i * nt + j] / tb;
+    }
+  }
+}
+
+cudaError_t prepare_mc_kernel(int precision, int dim, int k, int n_t) {
+  void* f = select_mc(precision, dim, k, n_t);
+  if (!f) return cudaErrorInvalidValue;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+cudaError_t launch_mc_apply(int precision, int dim, int k, int n_t, const McParams& p, int grid, int threads,
+                            size_t smem, cudaStream_t s) {
+  void* f = select_mc(precision, dim, k, n_t);
+  if (!f) return cudaErrorInvalidValue;
+  for (int q = 0; q < p.n_prob; ++q) {
+    const McProblem& P = p.pr[q];
+    const dim3 ig((unsigned)std::max<long long>(1, std::min<long long>((P.n_x + 255) / 256, 64)),
+                  (unsigned)(P.S * n_t));
+    if (precision == kPrecF32)
+      mc_init_y<float><<<ig, 256, 0, s>>>(static_cast<const float*>(P.x), static_cast<float*>(P.y),
+                                          static_cast<const float*>(P.b), p.mode, (int)P.n_x, P.nn[0], P.nn[1],
+                                          P.nn[2], dim);
+    else
+      mc_init_y<double><<<ig, 256, 0, s>>>(static_cast<const double*>(P.x), static_cast<double*>(P.y),
+                                           static_cast<const double*>(P.b), p.mode, (int)P.n_x, P.nn[0], P.nn[1],
+                                           P.nn[2], dim);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<McParams*>(&p)};
+  return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
+}
+
+}  // namespace sg

@@ -82,6 +82,7 @@ struct VankaParams {
   const int* blk_cls;       // [n_blk] class of every mode block
   const int* blk_alpha;     // [n_blk][kVankaVB] modes, -1 padded
   int n_blk, n_xi, chunk, npp;
+  int tile_modes, n_tiles;  // modes per tile (single class when n_tiles > 1)
   long long n_x, n_cells;
   int cells[3], nn[3];
   T omega;
@@ -107,17 +108,24 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
   constexpr int VB = kVankaVB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int V = p.n_xi * NT, C = p.chunk;
+  const int VTM = p.tile_modes * NT, C = p.chunk;
   const int LX = C * K + 1;                         // chunk nodes along x
   constexpr int LYZ = DIM == 2 ? N : N * N;         // nodes across y (and z)
   const int LN = LX * LYZ;
-  T* Rl = reinterpret_cast<T*>(smem_raw);           // [V][LN]
-  T* Zc = Rl + (size_t)V * LN;                      // [V][LN]
+  T* Rl = reinterpret_cast<T*>(smem_raw);           // [tile vectors][LN]
+  T* Zc = Rl + (size_t)VTM * LN;                    // [tile vectors][LN]
   const W* inv = static_cast<const W*>(p.inv);
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
   const int cpr = (p.cells[0] + C - 1) / C;         // chunks per row of cells
   const long long n_chunks = (long long)cpr * p.cells[1] * p.cells[2];
-  for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+  for (long long unit = blockIdx.x; unit < n_chunks * p.n_tiles; unit += gridDim.x) {
+    const long long ch = unit % n_chunks;
+    const int tile = (int)(unit / n_chunks);
+    const int m0 = tile * p.tile_modes, tm = min(p.tile_modes, p.n_xi - m0);
+    const int V = tm * NT;                          // this tile's vectors, from m0 * NT on
+    const int nb = p.n_tiles == 1 ? p.n_blk : (tm + VB - 1) / VB;
+    const int b0 = p.n_tiles == 1 ? 0 : m0 / VB;
+    const long long voff = (long long)m0 * NT;
     const int cx0 = (int)(ch % cpr) * C;
     const long long row = ch / cpr;
     const int cy = (int)(row % p.cells[1]), cz = (int)(row / p.cells[1]);
@@ -133,18 +141,18 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
         const int gx = cx0 * K + lx, gy = cy * K + lyz % N, gz = DIM == 3 ? cz * K + lyz / N : 0;
         bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
         if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
-        if (in) val = p.r[(long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx];
+        if (in) val = p.r[(voff + v) * p.n_x + ((long long)gz * nny + gy) * nnx + gx];
       }
       Rl[idx] = val;
       Zc[idx] = T(0);
     }
     __syncthreads();
     // patch rows
-    const int items = nc * NP * p.n_blk;
+    const int items = nc * NP * nb;
     for (int it = tid; it < items; it += nthr) {
       const int rho = it % NP;
       const int cb = it / NP;
-      const int c = cb % nc, b = cb / nc;
+      const int c = cb % nc, b = b0 + cb / nc;
       const int i = rho / NKD, a = rho - i * NKD;
       const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
       const int gx = (cx0 + c) * K + ax, gy = cy * K + ay, gz = DIM == 3 ? cz * K + az : 0;
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
       const W* M = inv + ((long long)p.blk_cls[b] * p.n_cells + cell) * NP * p.npp;
       int al[VB];
 #pragma unroll
-      for (int u = 0; u < VB; ++u) al[u] = p.blk_alpha[b * VB + u];
+      for (int u = 0; u < VB; ++u) al[u] = p.blk_alpha[b * VB + u] < 0 ? -1 : p.blk_alpha[b * VB + u] - m0;
       T acc[VB];
 #pragma unroll
       for (int u = 0; u < VB; ++u) acc[u] = T(0);
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
       if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
       if (!in) continue;
       const T val = Zc[idx];
-      T* dst = p.x + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx;
+      T* dst = p.x + (voff + v) * p.n_x + ((long long)gz * nny + gy) * nnx + gx;
       const bool priv = lx > 0 && lx < lxn - 1 && ly > 0 && ly < K && (DIM == 2 || (lz > 0 && lz < K));
       if (priv) *dst += val;
       else atomicAdd(dst, val);
@@ -654,6 +662,39 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans);
 template <typename T>
 cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
   MGLevel& L = mg.lv[l];
+  if (mg.mc) {
+    McParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.n_prob = 1;
+    McProblem& P = q.pr[0];
+    P.x = L.d_x;
+    P.y = L.d_r;
+    P.b = L.d_b;
+    P.ctab = static_cast<const double*>(L.d_ctab);
+    P.wgt = mg.d_wgt;
+    P.amq = L.d_amq;
+    P.n_x = L.hp.n_x;
+    P.unit0 = 0;
+    P.n_cells = (int)L.hp.n_cells;
+    P.S = L.hp.n_xi;
+    P.ts = mg.mc_ts;
+    P.tiles = (P.S + P.ts - 1) / P.ts;
+    for (int d = 0; d < 3; ++d) {
+      P.nn[d] = L.hp.nn[d];
+      P.cells[d] = L.hp.cells[d];
+      P.ratio[d] = d < L.hp.dim ? (L.hp.h[0] * L.hp.h[0]) / (L.hp.h[d] * L.hp.h[d]) : 0.0;
+    }
+    P.aniso = 0;
+    for (int d = 1; d < L.hp.dim; ++d) P.aniso |= L.hp.h[d] != L.hp.h[0];
+    q.n_terms = L.hp.n_terms;
+    q.chunk = L.mc_chunk;
+    q.mode = kApplyResidual;
+    q.mass_only = 0;
+    q.units = (long long)P.tiles * P.n_cells;
+    for (int i = 0; i < L.hp.n_t; ++i) q.tb[i] = L.hp.tau * L.hp.B_hat[i * L.hp.n_t + i];
+    (void)trans;
+    return launch_mc_apply(mg.precision, L.hp.dim, L.hp.k, L.hp.n_t, q, L.mc_grid, L.mc_threads, L.mc_smem, s);
+  }
   ApplyParams p;
   fill_apply_params(L.hp, L.ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, trans, p);
   p.b = L.d_b;
@@ -677,18 +718,18 @@ __global__ void mg_first_residual(const T* __restrict__ b, T* __restrict__ r, lo
 }
 
 // Cells per Vanka chunk: up to 8, within the shared-memory budget.
-int vanka_chunk(const MGLevel& L, size_t value_bytes, size_t budget) {
+int vanka_chunk(const MGLevel& L, int tile_modes, size_t value_bytes, size_t budget) {
   const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
-  const size_t V = (size_t)L.hp.n_xi * L.hp.n_t;
+  const size_t V = (size_t)tile_modes * L.hp.n_t;
   int best = 0;
   for (int c = 1; c <= std::min(8, L.hp.cells[0]); ++c)
     if (2 * V * (size_t)(c * L.hp.k + 1) * lyz * value_bytes <= budget) best = c;
   return best;
 }
 
-size_t vanka_smem(const MGLevel& L, int chunk, size_t value_bytes) {
+size_t vanka_smem(const MGLevel& L, int tile_modes, int chunk, size_t value_bytes) {
   const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
-  return 2 * (size_t)L.hp.n_xi * L.hp.n_t * (size_t)(chunk * L.hp.k + 1) * lyz * value_bytes;
+  return 2 * (size_t)tile_modes * L.hp.n_t * (size_t)(chunk * L.hp.k + 1) * lyz * value_bytes;
 }
 
 template <typename T, typename W, int DIM, int K, int NT>
@@ -702,6 +743,8 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   p.n_blk = mg.n_blk;
   p.n_xi = L.hp.n_xi;
   p.chunk = L.vanka_chunk;
+  p.tile_modes = mg.vanka_tile;
+  p.n_tiles = (L.hp.n_xi + mg.vanka_tile - 1) / mg.vanka_tile;
   p.npp = vanka_row_pitch(L.np);
   p.n_x = L.hp.n_x;
   p.n_cells = L.hp.n_cells;
@@ -710,10 +753,10 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
     p.nn[d] = L.hp.nn[d];
   }
   p.omega = T(mg.omega);
-  const size_t smem = vanka_smem(L, L.vanka_chunk, sizeof(T));
+  const size_t smem = vanka_smem(L, mg.vanka_tile, L.vanka_chunk, sizeof(T));
   const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
-  const long long chunks = (long long)cpr * L.hp.cells[1] * L.hp.cells[2];
-  const int grid = (int)std::min<long long>(chunks, 152LL * 8);
+  const long long units = (long long)cpr * L.hp.cells[1] * L.hp.cells[2] * p.n_tiles;
+  const int grid = (int)std::min<long long>(units, 152LL * 8);
   auto kern = trans ? &mg_vanka<T, W, DIM, K, NT, true> : &mg_vanka<T, W, DIM, K, NT, false>;
   kern<<<grid, 256, smem, s>>>(p);
   return cudaGetLastError();
@@ -954,10 +997,12 @@ void mg_free(MG& mg) {
   cudaFree(mg.d_cls);
   cudaFree(mg.d_blk_cls);
   cudaFree(mg.d_blk_alpha);
+  cudaFree(mg.d_wgt);
+  mg.d_wgt = nullptr;
   mg.d_blk_cls = mg.d_blk_alpha = nullptr;
   for (MGLevel& L : mg.lv) {
     cudaFree(L.d_ctab); cudaFree(L.d_grow); cudaFree(L.d_gcol); cudaFree(L.d_gterm); cudaFree(L.d_gval);
-    cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner);
+    cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner); cudaFree(L.d_amq);
     cudaFree(L.d_x); cudaFree(L.d_b); cudaFree(L.d_r);
     for (int d = 0; d < 3; ++d) {
       cudaFree(L.d_pc[d]); cudaFree(L.d_pw[d]); cudaFree(L.d_rptr[d]); cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
@@ -1015,6 +1060,7 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     }
   }
   mg.n_blk = (int)blk_cls.size();
+  if (mg.vanka_tile <= 0 || !single_class) mg.vanka_tile = fine.n_xi;
   // level problems
   std::vector<HostProblem> hps;
   hps.push_back(fine);
@@ -1057,9 +1103,25 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     for (int a = 0; a < L.hp.n_xi; ++a) L.hp.perm[a] = a;
     L.hp.precision = precision;
     L.coarsest = l + 1 == mg.lv.size();
-    sg_status st = plan_apply(L.hp, L.ls, msg);
-    if (st != SG_OK) return st;
-    if ((e = prepare_apply_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t, L.ls.smem)) != cudaSuccess) break;
+    if (mg.mc) {
+      // Monte-Carlo rows: the level residual is the Monte-Carlo apply
+      std::vector<double> amq;
+      mc_amq(L.hp, L.hp.A_hat, amq);
+      if ((e = upload_vec(&L.d_amq, amq)) != cudaSuccess) break;
+      if ((e = prepare_mc_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t)) != cudaSuccess) break;
+      const int vbm = precision == kPrecF32 ? 4 : 8;
+      L.mc_chunk = 0;
+      for (int c = 1; c <= 8; ++c)
+        if (mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, mg.mc_ts, L.hp.n_terms, c, vbm) <= 100 * 1024) L.mc_chunk = c;
+      if (L.mc_chunk == 0) { msg = "Monte-Carlo tile does not fit in shared memory"; return SG_ERR_UNSUPPORTED; }
+      L.mc_smem = mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, mg.mc_ts, L.hp.n_terms, L.mc_chunk, vbm);
+      const long long units = (long long)((L.hp.n_xi + mg.mc_ts - 1) / mg.mc_ts) * L.hp.n_cells;
+      L.mc_grid = (int)std::max<long long>(1, std::min<long long>(units / std::max(1, L.mc_chunk), 152LL * 4));
+    } else {
+      sg_status st = plan_apply(L.hp, L.ls, msg);
+      if (st != SG_OK) return st;
+      if ((e = prepare_apply_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t, L.ls.smem)) != cudaSuccess) break;
+    }
     const int n = L.hp.k + 1;
     const int nkd = L.hp.dim == 2 ? n * n : n * n * n;
     L.np = L.hp.n_t * nkd;
@@ -1101,8 +1163,8 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       const size_t vb = precision == kPrecF32 ? 4 : 8;
-      L.vanka_chunk = vanka_chunk(L, vb, 100 * 1024);
-      if (L.vanka_chunk == 0) L.vanka_chunk = vanka_chunk(L, vb, (size_t)optin - 1024);
+      L.vanka_chunk = vanka_chunk(L, mg.vanka_tile, vb, 100 * 1024);
+      if (L.vanka_chunk == 0) L.vanka_chunk = vanka_chunk(L, mg.vanka_tile, vb, (size_t)optin - 1024);
       if (L.vanka_chunk == 0) {
         msg = "Vanka smoother: one cell with all rows does not fit in shared memory (fewer samples per batch)";
         return SG_ERR_UNSUPPORTED;
@@ -1149,7 +1211,7 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_cls, blk_cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_alpha, blk_alpha);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = tune_level_applies(mg);
+  if (e == cudaSuccess && !mg.mc) e = tune_level_applies(mg);
   if (e == cudaSuccess) e = tune_vanka(mg);
   if (e != cudaSuccess) {
     msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);
@@ -1157,6 +1219,25 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
   }
   mg.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return SG_OK;
+}
+
+sg_status mg_build_mc(const HostProblem& fine, int precision, int nu, double omega, const std::vector<double>& wgt,
+                      int ts, MG& mg, std::string& msg) {
+  if (ts < 1 || (size_t)fine.n_xi * fine.n_terms != wgt.size()) {
+    msg = "Monte-Carlo weights or tile size inconsistent";
+    return SG_ERR_ARG;
+  }
+  mg.mc = true;
+  mg.mc_ts = std::min(ts, fine.n_xi);
+  // Vanka tiles: a multiple of 8 samples whose patch data fit beside each other
+  mg.vanka_tile = std::min(fine.n_xi, 64);
+  if (mg.vanka_tile < fine.n_xi) mg.vanka_tile = 64;
+  cudaError_t e = upload_vec(&mg.d_wgt, wgt);
+  if (e != cudaSuccess) {
+    msg = cudaGetErrorString(e);
+    return SG_ERR_CUDA;
+  }
+  return mg_build(fine, precision, nu, omega, mg, msg, true);
 }
 
 cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans) {

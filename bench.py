@@ -166,6 +166,39 @@ def oracle_apply_rate(spec, budget_s=15.0, min_reps=1):
     return n * reps / wall, reps, wall, max(1, round(cpu / wall))
 
 
+def _oracle_rate_worker(args):
+    """One process of the all-cores oracle timing (spawned; CPU only)."""
+    spec, budget = args
+    return oracle_apply_rate(spec, budget_s=budget)
+
+
+def oracle_apply_rate_all_cores(spec, budget_s=10.0, procs=None):
+    """The oracle's apply, as it stands, run as independent applies in one
+    process per host core at the same time: (unknowns/s summed, processes)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    procs = procs or os.cpu_count() or 1
+    # spawn: the parent already holds a CUDA context; a dead worker raises
+    # (BrokenProcessPool) instead of leaving the pool waiting
+    with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(_oracle_rate_worker, (spec, budget_s)) for _ in range(procs)]
+        res = [f.result(timeout=budget_s + 300) for f in futs]
+    return sum(r[0] for r in res), procs
+
+
+def oracle_solve_ms(spec, rtol=1e-8):
+    """The oracle's slab solve (FGMRES, exact block-Jacobi LU) of one seeded
+    right-hand side: (wall ms including the factorisation, iterations)."""
+    from oracle import operator, solver
+    from paper_2605_21046_gb300 import inputs
+    t0 = time.perf_counter()
+    p = operator.SGProblem(spec)
+    pre = solver.BlockJacobiLU(p)
+    b = inputs.random_rhs(spec)
+    _, its, _ = solver.fgmres(p, b, pre.apply, rtol=rtol)
+    return 1e3 * (time.perf_counter() - t0), its
+
+
 def run_reference(args, world, rank):
     spec = workload()
     from paper_2605_21046_gb300 import inputs
@@ -332,6 +365,16 @@ def run_ours(args, world, rank, local):
         rate, reps, wall, cores = oracle_apply_rate(spec, budget_s=args.cpu_seconds)
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{reps} full oracle applies of the {n}-unknown workload in {wall:.1f} s"}
+        if not args.no_cpu_all_cores:
+            rate_all, procs = oracle_apply_rate_all_cores(spec, budget_s=min(args.cpu_seconds, 10.0))
+            cpu["all_cores"] = {"value": rate_all / 1e9, "unit": UNIT, "processes": procs,
+                                "sample": "one process per host core, each timing full oracle applies for 10 s"}
+        if solve is not None:
+            for name, sp in (("2d-q1-8x8-M2P2", inputs.config_small_2d_q1()), (spec["name"], spec)):
+                ms, its = oracle_solve_ms(sp)
+                solve.setdefault("cpu_oracle", {})[name] = {
+                    "ms_per_slab": ms, "iterations": its, "cores": 1,
+                    "solver": "oracle FGMRES(30) + exact block-Jacobi sparse LU, factorisation included"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -486,7 +529,8 @@ def next_mc_vs_sg(sg, torch, inputs, n_samples=4096, tile=64):
     return {"row": "batched Monte-Carlo vs SG", "slabs": 50, "samples": n_samples,
             "xi": "default_rng(4096).standard_normal((4096, 4))", "rtol": 1e-8,
             "mc": {"ms": mc_ms, "one_system": "both meshes, all samples, one apply launch per FGMRES step",
-                   "tile": tile, "groups": st["batches"], "fgmres_iterations_total": st["total_iterations"],
+                   "tile_cap": tile, "tile_autotuned": st["tile"], "chunk_autotuned": st["chunk"],
+                   "groups": st["batches"], "fgmres_iterations_total": st["total_iterations"],
                    "max_slab_iterations": st["max_slab_iterations"], "max_rel_residual": st["max_rel_residual"]},
             "sg_ms_both_meshes": sg_total, "sg_faster": sg_total < mc_ms, "meshes": rows}
 
@@ -578,6 +622,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-dw", action="store_true", help="skip the double-word variant")
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")

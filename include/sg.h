@@ -155,6 +155,8 @@ typedef struct {
   int max_slab_iterations; /* largest per-slab iteration count               */
   double max_rel_residual; /* largest final relative residual of a slab      */
   double solve_ms;         /* wall time of the call                          */
+  int tile;                /* samples per tile of the apply (autotuned)      */
+  int chunk;               /* cells per chunk of the apply (autotuned)       */
 } sg_mc_stats;
 
 /* Statistics of one sg_adjoint_gradient call (host struct out). */

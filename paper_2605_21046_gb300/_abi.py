@@ -51,7 +51,8 @@ class sg_adjoint_stats(C.Structure):
 
 class sg_mc_stats(C.Structure):
     _fields_ = [("n_samples", C.c_int), ("batches", C.c_int), ("total_iterations", C.c_int),
-                ("max_slab_iterations", C.c_int), ("max_rel_residual", C.c_double), ("solve_ms", C.c_double)]
+                ("max_slab_iterations", C.c_int), ("max_rel_residual", C.c_double), ("solve_ms", C.c_double),
+                ("tile", C.c_int), ("chunk", C.c_int)]
 
 
 _lib = None

@@ -316,13 +316,28 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
     if (e == cudaSuccess) e = cudaMemsetAsync(mean_T[p], 0, h.n_x * sizeof(double), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(var_T[p], 0, h.n_x * sizeof(double), stream);
   }
-  // sample tile of the apply: the largest <= tile whose chunk of 2 cells fits
-  int ts = std::max(1, tile);
-  while (ts > 1 && mc_smem_bytes(h0.dim, h0.k, nt, ts, nterm, 2, 8) > 100 * 1024) ts = (ts + 1) / 2;
-  int chunk = 1;
-  for (int c = 1; c <= 8; ++c)
-    if (mc_smem_bytes(h0.dim, h0.k, nt, ts, nterm, c, 8) <= 100 * 1024) chunk = c;
-  const size_t smem = mc_smem_bytes(h0.dim, h0.k, nt, ts, nterm, chunk, 8);
+  // apply tile shapes: (samples per tile, cells per chunk) candidates within the
+  // shared-memory budget; the fastest on the first group's system is kept
+  struct Shape2 {
+    int ts, chunk;
+    size_t smem;
+  };
+  std::vector<Shape2> cand;
+  for (int t = 8; t <= std::max(8, tile); t *= 2) {
+    const int tt = std::min(t, std::max(1, tile));
+    int best_c = 0;
+    for (int c = 1; c <= 8; ++c)
+      if (mc_smem_bytes(h0.dim, h0.k, nt, tt, nterm, c, 8) <= 100 * 1024) best_c = c;
+    if (best_c == 0) break;
+    cand.push_back({tt, best_c, mc_smem_bytes(h0.dim, h0.k, nt, tt, nterm, best_c, 8)});
+    if (best_c > 2) cand.push_back({tt, best_c / 2, mc_smem_bytes(h0.dim, h0.k, nt, tt, nterm, best_c / 2, 8)});
+    if (tt == tile) break;
+  }
+  if (cand.empty()) cand.push_back({1, 1, mc_smem_bytes(h0.dim, h0.k, nt, 1, nterm, 1, 8)});
+  int ts = cand.back().ts, chunk = cand.back().chunk;
+  size_t smem = cand.back().smem;
+  bool tuned = cand.size() == 1;
+  stats.max_rel_residual = 0.0;
   if (e == cudaSuccess) e = prepare_mc_kernel(SG_PREC_FP64, h0.dim, h0.k, nt);
   // sample groups: all samples in one system unless the device memory says otherwise
   const int m_restart = 10;
@@ -416,35 +431,40 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
     if (e == cudaSuccess) e = cudaMemsetAsync(U, 0, N * sizeof(double), stream);
     if (e != cudaSuccess) break;
     McParams base;
-    std::memset(&base, 0, sizeof(base));
     long long units = 0;
-    for (int p = 0; p < P; ++p) {
-      McMesh& m = ms[p];
-      if (m.S == 0) continue;
-      McProblem& pr = base.pr[base.n_prob++];
-      const HostProblem& ph = m.parent->hp;
-      pr.ctab = m.parent->d_ctab;
-      pr.wgt = m.d_wgt;
-      pr.n_x = ph.n_x;
-      pr.unit0 = units;
-      pr.n_cells = (int)ph.n_cells;
-      pr.S = m.S;
-      pr.ts = std::min(ts, m.S);
-      pr.tiles = (m.S + pr.ts - 1) / pr.ts;
-      for (int d = 0; d < 3; ++d) {
-        pr.nn[d] = ph.nn[d];
-        pr.cells[d] = ph.cells[d];
-        pr.ratio[d] = d < ph.dim ? (ph.h[0] * ph.h[0]) / (ph.h[d] * ph.h[d]) : 0.0;
+    int grid = 1;
+    auto build_base = [&]() {
+      std::memset(&base, 0, sizeof(base));
+      units = 0;
+      for (int p = 0; p < P; ++p) {
+        McMesh& m = ms[p];
+        if (m.S == 0) continue;
+        McProblem& pr = base.pr[base.n_prob++];
+        const HostProblem& ph = m.parent->hp;
+        pr.ctab = m.parent->d_ctab;
+        pr.wgt = m.d_wgt;
+        pr.n_x = ph.n_x;
+        pr.unit0 = units;
+        pr.n_cells = (int)ph.n_cells;
+        pr.S = m.S;
+        pr.ts = std::min(ts, m.S);
+        pr.tiles = (m.S + pr.ts - 1) / pr.ts;
+        for (int d = 0; d < 3; ++d) {
+          pr.nn[d] = ph.nn[d];
+          pr.cells[d] = ph.cells[d];
+          pr.ratio[d] = d < ph.dim ? (ph.h[0] * ph.h[0]) / (ph.h[d] * ph.h[d]) : 0.0;
+        }
+        pr.aniso = 0;
+        for (int d = 1; d < ph.dim; ++d) pr.aniso |= ph.h[d] != ph.h[0];
+        units += (long long)pr.tiles * pr.n_cells;
       }
-      pr.aniso = 0;
-      for (int d = 1; d < ph.dim; ++d) pr.aniso |= ph.h[d] != ph.h[0];
-      units += (long long)pr.tiles * pr.n_cells;
-    }
-    base.n_terms = nterm;
-    base.chunk = chunk;
-    base.units = units;
-    for (int i = 0; i < nt; ++i) base.tb[i] = h0.tau * h0.B_hat[i * nt + i];
-    const int grid = (int)std::max<long long>(1, std::min<long long>(units / chunk, 152LL * 2));
+      base.n_terms = nterm;
+      base.chunk = chunk;
+      base.units = units;
+      for (int i = 0; i < nt; ++i) base.tb[i] = h0.tau * h0.B_hat[i * nt + i];
+      grid = (int)std::max<long long>(1, std::min<long long>(units / chunk, 152LL * 2));
+    };
+    build_base();
     auto mc_launch = [&](const double* x, double* y, const double* b, int mode, bool transfer) -> cudaError_t {
       McParams q = base;
       q.mode = mode;
@@ -462,6 +482,42 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
       return launch_mc_apply(SG_PREC_FP64, h0.dim, h0.k, nt, q, grid, 256, smem, stream);
     };
     auto apply = [&](const double* in, double* out) { return mc_launch(in, out, nullptr, kApplyPlain, false); };
+    if (!tuned) {
+      // time one apply per candidate shape (after one untimed launch) on this system
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      e = cudaEventCreate(&ea);
+      if (e == cudaSuccess) e = cudaEventCreate(&eb);
+      float best_ms = 1e30f;
+      Shape2 best = cand.back();
+      for (const Shape2& c : cand) {
+        if (e != cudaSuccess) break;
+        ts = c.ts;
+        chunk = c.chunk;
+        smem = c.smem;
+        build_base();
+        e = apply(U, RHS);
+        if (e == cudaSuccess) e = cudaEventRecord(ea, stream);
+        if (e == cudaSuccess) e = apply(U, RHS);
+        if (e == cudaSuccess) e = cudaEventRecord(eb, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(eb);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ea, eb);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+      if (ea) cudaEventDestroy(ea);
+      if (eb) cudaEventDestroy(eb);
+      ts = best.ts;
+      chunk = best.chunk;
+      smem = best.smem;
+      build_base();
+      tuned = true;
+      stats.tile = ts;
+      stats.chunk = chunk;
+      if (e != cudaSuccess) break;
+    }
     auto prec = [&](const double* in, double* out) -> cudaError_t {
       for (int p = 0; p < P; ++p) {
         McMesh& m = ms[p];

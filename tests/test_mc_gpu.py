@@ -139,6 +139,7 @@ def test_more_samples_than_one_tile_family(cuda):
     se = np.sqrt((c[1:] ** 2).sum() * phi.max() ** 2 / N)
     assert np.abs(mean.cpu().numpy() - c[0] * phi).max() <= 4 * se + 5e-3
     assert st["max_rel_residual"] <= 1e-10 and st["batches"] == 1
+    assert 8 <= st["tile"] <= 64 and st["chunk"] >= 1          # the autotuned apply shape
 
 
 def test_mean_within_standard_errors_of_exact(cuda):

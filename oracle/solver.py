@@ -131,7 +131,7 @@ class Level:
                 inv.append(self.factor_round(m) if self.factor_round is not None else m)
             self.patch_inv.append(inv)
 
-    def smooth(self, cls, x, b):
+    def smooth(self, cls, x, b, omega=OMEGA):
         r = b - self.A[cls] @ x
         dx = np.zeros_like(x)
         for dofs, inv in zip(self.patches, self.patch_inv[cls]):
@@ -139,7 +139,7 @@ class Level:
                 dx[dofs] += inv @ r[dofs]
         nz = self.mult > 0
         x = x.copy()
-        x[nz] += OMEGA * dx[nz] / self.mult[nz]
+        x[nz] += omega * dx[nz] / self.mult[nz]
         return x
 
 
@@ -184,8 +184,9 @@ class Multigrid:
     """Block-Jacobi (in alpha) preconditioner: one V-cycle of the diagonal
     block A_alpha for every chaos mode and both time nodes at once."""
 
-    def __init__(self, problem, factor_round=None):
+    def __init__(self, problem, factor_round=None, nu=NU, omega=OMEGA):
         self.p = problem
+        self.nu, self.omega = nu, omega
         specs = coarse_specs(problem.spec)
         self.keys, self.cls = diagonal_classes(problem.G)
         self.levels = [Level(s, problem.At, problem.Bt, self.keys, i == len(specs) - 1, factor_round)
@@ -202,16 +203,16 @@ class Multigrid:
             return x
         x = np.zeros_like(b)
         x[bm] = b[bm]
-        for _ in range(NU):
-            x = L.smooth(cls, x, b)
+        for _ in range(self.nu):
+            x = L.smooth(cls, x, b, self.omega)
         r = b - L.A[cls] @ x
         P = self.P[lev]
         rc = np.concatenate([P.T @ r[i * n_x:(i + 1) * n_x] for i in range(n_t)])
         ec = self.vcycle_block(cls, rc, lev + 1)
         nc = self.levels[lev + 1].n_x
         x = x + np.concatenate([P @ ec[i * nc:(i + 1) * nc] for i in range(n_t)])
-        for _ in range(NU):
-            x = L.smooth(cls, x, b)
+        for _ in range(self.nu):
+            x = L.smooth(cls, x, b, self.omega)
         return x
 
     def apply(self, r):

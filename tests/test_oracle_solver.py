@@ -145,3 +145,23 @@ def test_vcycle_with_bf16_factors_still_contracts():
         rates.append(np.linalg.norm(e) / n0)
     assert rates[0] < 0.2 and rates[1] < 0.3
     assert abs(rates[1] - rates[0]) < 0.1
+
+
+def test_vcycle_one_smoothing_step_contracts():
+    """nu = 1, omega = 0.9: the V-cycle is still a contraction for the block
+    operator, a little weaker than nu = 2."""
+    spec = spec2((16, 16), k=2)
+    p = operator.SGProblem(spec)
+    rates = []
+    for nu, om in ((2, 0.7), (1, 0.9)):
+        mg = solver.Multigrid(p, nu=nu, omega=om)
+        L = mg.levels[0]
+        A = L.A[0]
+        e = np.random.default_rng(3).standard_normal(A.shape[0])
+        e[np.tile(L.bmask, L.n_t)] = 0.0
+        for _ in range(3):
+            e = e - mg.vcycle_block(0, A @ e)
+        n0 = np.linalg.norm(e)
+        e = e - mg.vcycle_block(0, A @ e)
+        rates.append(np.linalg.norm(e) / n0)
+    assert rates[0] < rates[1] < 0.3

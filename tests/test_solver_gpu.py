@@ -76,6 +76,27 @@ def test_vcycle_matches_oracle(cuda, name, prec):
     assert _rel(z2.cpu().numpy(), got) < 1e-6
 
 
+@pytest.mark.parametrize("name", ["2d-q2-16x16", "2d-q2-paper-15classes", "3d-q2-4x4x4"])
+def test_vcycle_one_smoothing_step_matches_oracle(cuda, name):
+    """nu = 1, omega = 0.9 (the pair the benchmarks use) against the oracle's
+    V-cycle with the same pair, FP64 levels."""
+    torch = cuda
+    spec = VCYCLE_CASES[name]
+    p = operator.SGProblem(spec)
+    mg = solver.Multigrid(p, nu=1, omega=0.9)
+    r = np.random.default_rng(6).uniform(-1, 1, p.shape)
+    want = mg.apply(r).reshape(-1)
+    ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_setup(ctx, sg.SG_PREC_FP64, 1, 0.9)
+    rd = torch.from_numpy(r.reshape(-1).copy()).cuda()
+    zd = torch.empty_like(rd)
+    sg.sg_vcycle(ctx, rd, zd)
+    torch.cuda.synchronize()
+    got = zd.cpu().numpy()
+    ctx.destroy()
+    assert _rel(got, want) < 1e-10
+
+
 @pytest.mark.parametrize("prec", list(MG_PREC))
 def test_solve_small_matches_direct(cuda, prec):
     torch = cuda

@@ -94,6 +94,11 @@ template <>
 __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
 
 template <typename T, typename W>
+__device__ __forceinline__ T conv(W w) { return (T)w; }
+template <>
+__device__ __forceinline__ float conv<float, __nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
+
+template <typename T, typename W>
 __device__ __forceinline__ T wval(const W* p) { return (T)to_f<W>(*p); }
 template <>
 __device__ __forceinline__ double wval<double, double>(const double* p) { return __ldg(p); }
@@ -168,15 +173,38 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
 #pragma unroll
       for (int u = 0; u < VB; ++u) acc[u] = T(0);
       const int lbase = c * K;                       // local x of the cell's first node
+      if constexpr (TRANS) {
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        const int iq = q / NKD, aq = q - iq * NKD;
-        const int ln = (lbase + aq % N) + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
-        const T w = TRANS ? wval<T, W>(M + (size_t)q * p.npp + rho) : wval<T, W>(M + (size_t)rho * p.npp + q);
-        const T* rq = Rl + (size_t)iq * LN + ln;
+        for (int q = 0; q < NP; ++q) {
+          const int iq = q / NKD, aq = q - iq * NKD;
+          const int ln = (lbase + aq % N) + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
+          const T w = wval<T, W>(M + (size_t)q * p.npp + rho);
+          const T* rq = Rl + (size_t)iq * LN + ln;
 #pragma unroll
-        for (int u = 0; u < VB; ++u)
-          if (al[u] >= 0) acc[u] += w * rq[(size_t)al[u] * NT * LN];
+          for (int u = 0; u < VB; ++u)
+            if (al[u] >= 0) acc[u] += w * rq[(size_t)al[u] * NT * LN];
+        }
+      } else {
+        // the row in 16-byte pieces (rows are padded to a multiple of 8 values)
+        constexpr int QV = 16 / (int)sizeof(W);
+        const uint4* mrow = reinterpret_cast<const uint4*>(M + (size_t)rho * p.npp);
+#pragma unroll
+        for (int q0 = 0; q0 < NP; q0 += QV) {
+          const uint4 raw = __ldg(mrow + q0 / QV);
+          const W* wv = reinterpret_cast<const W*>(&raw);
+#pragma unroll
+          for (int k = 0; k < QV; ++k) {
+            const int q = q0 + k;
+            if (q >= NP) break;
+            const int iq = q / NKD, aq = q - iq * NKD;
+            const int ln = (lbase + aq % N) + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
+            const T w = conv<T, W>(wv[k]);
+            const T* rq = Rl + (size_t)iq * LN + ln;
+#pragma unroll
+            for (int u = 0; u < VB; ++u)
+              if (al[u] >= 0) acc[u] += w * rq[(size_t)al[u] * NT * LN];
+          }
+        }
       }
       const int mult = (gx % K == 0 ? 2 : 1) * (gy % K == 0 ? 2 : 1) * (DIM == 3 && gz % K == 0 ? 2 : 1);
       const T sc = p.omega / T(mult);

@@ -5,7 +5,7 @@ sg_vcycle is a fixed linear map: the GPU result is compared element by element
 with the oracle's V-cycle (FP64 levels: 1e-10 relative; FP32 levels: 1e-4;
 FP32 levels with bf16-stored Vanka inverses: 1e-4 against the oracle's V-cycle
 whose inverses are rounded to bf16 in the same way).
-sg_solve_slab is checked by the property the benchmark spec fixes for solves: the
+sg_solve_slab is checked by the property required of every solve: the
 true residual ||b - A x|| / ||b||, evaluated by the oracle's operator, is at
 most the requested tolerance (1e-8 at scale, 1e-10 on the small case), and the
 solution matches a sparse direct solve where one is affordable."""

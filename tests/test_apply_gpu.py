@@ -53,6 +53,9 @@ FULL_CASES = {
     "3d-q1-5x4x3": small(3, (5, 4, 3), 1, 1, 2, 2),
     "3d-q2-4x3x5": small(3, (4, 3, 5), 2, 1, 3, 2, hi=(1.0, 0.6, 1.3)),
     "3d-q2-r0-3x3x3": small(3, (3, 3, 3), 2, 0, 2, 1),
+    # 495 chaos modes (M = 4, P = 8), close to the 512-mode limit: phase 2 then
+    # runs one point per round with up to 3 rows per thread
+    "2d-q1-4x4-M4P8-495modes": small(2, (4, 4), 1, 1, 4, 8),
 }
 
 
@@ -156,6 +159,16 @@ def test_repeat_is_stable(cuda):
     b = gpu_apply(cuda, spec, x, ctx=ctx)
     ctx.destroy()
     assert _rel(a, b) < 1e-15
+
+
+def test_more_than_512_modes_is_refused(cuda):
+    """M = 8, P = 4 has 495 modes (accepted); M = 5, P = 7 has 792 (refused at
+    set-up, before anything is launched)."""
+    ok = sg.sg_setup_spec(small(2, (2, 2), 1, 1, 8, 4))
+    assert ok.info["n_xi"] == 495
+    ok.destroy()
+    with pytest.raises(sg.SGError, match="512"):
+        sg.sg_setup_spec(small(2, (2, 2), 1, 1, 5, 7))
 
 
 def test_errors_are_reported_not_faulted(cuda):

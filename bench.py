@@ -590,6 +590,45 @@ def next_adjoint(sg, torch, inputs, fd_rel_step=1e-6):
             "fd_relative_step": fd_rel_step, "fd_checks": fd}
 
 
+def next_vcycle(sg, torch, inputs, profile_range=False):
+    """One V-cycle of the block-Jacobi multigrid (all modes at once) on the
+    64x64 Q2 P=3 and 32^3 Q2 P=3 workloads, per precision: device ms per
+    V-cycle (10 graph launches after 3 warm-up ones).  With profile_range the
+    last FP32 3D V-cycle is bracketed by cudaProfilerStart/Stop."""
+    out = {}
+    for wname, maker in (("2d-q2-64x64-M4P3", inputs.config_2d_q2_64), ("3d-q2-32x32x32-M3P3", inputs.config_3d_q2_32)):
+        spec = maker()
+        ctx = sg.sg_setup_spec(spec)
+        n = ctx.info["n_unknowns"]
+        r = torch.rand(n, dtype=torch.float64, device="cuda")
+        z = torch.empty_like(r)
+        row = {}
+        for pname, prec in (("fp64", sg.SG_PREC_FP64), ("fp32", sg.SG_PREC_FP32), ("bf16_factors", sg.SG_PREC_BF16)):
+            for nu, om in ((2, 0.7), (MG_NU, MG_OMEGA)):
+                sg.sg_mg_setup(ctx, prec, nu, om)
+                for _ in range(3):
+                    sg.sg_vcycle(ctx, r, z)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(10):
+                    sg.sg_vcycle(ctx, r, z)
+                b.record()
+                torch.cuda.synchronize()
+                row[f"{pname}_nu{nu}"] = a.elapsed_time(b) / 10
+        if profile_range and wname.startswith("3d"):
+            sg.sg_mg_setup(ctx, sg.SG_PREC_FP32, 2, 0.7)
+            sg.sg_vcycle(ctx, r, z)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            sg.sg_vcycle(ctx, r, z)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        ctx.destroy()
+        out[wname] = row
+    return {"row": "V-cycle", "unit": "ms per V-cycle", "workloads": out}
+
+
 def run_next(args, world, rank, local):
     import torch
     import paper_2605_21046_gb300 as sg
@@ -608,6 +647,8 @@ def run_next(args, world, rank, local):
                 out = next_mc_vs_sg(sg, torch, inputs, n_samples=args.mc_samples)
             elif row == "adjoint":
                 out = next_adjoint(sg, torch, inputs)
+            elif row == "vcycle":
+                out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range)
             else:
                 raise ValueError(row)
         except sg.SGError as ex:

@@ -190,7 +190,11 @@ struct MGLevel {
   int* d_gterm = nullptr;
   double* d_gval = nullptr;
   int* d_perm = nullptr;
-  double* d_amq = nullptr;   // Monte-Carlo levels: the time-mass table of the level
+  double* d_amq = nullptr;   // time-mass tables of the level's diagonal apply (A_t and A_t^T)
+  double* d_amqT = nullptr;
+  int mc_ts = 0;             // rows per tile of the level's diagonal apply
+  bool use_diag = true;      // residual by the diagonal apply (else the SG cell kernel, ls)
+  bool chunk_ok = false;     // the SG cell kernel has a launch shape for this level
   int mc_chunk = 0, mc_grid = 0, mc_threads = 256;
   size_t mc_smem = 0;
   void* d_inv = nullptr;     // [class][cell][np][pitch] patch inverses (pitch = np rounded up to 8;

@@ -690,7 +690,9 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans);
 template <typename T>
 cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
   MGLevel& L = mg.lv[l];
-  if (mg.mc) {
+  if (L.use_diag) {
+    // the level operator couples no two rows (block Jacobi): the diagonal
+    // apply with per-row weights G_mu[alpha][alpha] (Psi_mu(xi_s) for samples)
     McParams q;
     std::memset(&q, 0, sizeof(q));
     q.n_prob = 1;
@@ -700,12 +702,12 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
     P.b = L.d_b;
     P.ctab = static_cast<const double*>(L.d_ctab);
     P.wgt = mg.d_wgt;
-    P.amq = L.d_amq;
+    P.amq = trans ? L.d_amqT : L.d_amq;
     P.n_x = L.hp.n_x;
     P.unit0 = 0;
     P.n_cells = (int)L.hp.n_cells;
     P.S = L.hp.n_xi;
-    P.ts = mg.mc_ts;
+    P.ts = L.mc_ts;
     P.tiles = (P.S + P.ts - 1) / P.ts;
     for (int d = 0; d < 3; ++d) {
       P.nn[d] = L.hp.nn[d];
@@ -720,7 +722,6 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
     q.mass_only = 0;
     q.units = (long long)P.tiles * P.n_cells;
     for (int i = 0; i < L.hp.n_t; ++i) q.tb[i] = L.hp.tau * L.hp.B_hat[i * L.hp.n_t + i];
-    (void)trans;
     return launch_mc_apply(mg.precision, L.hp.dim, L.hp.k, L.hp.n_t, q, L.mc_grid, L.mc_threads, L.mc_smem, s);
   }
   ApplyParams p;
@@ -743,6 +744,20 @@ __global__ void mg_first_residual(const T* __restrict__ b, T* __restrict__ r, lo
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
     r[idx] = bd ? T(0) : b[idx];
   }
+}
+
+// Tile (rows) and chunk (cells) of a level's diagonal apply: the largest
+// chunk <= max_chunk within 100 KB of shared memory; the grid covers the units.
+sg_status level_diag_shape(MGLevel& L, int ts, int max_chunk, int vb) {
+  L.mc_ts = std::max(1, std::min(ts, L.hp.n_xi));
+  L.mc_chunk = 0;
+  for (int c = 1; c <= max_chunk; ++c)
+    if (mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, L.mc_ts, L.hp.n_terms, c, vb) <= 100 * 1024) L.mc_chunk = c;
+  if (L.mc_chunk == 0) return SG_ERR_UNSUPPORTED;
+  L.mc_smem = mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, L.mc_ts, L.hp.n_terms, L.mc_chunk, vb);
+  const long long units = (long long)((L.hp.n_xi + L.mc_ts - 1) / L.mc_ts) * L.hp.n_cells;
+  L.mc_grid = (int)std::max<long long>(1, std::min<long long>(units / std::max(1, L.mc_chunk), 152LL * 4));
+  return SG_OK;
 }
 
 // Cells per Vanka chunk: up to 8, within the shared-memory budget.
@@ -920,51 +935,88 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
 
 }  // namespace
 
-// Picks the launch shape (cells per chunk x threads) of every smoothed level's
-// residual apply by timing it on the level's own buffers (levels of at least
-// 256 cells; smaller ones keep the default).
+// Picks, for every smoothed level of at least 256 cells, the faster residual
+// apply on the level's own buffers: the diagonal apply over (rows per tile x
+// cells per chunk) or, where it applies, the SG cell kernel over (cells per
+// chunk x threads).  Smaller levels keep the SG cell kernel where it applies.
 static cudaError_t tune_level_applies(MG& mg) {
   const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
-  for (MGLevel& L : mg.lv) {
-    if (L.coarsest || L.hp.n_cells < 256 || e != cudaSuccess) continue;
+  for (size_t l = 0; l < mg.lv.size() && e == cudaSuccess; ++l) {
+    MGLevel& L = mg.lv[l];
+    if (L.coarsest || L.hp.n_cells < 256) continue;
     const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
     if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(L.d_b, 0, n * vb, mg.stream)) != cudaSuccess) break;
-    const int max1 = max_apply_chunk(L.hp, (size_t)optin - 1024);
-    std::vector<int> chunks;
-    for (int c = max1; c >= 1; c = c > 1 ? (c + 1) / 2 - (c == 2) : 0) chunks.push_back(c);
-    LaunchShape best = L.ls;
+    std::vector<int> tss;
+    for (int t : {8, 16, 32, 64, L.hp.n_xi})
+      if (t <= L.hp.n_xi && std::find(tss.begin(), tss.end(), t) == tss.end()) tss.push_back(t);
+    int best_ts = L.mc_ts, best_c = 8;
     float best_ms = 1e30f;
-    for (int c : chunks) {
-      for (int t : {128, 256, 384, 512}) {
+    bool best_diag = true;
+    LaunchShape best_ls = L.ls;
+    L.use_diag = true;
+    for (int ts : tss) {
+      for (int cmax : {8, 4, 2}) {
         if (e != cudaSuccess) break;
-        LaunchShape ls;
-        std::string msg;
-        if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
-        ApplyParams p;
-        fill_apply_params(L.hp, ls, L.d_ctab, L.d_grow, L.d_gcol, L.d_gterm, L.d_gval, L.d_perm, L.d_x, L.d_r, 0, p);
-        p.b = L.d_b;
-        p.mode = kApplyResidual;
-        e = launch_apply(L.hp, ls, p, mg.stream);
+        if (level_diag_shape(L, ts, cmax, (int)vb) != SG_OK) continue;
+        if (L.mc_chunk != cmax && cmax != 8) continue;           // the same shape as a larger cap
+        e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
+                                     : residual<double>(mg, (int)l, mg.stream, 0);
         if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_apply(L.hp, ls, p, mg.stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+          e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
+                                       : residual<double>(mg, (int)l, mg.stream, 0);
         if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
         if (e == cudaSuccess && ms < best_ms) {
           best_ms = ms;
-          best = ls;
+          best_ts = ts;
+          best_c = L.mc_chunk;
         }
       }
     }
-    L.ls = best;
+    level_diag_shape(L, best_ts, best_c, (int)vb);
+    if (L.chunk_ok) {
+      // the SG cell kernel over (cells per chunk x threads)
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const int max1 = max_apply_chunk(L.hp, (size_t)optin - 1024);
+      std::vector<int> chunks;
+      for (int c = max1; c >= 1; c = c > 1 ? (c + 1) / 2 - (c == 2) : 0) chunks.push_back(c);
+      L.use_diag = false;
+      const LaunchShape keep = L.ls;
+      for (int c : chunks)
+        for (int t : {128, 256, 384, 512}) {
+          if (e != cudaSuccess) break;
+          LaunchShape ls;
+          std::string msg;
+          if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
+          L.ls = ls;
+          e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
+                                       : residual<double>(mg, (int)l, mg.stream, 0);
+          if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
+          for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+            e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
+                                         : residual<double>(mg, (int)l, mg.stream, 0);
+          if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(b);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+          if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best_diag = false;
+            best_ls = ls;
+          }
+        }
+      L.ls = best_diag ? keep : best_ls;
+    }
+    L.use_diag = best_diag;
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
@@ -1030,7 +1082,7 @@ void mg_free(MG& mg) {
   mg.d_blk_cls = mg.d_blk_alpha = nullptr;
   for (MGLevel& L : mg.lv) {
     cudaFree(L.d_ctab); cudaFree(L.d_grow); cudaFree(L.d_gcol); cudaFree(L.d_gterm); cudaFree(L.d_gval);
-    cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner); cudaFree(L.d_amq);
+    cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner); cudaFree(L.d_amq); cudaFree(L.d_amqT);
     cudaFree(L.d_x); cudaFree(L.d_b); cudaFree(L.d_r);
     for (int d = 0; d < 3; ++d) {
       cudaFree(L.d_pc[d]); cudaFree(L.d_pw[d]); cudaFree(L.d_rptr[d]); cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
@@ -1131,24 +1183,25 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     for (int a = 0; a < L.hp.n_xi; ++a) L.hp.perm[a] = a;
     L.hp.precision = precision;
     L.coarsest = l + 1 == mg.lv.size();
-    if (mg.mc) {
-      // Monte-Carlo rows: the level residual is the Monte-Carlo apply
-      std::vector<double> amq;
+    {
+      // the level residual is the diagonal apply: time-mass tables of A_t and A_t^T
+      std::vector<double> amq, amqT, At((size_t)L.hp.n_t * L.hp.n_t);
+      for (int i = 0; i < L.hp.n_t; ++i)
+        for (int j = 0; j < L.hp.n_t; ++j) At[(size_t)i * L.hp.n_t + j] = L.hp.A_hat[(size_t)j * L.hp.n_t + i];
       mc_amq(L.hp, L.hp.A_hat, amq);
+      mc_amq(L.hp, At, amqT);
       if ((e = upload_vec(&L.d_amq, amq)) != cudaSuccess) break;
+      if ((e = upload_vec(&L.d_amqT, amqT)) != cudaSuccess) break;
       if ((e = prepare_mc_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t)) != cudaSuccess) break;
-      const int vbm = precision == kPrecF32 ? 4 : 8;
-      L.mc_chunk = 0;
-      for (int c = 1; c <= 8; ++c)
-        if (mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, mg.mc_ts, L.hp.n_terms, c, vbm) <= 100 * 1024) L.mc_chunk = c;
-      if (L.mc_chunk == 0) { msg = "Monte-Carlo tile does not fit in shared memory"; return SG_ERR_UNSUPPORTED; }
-      L.mc_smem = mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, mg.mc_ts, L.hp.n_terms, L.mc_chunk, vbm);
-      const long long units = (long long)((L.hp.n_xi + mg.mc_ts - 1) / mg.mc_ts) * L.hp.n_cells;
-      L.mc_grid = (int)std::max<long long>(1, std::min<long long>(units / std::max(1, L.mc_chunk), 152LL * 4));
-    } else {
-      sg_status st = plan_apply(L.hp, L.ls, msg);
-      if (st != SG_OK) return st;
-      if ((e = prepare_apply_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t, L.ls.smem)) != cudaSuccess) break;
+      if (level_diag_shape(L, mg.mc ? mg.mc_ts : std::min(L.hp.n_xi, 32), 8, precision == kPrecF32 ? 4 : 8) != SG_OK) {
+        msg = "multigrid level tile does not fit in shared memory";
+        return SG_ERR_UNSUPPORTED;
+      }
+      // the SG cell kernel with the diagonal coupling table, where it applies
+      std::string m2;
+      L.chunk_ok = !mg.mc && plan_apply(L.hp, L.ls, m2) == SG_OK;
+      if (L.chunk_ok && (e = prepare_apply_kernel(precision, L.hp.dim, L.hp.k, L.hp.n_t, L.ls.smem)) != cudaSuccess) break;
+      L.use_diag = !L.chunk_ok;
     }
     const int n = L.hp.k + 1;
     const int nkd = L.hp.dim == 2 ? n * n : n * n * n;
@@ -1235,11 +1288,18 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
       if (e != cudaSuccess) break;
     }
   }
+  if (e == cudaSuccess && !mg.d_wgt) {
+    // per-row weights of the diagonal level apply: G_mu[alpha][alpha]
+    std::vector<double> wgt((size_t)fine.n_xi * fine.n_terms);
+    for (int a = 0; a < fine.n_xi; ++a)
+      for (int t = 0; t < fine.n_terms; ++t) wgt[(size_t)a * fine.n_terms + t] = drow[a][t];
+    e = upload_vec(&mg.d_wgt, wgt);
+  }
   if (e == cudaSuccess) e = upload_vec(&mg.d_cls, mg.cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_cls, blk_cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_alpha, blk_alpha);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess && !mg.mc) e = tune_level_applies(mg);
+  if (e == cudaSuccess) e = tune_level_applies(mg);
   if (e == cudaSuccess) e = tune_vanka(mg);
   if (e != cudaSuccess) {
     msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);

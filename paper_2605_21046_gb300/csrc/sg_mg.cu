@@ -3,8 +3,10 @@
 // preconditioned by one V-cycle of its diagonal block
 //     A_alpha = A_t (x) M_x + sum_mu [G_mu]_{alpha alpha} B_t (x) K_mu,
 // with a space-time Vanka patch smoother.  All N_xi * N_t vectors go through
-// the V-cycle together: the level operator is the apply kernel with the
-// diagonal coupling table, so one launch smooths every mode.
+// the V-cycle together, so one launch smooths every mode.  A level residual is
+// either the SG cell kernel with the diagonal coupling table or the diagonal
+// (Monte-Carlo) apply with per-row weights [G_mu]_{alpha alpha}; set-up times
+// both on the level and keeps the faster.
 //
 // Levels halve the cells per direction while every count is even and > 2;
 // coefficients are re-evaluated on every level (a per-cell scale is averaged

@@ -79,6 +79,24 @@ def test_gradient_matches_oracle(cuda, cells, k, r, slabs, every):
     assert np.abs(c - c0).max() <= GRAD_TOL * np.abs(c0).max()
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_gradient_3d_matches_oracle(cuda, k):
+    """The gradient kernel's 3D shapes: 4x4x4 Q1 / 3x3x3 Q2, dG(1), 2 slabs,
+    a mean field with a per-cell scale and two sine pieces."""
+    cells = (4, 4, 4) if k == 1 else (3, 3, 3)
+    coef = I.linear_sine_coef(2, 3, 0.08, [(1, 1, 1), (2, 1, 1)], a0_cells=np.ones(int(np.prod(cells))))
+    spec = dict(dim=3, cells=cells, lo=(0.0,) * 3, hi=(1.0,) * 3, k=k, r=1, n_slabs=2, T=0.4, M=2, P=1, coef=coef)
+    exact = {"q": 1, "c": [1.0, 0.3, 0.2], "phi": [[("sin", 1)] * 3] * 3, "T": [0.0, 1.0, 1.0]}
+    J0, g0, c0 = adjoint.gradient(spec, exact, cell_piece=0)
+    ctx = _ctx(spec, exact)
+    J, g, c, st = sg.sg_adjoint_gradient(ctx, rtol=1e-12, checkpoint_every=1, cell_piece=0)
+    ctx.destroy()
+    assert st["adjoint_solves"] == 2
+    assert abs(J - J0) <= GRAD_TOL * J0
+    assert np.abs(g - g0).max() <= GRAD_TOL * np.abs(g0).max()
+    assert np.abs(c - c0).max() <= GRAD_TOL * np.abs(c0).max()
+
+
 def test_checkpoint_spacing_does_not_change_the_result(cuda):
     spec = I.config_adjoint_2d(cells=(8, 8), k=2, r=1, n_slabs=7)
     exact = sine_exact(2, 2, 2)

@@ -132,3 +132,21 @@ def test_march_matches_manufactured_march():
     b = man.march(2)
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-10 * np.abs(y).max()
+
+
+def test_gradient_3d_matches_central_differences():
+    """The same pin on a 3D 3x3x3 Q1 mesh: every amplitude and two cells."""
+    cells = (3, 3, 3)
+    coef = I.linear_sine_coef(2, 3, 0.08, [(1, 1, 1), (2, 1, 1)],
+                              a0_cells=np.random.default_rng(4).uniform(0.8, 1.2, 27))
+    spec = dict(dim=3, cells=cells, lo=(0.0,) * 3, hi=(1.0,) * 3, k=1, r=1, n_slabs=2, T=0.4, M=2, P=1, coef=coef)
+    exact = {"q": 1, "c": [1.0, 0.3, 0.2], "phi": [[("sin", 1)] * 3] * 3, "T": [0.0, 1.0, 1.0]}
+    J, g_amp, g_cell = adjoint.gradient(spec, exact, cell_piece=0)
+    scale = np.abs(g_amp).max()
+    for j in range(len(spec["coef"])):
+        fd = _fd(spec, exact, amp=j)
+        assert abs(g_amp[j] - fd) <= FD_TOL * scale, (j, g_amp[j], fd)
+    cscale = np.abs(g_cell).max()
+    for c in (0, 13):
+        fd = _fd(spec, exact, cell_piece=0, cells=coef[0]["cell_scale"], c_idx=c)
+        assert abs(g_cell[c] - fd) <= FD_TOL * cscale, (c, g_cell[c], fd)

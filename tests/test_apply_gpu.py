@@ -131,6 +131,20 @@ def test_multi_index_order_matches_oracle(cuda):
         ctx.destroy()
 
 
+@pytest.mark.parametrize("name", ["config-2d-q2-64x64", "ragged-2d-q2-13x7", "3d-q2-4x3x5", "one-row-2d-q1-5x1"])
+def test_host_entry_point_shapes_match(cuda, name):
+    """sg_apply_host (host buffers in and out) equals the device apply on
+    ragged, 3D and one-row meshes, for both transposes."""
+    spec = FULL_CASES.get(name) or small(2, (5, 1), 1, 1, 2, 2)
+    ctx = sg.sg_setup_spec(spec)
+    x = I.random_vector(spec, seed=5)
+    for tr in (False, True):
+        y_dev = gpu_apply(cuda, spec, x, ctx=ctx, transpose=tr)
+        y_host = sg.sg_apply_host(ctx, 0, x, transpose=tr)
+        assert _rel(y_host, y_dev) < 1e-15, (name, tr)
+    ctx.destroy()
+
+
 def test_host_entry_point_matches(cuda):
     spec = I.config_2d_q2_64()
     ctx = sg.sg_setup_spec(spec)

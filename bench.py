@@ -346,6 +346,12 @@ def run_ours(args, world, rank, local):
                          "threads": ctx_dw.info["threads"]}}
         ctx_dw.destroy()
 
+    # the same applies on one x/y pair (x, y and the tables stay in L2)
+    e_hot, t_hot, _ = time_applies(sg, torch, ctx, X[:1], Y[:1], args.steps, args.warmup, stream, world, False, local)
+    hot = {"value": world * n * args.steps / (e_hot / 1e3) / 1e9, "unit": UNIT,
+           "ms_per_step": e_hot / args.steps, "l2": "one x/y pair, L2-resident",
+           "fp64_tflops": FLOP_PER_UNKNOWN * n / t_hot / 1e12}
+
     solve = None if args.no_solve else measure_solve(sg, torch, spec, dev, autotune=not args.no_autotune)
 
     # end to end through the host-buffer entry point: pinned x in, y out
@@ -399,7 +405,7 @@ def run_ours(args, world, rank, local):
                          "hbm": {"achieved": hbm_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                                  "frac": hbm_gbs / pk.get("hbm_gbs", 6800.0)}},
             "cpu_baseline": cpu,
-            "variants": {"dw": dw},
+            "variants": {"dw": dw, "l2_hot": hot},
             "solve": solve,
         }
         print(json.dumps(line), flush=True)
@@ -590,11 +596,71 @@ def next_adjoint(sg, torch, inputs, fd_rel_step=1e-6):
             "fd_relative_step": fd_rel_step, "fd_checks": fd}
 
 
+# algorithmic FP64 flop per unknown of the sum-factorised apply (operation count of
+# the forward/backward sum factorisation plus the point kernel) per workload
+FLOP_PER_UNKNOWN_BY_WORKLOAD = {"2d-q2-64x64-M4P3": 166.0, "3d-q2-32x32x32-M3P3": 345.0,
+                                "2d-q2-128x128-M4P4": 172.0}
+
+
+def next_applies(sg, torch, inputs, steps=100, warmup=10):
+    """The apply on the two large workloads (32^3 Q2 M=3 P=3, 10.99 M unknowns;
+    128x128 Q2 M=4 P=4, 9.25 M unknowns): FP64 forward, FP64 transpose (the
+    adjoint apply) and double-word forward, autotuned launch shape, over
+    rotating x/y pairs larger than L2, per-launch CUDA events."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for maker in (inputs.config_3d_q2_32, inputs.config_2d_q2_128):
+        spec = maker()
+        row = {}
+        X = Y = None
+        for vname, prec, transpose in (("fp64", sg.SG_PREC_FP64, False), ("fp64_transpose", sg.SG_PREC_FP64, True),
+                                       ("dw", sg.SG_PREC_DW, False)):
+            ctx = sg.sg_setup_spec(spec, prec)
+            sg.sg_autotune(ctx, reps=5)
+            n = ctx.info["n_unknowns"]
+            if X is None:
+                R = max(2, math.ceil(2.2 * L2_BYTES / (16 * n)))
+                gen = torch.Generator(device=dev)
+                gen.manual_seed(inputs.SEED_X)
+                X = [torch.rand(n, dtype=torch.float64, device=dev, generator=gen) * 2 - 1 for _ in range(R)]
+                Y = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(R)]
+            for s_ in range(warmup):
+                sg.sg_apply(ctx, 0, X[s_ % R], Y[s_ % R], transpose, stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with ClockSampler(torch.cuda.current_device()) as clk:
+                torch.cuda.synchronize()
+                for s_ in range(steps):
+                    ev[s_][0].record(stream)
+                    sg.sg_apply(ctx, 0, X[s_ % R], Y[s_ % R], transpose, stream)
+                    ev[s_][1].record(stream)
+                torch.cuda.synchronize()
+            t = statistics.mean(a.elapsed_time(b) for a, b in ev) / 1e3
+            tf = FLOP_PER_UNKNOWN_BY_WORKLOAD[spec["name"]] * n / t / 1e12
+            row[vname] = {"value": n / t / 1e9, "unit": UNIT, "ms_per_apply": 1e3 * t,
+                          "fp64_equivalent_tflops": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
+                          "hbm_gbs": BYTES_PER_UNKNOWN * n / t / 1e9,
+                          "launch": {"chunk_cells": ctx.info["chunk"], "grid": ctx.info["grid"],
+                                     "threads": ctx.info["threads"]},
+                          "clocks": clk.summary()}
+            ctx.destroy()
+        row["unknowns"] = n
+        row["l2"] = f"{R} rotating x/y pairs, {16 * R * n / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2"
+        out[spec["name"]] = row
+        del X, Y
+        torch.cuda.empty_cache()
+    return {"row": "applies", "metric": METRIC, "unit": UNIT,
+            "flop_per_unknown": FLOP_PER_UNKNOWN_BY_WORKLOAD, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+            "workloads": out}
+
+
 def next_vcycle(sg, torch, inputs, profile_range=False):
     """One V-cycle of the block-Jacobi multigrid (all modes at once) on the
     64x64 Q2 P=3 and 32^3 Q2 P=3 workloads, per precision: device ms per
-    V-cycle (10 graph launches after 3 warm-up ones).  With profile_range the
-    last FP32 3D V-cycle is bracketed by cudaProfilerStart/Stop."""
+    V-cycle (10 graph launches after 3 warm-up ones).  With profile_range one
+    more FP32 3D V-cycle with the solver's sweeps and damping is bracketed by
+    cudaProfilerStart/Stop."""
     out = {}
     for wname, maker in (("2d-q2-64x64-M4P3", inputs.config_2d_q2_64), ("3d-q2-32x32x32-M3P3", inputs.config_3d_q2_32)):
         spec = maker()
@@ -617,7 +683,7 @@ def next_vcycle(sg, torch, inputs, profile_range=False):
                 torch.cuda.synchronize()
                 row[f"{pname}_nu{nu}"] = a.elapsed_time(b) / 10
         if profile_range and wname.startswith("3d"):
-            sg.sg_mg_setup(ctx, sg.SG_PREC_FP32, 2, 0.7)
+            sg.sg_mg_setup(ctx, sg.SG_PREC_FP32, MG_NU, MG_OMEGA)
             sg.sg_vcycle(ctx, r, z)
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
@@ -649,6 +715,8 @@ def run_next(args, world, rank, local):
                 out = next_adjoint(sg, torch, inputs)
             elif row == "vcycle":
                 out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range)
+            elif row == "applies":
+                out = next_applies(sg, torch, inputs)
             else:
                 raise ValueError(row)
         except sg.SGError as ex:
@@ -675,7 +743,8 @@ def main():
                     help="bracket the timed FP64 applies with cudaProfilerStart/Stop")
     ap.add_argument("--suite", choices=["apply", "next"], default="apply",
                     help="apply: the headline line; next: one line per solver-side row")
-    ap.add_argument("--rows", default="mixed,mc,adjoint", help="rows of --suite next")
+    ap.add_argument("--rows", default="mixed,mc,adjoint", help="rows of --suite next "
+                    "(mixed, mc, adjoint, vcycle, applies)")
     ap.add_argument("--mc-samples", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -13,7 +13,11 @@
 // the Gauss-point work couples every chaos mode (through G_mu) and every time
 // node (through A_t):
 //   phase 0  gather the chunk's nodal values of every vector (Dirichlet
-//            nodes read as 0) and the coefficient values of its cells;
+//            nodes read as 0) and the coefficient values of its cells, as
+//            products G value x a_mu(x_q) for each distinct (mu, G value) pair
+//            of the coupling table (13 pairs for M = 4, P = 3: the mean term's
+//            1 and sqrt(1..3) for each xi_m), so the entries below need no
+//            multiply;
 //   phase 1  per (cell, vector): sum-factorised interpolation to the
 //            (k+1)^d Gauss points and collocation gradients (reference
 //            tables are compile-time constants, so their exact zeros and ones
@@ -76,17 +80,43 @@ __global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* y, const IO* b, i
   }
 }
 
-size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk,
-                        int value_bytes) {
+size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int coef_rows, int nnz, int chunk,
+                        int value_bytes, bool premul) {
   const size_t nqd = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
   const size_t V = (size_t)n_xi * n_t;
   size_t vals = (size_t)chunk * V * (1 + dim) * nqd      // Qs
-                + (size_t)chunk * n_terms * nqd          // Cs
+                + (size_t)chunk * coef_rows * nqd        // Cs
                 + nqd * n_t * n_t                        // Amq
-                + n_t + 3;                               // Tb, Rt
-  size_t ints = (n_xi + 1) + n_xi;                       // Gr, Pm
-  // values, then 16-byte packed coupling entries at a 16-byte boundary, then ints
-  return ((vals * value_bytes + 15) / 16) * 16 + 16 * (size_t)nnz + ints * sizeof(int);
+                + n_t + 3                                // Tb, Rt
+                + (premul ? coef_rows : nnz);            // G value per pair / per entry
+  size_t ints = (n_xi + 1) + n_xi + (premul ? coef_rows : 0);   // Gr, Pm, pair terms
+  // values, then 8-byte coupling entries at a 16-byte boundary, then ints
+  return ((vals * value_bytes + 15) / 16) * 16 + 8 * (size_t)nnz + ints * sizeof(int);
+}
+
+int coupling_pairs(const HostProblem& hp, int* term, double* val) {
+  int n = 0;
+  for (size_t e = 0; e < hp.g.col.size(); ++e) {
+    const int t = hp.g.term[e];
+    const double v = hp.g.val[e];
+    int k = 0;
+    while (k < n && !(term[k] == t && val[k] == v)) ++k;
+    if (k < n) continue;
+    if (n == kMaxPairs) return -1;
+    term[n] = t;
+    val[n] = v;
+    ++n;
+  }
+  return n;
+}
+
+// Coefficient rows per cell the kernel stages and whether they are pre-multiplied pairs.
+static int coef_rows(const HostProblem& hp, bool& premul) {
+  int term[kMaxPairs];
+  double val[kMaxPairs];
+  const int n = coupling_pairs(hp, term, val);
+  premul = n >= 0;
+  return premul ? n : hp.n_terms;
 }
 
 template <int K>
@@ -124,9 +154,11 @@ cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t 
 int max_apply_chunk(const HostProblem& hp, size_t budget) {
   const int nnz = (int)hp.g.col.size();
   const int vb = hp.precision == kPrecF32 ? 4 : 8;
+  bool premul = false;
+  const int rows = coef_rows(hp, premul);
   int chunk = 0;
   for (int c = 1; c <= 64; ++c) {
-    if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, c, vb) > budget) break;
+    if (apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, rows, nnz, c, vb, premul) > budget) break;
     chunk = c;
   }
   return chunk;
@@ -191,7 +223,11 @@ sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, Launch
   }
   ls.chunk = chunk;
   ls.threads = threads;
-  ls.smem = apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, hp.n_terms, nnz, chunk, vb);
+  {
+    bool premul = false;
+    const int rows = coef_rows(hp, premul);
+    ls.smem = apply_smem_bytes(hp.dim, hp.k, hp.n_t, hp.n_xi, rows, nnz, chunk, vb, premul);
+  }
   cudaError_t e = prepare_apply_kernel(hp.precision, hp.dim, hp.k, hp.n_t, ls.smem);
   int per_sm = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, ls.threads, ls.smem);
@@ -234,6 +270,11 @@ void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void*
   p.n_xi = hp.n_xi;
   p.n_terms = hp.n_terms;
   p.nnz = (int)hp.g.col.size();
+  {
+    const int n = coupling_pairs(hp, p.pair_term, p.pair_val);
+    p.premul = n >= 0;
+    p.n_pairs = n >= 0 ? n : 0;
+  }
   const int nq = hp.k + 1;
   const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
   double detJ = 1.0;

@@ -199,14 +199,14 @@ __device__ __forceinline__ void backward_cell(typename A::T* q) {
   }
 }
 
-// One coupling entry of a chaos row, packed for a single 16-byte shared load:
-// the offset of column beta's vectors in a cell's value block, the offset of
-// the entry's coefficient term in a cell's coefficient block, and G.
-template <class T>
-struct alignas(16) CoupleEntry {
+// One coupling entry of a chaos row, packed for a single 8-byte shared load:
+// the offset of column beta's vectors in a cell's value block and the offset
+// of the entry's coefficient row in a cell's coefficient block (its (term, G)
+// pair with pre-multiplied rows, else its term; -1 - e for an entry e whose
+// pair is missing from the pair list, which then reads its tables globally).
+struct alignas(8) CoupleEntry {
   int off;
   int tq;
-  T g;
 };
 
 // Phase-2 items held per thread (their results live in registers until the
@@ -238,22 +238,41 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int n_xi = p.n_xi, V = n_xi * NT, C = p.chunk;
 
+  const bool premul = p.premul != 0;
+  const int rows = premul ? p.n_pairs : p.n_terms;              // coefficient rows per cell
   T* Qs = reinterpret_cast<T*>(smem_raw);                       // [C][V][NC][NQD]
-  T* Cs = Qs + (size_t)C * V * SLOT;                            // [C][term][NQD]
-  T* Amq = Cs + (size_t)C * p.n_terms * NQD;                    // [NQD][NT][NT]
+  T* Cs = Qs + (size_t)C * V * SLOT;                            // [C][rows][NQD]
+  T* Amq = Cs + (size_t)C * rows * NQD;                         // [NQD][NT][NT]
   T* Tb = Amq + NQD * NT * NT;                                  // [NT]
   T* Rt = Tb + NT;                                              // [3] (h_0/h_d)^2
+  T* Gv = Rt + 3;                                               // G per pair (premul) or per entry
   // the packed coupling entries follow at a 16-byte boundary
-  CoupleEntry<T>* Ge = reinterpret_cast<CoupleEntry<T>*>(
-      (reinterpret_cast<uintptr_t>(Rt + 3) + 15) & ~static_cast<uintptr_t>(15));   // [nnz]
+  CoupleEntry* Ge = reinterpret_cast<CoupleEntry*>(
+      (reinterpret_cast<uintptr_t>(Gv + (premul ? p.n_pairs : p.nnz)) + 15) & ~static_cast<uintptr_t>(15));
   int* Gr = reinterpret_cast<int*>(Ge + p.nnz);                 // [n_xi+1]
   int* Pm = Gr + n_xi + 1;                                      // [n_xi]
+  int* Pt = Pm + n_xi;                                          // [n_pairs] term of each pair
 
+  if (premul) {
+    for (int k = tid; k < p.n_pairs; k += nthr) {
+      Gv[k] = A::in(p.pair_val[k]);
+      Pt[k] = p.pair_term[k];
+    }
+  } else {
+    for (int e = tid; e < p.nnz; e += nthr) Gv[e] = A::in(p.g_val[e]);
+  }
   for (int e = tid; e < p.nnz; e += nthr) {
-    CoupleEntry<T> ce;
+    CoupleEntry ce;
     ce.off = p.g_col[e] * NT * SLOT;
-    ce.tq = p.g_term[e] * NQD;
-    ce.g = A::in(p.g_val[e]);
+    const int t = p.g_term[e];
+    if (premul) {
+      const double v = p.g_val[e];
+      int k = 0;
+      while (k < p.n_pairs && !(p.pair_term[k] == t && p.pair_val[k] == v)) ++k;
+      ce.tq = k < p.n_pairs ? k * NQD : -1 - e;
+    } else {
+      ce.tq = t * NQD;
+    }
     Ge[e] = ce;
   }
   for (int e = tid; e <= n_xi; e += nthr) Gr[e] = p.g_row[e];
@@ -272,7 +291,18 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
     // ---------------------------------------------------------- phase 0
     {
       const int per_cell = p.n_terms * NQD;
-      for (int idx = tid; idx < nc * per_cell; idx += nthr) Cs[idx] = A::in(p.ctab[c0 * per_cell + idx]);
+      if (premul) {
+        // G value x a_term(x_q) per (cell, pair, point), rounded exactly as the
+        // product at the Gauss point would be
+        const int per_row = rows * NQD;
+        for (int idx = tid; idx < nc * per_row; idx += nthr) {
+          const int c = idx / per_row, r = idx - c * per_row;
+          const int k = r / NQD, q = r - k * NQD;
+          Cs[idx] = A::fin(A::mul(Gv[k], A::in(p.ctab[(c0 + c) * per_cell + Pt[k] * NQD + q])));
+        }
+      } else {
+        for (int idx = tid; idx < nc * per_cell; idx += nthr) Cs[idx] = A::in(p.ctab[c0 * per_cell + idx]);
+      }
     }
     for (int idx = tid; idx < nc * V * NKD; idx += nthr) {
       const int a = idx % NKD;
@@ -341,16 +371,31 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
 #pragma unroll
               for (int d = 0; d < DIM; ++d) out[kk][i][1 + d] = A::zero();
             }
-            const T* cq = Cs + (size_t)c * p.n_terms * NQD + q;
-            const int e_end = Gr[a + 1];
-            for (int e = Gr[a]; e < e_end; ++e) {
-              const CoupleEntry<T> ce = Ge[e];
-              const T w = A::fin(A::mul(ce.g, cq[ce.tq]));
-              const T* gb = base + ce.off;
+            const T* cq = Cs + (size_t)c * rows * NQD + q;
+            const int e_beg = Gr[a], e_end = Gr[a + 1];
+            auto couple = [&](const T w, const int off) {
+              const T* gb = base + off;
 #pragma unroll
               for (int i = 0; i < NT; ++i)
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) A::fma(w, gb[(size_t)i * SLOT + (1 + d) * NQD], out[kk][i][1 + d]);
+            };
+            if (premul) {
+              for (int e = e_beg; e < e_end; ++e) {
+                const CoupleEntry ce = Ge[e];
+                if (ce.tq >= 0) {
+                  couple(cq[ce.tq], ce.off);
+                } else {
+                  const int ee = -1 - ce.tq;
+                  const double a_q = p.ctab[(c0 + c) * p.n_terms * NQD + p.g_term[ee] * NQD + q];
+                  couple(A::fin(A::mul(A::in(p.g_val[ee]), A::in(a_q))), ce.off);
+                }
+              }
+            } else {
+              for (int e = e_beg; e < e_end; ++e) {
+                const CoupleEntry ce = Ge[e];
+                couple(A::fin(A::mul(Gv[e], cq[ce.tq])), ce.off);
+              }
             }
 #pragma unroll
             for (int i = 0; i < NT; ++i)

@@ -17,6 +17,7 @@ constexpr int kMaxNQ = kMaxK + 1; // Gauss points per direction
 constexpr int kMaxNT = 4;         // largest number of time nodes (dG(3))
 constexpr int kMaxQD = 64;        // largest tensor Gauss rule per cell (4^3)
 constexpr int kMaxAmq = 256;      // largest (points x time nodes^2) coupling table
+constexpr int kMaxPairs = 32;     // largest number of distinct (term, G value) pairs pre-multiplied
 
 // ---------------------------------------------------------------- host maths
 // One-dimensional rules and bases on the reference interval [0, 1].
@@ -110,6 +111,14 @@ struct ApplyParams {
   const void* b;          // right-hand side of the residual / accumulate modes
   int mode;               // kApplyPlain: y = A x; kApplyResidual: y = b - A x;
                           // kApplyAccumulate: y = b + A x without the Dirichlet identity rows
+  // Distinct (term, G value) pairs of the coupling table.  With premul set the
+  // kernel stages G value x a_term(x_q) per pair and cell once per chunk, so a
+  // coupling entry costs no multiply at the Gauss points; without it (more
+  // than kMaxPairs pairs) every entry multiplies G by a_term(x_q).
+  int premul;
+  int n_pairs;
+  int pair_term[kMaxPairs];
+  double pair_val[kMaxPairs];
 };
 constexpr int kApplyPlain = 0, kApplyResidual = 1, kApplyAccumulate = 2;
 
@@ -127,9 +136,13 @@ sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, Launch
 // Largest chunk whose shared memory fits the budget.
 int max_apply_chunk(const HostProblem& hp, size_t budget);
 // Size of the dynamic shared memory the apply kernel needs for a chunk of cells
-// (value_bytes = 8 for FP64 / DW, 4 for FP32).
-size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int n_terms, int nnz, int chunk,
-                        int value_bytes = 8);
+// (value_bytes = 8 for FP64 / DW, 4 for FP32; coef_rows = coefficient rows
+// staged per cell: the pairs with premul, else the terms).
+size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int coef_rows, int nnz, int chunk,
+                        int value_bytes, bool premul);
+// Distinct (term, G value) pairs of the coupling table in order of first
+// appearance; returns their number, or -1 if there are more than kMaxPairs.
+int coupling_pairs(const HostProblem& hp, int* term, double* val);
 // Fills the kernel parameter block of an apply (device table pointers given).
 void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void* ctab,
                        const int* grow, const int* gcol, const int* gterm, const double* gval,

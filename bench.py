@@ -41,7 +41,7 @@ L2_BYTES = 135_528_448
 MG_NU, MG_OMEGA = 1, 0.9
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 chunk-kernel launch on
 # this workload (ncu capture summarised in profiles/); None once the kernel changes
-NCU_TRAFFIC_BYTES = 19_922_176 + 0
+NCU_TRAFFIC_BYTES = None
 
 
 def workload():
@@ -343,7 +343,7 @@ def run_ours(args, world, rank, local):
               "fp64_equivalent_tflops": FLOP_PER_UNKNOWN * n / t_dw / 1e12,
               "gpu_launches": 2 * args.steps,
               "launch": {"chunk_cells": ctx_dw.info["chunk"], "grid": ctx_dw.info["grid"],
-                         "threads": ctx_dw.info["threads"]}}
+                         "threads": ctx_dw.info["threads"], "stagger": ctx_dw.info["stagger"]}}
         ctx_dw.destroy()
 
     # the same applies on one x/y pair (x, y and the tables stay in L2)
@@ -395,7 +395,7 @@ def run_ours(args, world, rank, local):
                        "l2": f"{R} rotating x/y pairs, {2 * R * vec_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2",
                        "parallelism": f"replicas x{world}",
                        "chunk_cells": ctx.info["chunk"], "grid": ctx.info["grid"],
-                       "threads": ctx.info["threads"]},
+                       "threads": ctx.info["threads"], "stagger": ctx.info["stagger"]},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": vec_bytes, "d2h_bytes_per_step": vec_bytes},
@@ -642,7 +642,7 @@ def next_applies(sg, torch, inputs, steps=100, warmup=10):
                           "fp64_equivalent_tflops": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
                           "hbm_gbs": BYTES_PER_UNKNOWN * n / t / 1e9,
                           "launch": {"chunk_cells": ctx.info["chunk"], "grid": ctx.info["grid"],
-                                     "threads": ctx.info["threads"]},
+                                     "threads": ctx.info["threads"], "stagger": ctx.info["stagger"]},
                           "clocks": clk.summary()}
             ctx.destroy()
         row["unknowns"] = n

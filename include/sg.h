@@ -133,6 +133,7 @@ typedef struct {
   int grid;        /* persistent CTAs of sg_apply       */
   int threads;     /* threads per CTA of sg_apply       */
   int smem_bytes;  /* dynamic shared memory per CTA     */
+  int stagger;     /* cells in the first chunk of the upper half of the CTAs (0: a full chunk) */
 } sg_info;
 
 /* Statistics of one sg_solve_slab call (host struct out). */
@@ -314,8 +315,10 @@ sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, doub
                                int transpose);
 
 /* sg_autotune - time the apply kernel of this context over candidate launch
- * shapes (cells per shared-memory chunk x threads per CTA) on the current
- * device and keep the fastest for every later sg_apply / sg_solve_slab; each
+ * shapes (cells per shared-memory chunk x threads per CTA x whether the upper
+ * half of the CTAs starts with a half chunk, so that CTAs sharing an SM reach
+ * their memory phases at different times) on the current device and keep the
+ * fastest for every later sg_apply / sg_solve_slab; each
  * candidate runs 2 + reps applies on a synthetic vector.  Allocates and frees
  * two temporary device vectors.  Synchronous.  Results are unchanged up to
  * the order of the atomic additions. */

@@ -35,7 +35,8 @@ class sg_info(C.Structure):
                 ("chaos_order", C.c_int), ("precision", C.c_int), ("n_xi", C.c_int), ("n_t", C.c_int), ("n_terms", C.c_int),
                 ("g_nnz", C.c_int), ("n_slabs", C.c_int), ("n_x", C.c_int64), ("n_cells", C.c_int64),
                 ("n_unknowns", C.c_int64), ("tau", C.c_double), ("chunk", C.c_int),
-                ("grid", C.c_int), ("threads", C.c_int), ("smem_bytes", C.c_int)]
+                ("grid", C.c_int), ("threads", C.c_int), ("smem_bytes", C.c_int),
+                ("stagger", C.c_int)]
 
 
 class sg_solve_stats(C.Structure):

@@ -380,26 +380,28 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
   const int thread_opts[] = {128, 256, 384, 512};
   for (int c : chunks) {
     if (e != cudaSuccess) break;
-    for (int t : thread_opts) {
-      sg::LaunchShape ls;
-      std::string msg;
-      if (sg::plan_apply_shape(ctx->hp, c, t, ls, msg) != SG_OK) continue;
-      ctx->ls = ls;
-      sg::ApplyParams p;
-      fill_params(ctx, x, y, 0, p);
-      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = sg::launch_apply(ctx->hp, ls, p, s);
-      if (e == cudaSuccess) e = cudaEventRecord(a, s);
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = sg::launch_apply(ctx->hp, ls, p, s);
-      if (e == cudaSuccess) e = cudaEventRecord(b, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(b);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      if (e != cudaSuccess) break;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = ls;
+    for (int t : thread_opts)
+      for (int staggered = 0; staggered < (c > 1 ? 2 : 1); ++staggered) {
+        sg::LaunchShape ls;
+        std::string msg;
+        if (sg::plan_apply_shape(ctx->hp, c, t, ls, msg) != SG_OK) continue;
+        ls.stagger = staggered ? (c + 1) / 2 : 0;
+        ctx->ls = ls;
+        sg::ApplyParams p;
+        fill_params(ctx, x, y, 0, p);
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = sg::launch_apply(ctx->hp, ls, p, s);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = sg::launch_apply(ctx->hp, ls, p, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = ls;
+        }
       }
-    }
   }
   ctx->ls = e == cudaSuccess ? best : orig;
   if (a) cudaEventDestroy(a);
@@ -551,6 +553,7 @@ sg_status sg_get_info(const sg_ctx* ctx, sg_info* out) {
   out->grid = ctx->ls.grid;
   out->threads = ctx->ls.threads;
   out->smem_bytes = (int)ctx->ls.smem;
+  out->stagger = ctx->ls.stagger;
   return SG_OK;
 }
 

@@ -223,6 +223,7 @@ sg_status plan_apply_shape(const HostProblem& hp, int chunk, int threads, Launch
   }
   ls.chunk = chunk;
   ls.threads = threads;
+  ls.stagger = 0;
   {
     bool premul = false;
     const int rows = coef_rows(hp, premul);
@@ -275,6 +276,7 @@ void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void*
     p.premul = n >= 0;
     p.n_pairs = n >= 0 ? n : 0;
   }
+  p.stagger = ls.stagger;
   const int nq = hp.k + 1;
   const int nqd = hp.dim == 2 ? nq * nq : nq * nq * nq;
   double detJ = 1.0;

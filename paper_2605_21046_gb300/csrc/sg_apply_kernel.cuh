@@ -285,8 +285,12 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
   const long long c_end = (long long)(blockIdx.x + 1) * p.n_cells / gridDim.x;
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
 
-  for (long long c0 = c_begin; c0 < c_end; c0 += C) {
-    const int nc = (int)min((long long)C, c_end - c0);
+  // the upper half of the CTAs may start with a shorter chunk, so that CTAs
+  // sharing an SM do not reach their gather and scatter phases together
+  const int first = (p.stagger > 0 && blockIdx.x >= gridDim.x / 2) ? min(C, p.stagger) : C;
+  int nc = 0;
+  for (long long c0 = c_begin; c0 < c_end; c0 += nc) {
+    nc = (int)min((long long)(c0 == c_begin ? first : C), c_end - c0);
     __syncthreads();   // previous chunk done with Qs / Cs; tables visible
     // ---------------------------------------------------------- phase 0
     {

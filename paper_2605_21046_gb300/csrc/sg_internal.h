@@ -116,6 +116,7 @@ struct ApplyParams {
   // coupling entry costs no multiply at the Gauss points; without it (more
   // than kMaxPairs pairs) every entry multiplies G by a_term(x_q).
   int premul;
+  int stagger;            // cells in the first chunk of CTAs blockIdx >= grid / 2 (0: a full chunk)
   int n_pairs;
   int pair_term[kMaxPairs];
   double pair_val[kMaxPairs];
@@ -127,6 +128,7 @@ struct LaunchShape {
   int threads;
   size_t smem;
   int grid;               // persistent CTAs
+  int stagger;            // first-chunk cells of the upper half of the CTAs (0: none)
 };
 
 // Chooses a chunk size and thread count for the apply kernel of a problem.

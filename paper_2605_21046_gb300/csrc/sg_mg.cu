@@ -994,28 +994,30 @@ static cudaError_t tune_level_applies(MG& mg) {
       L.use_diag = false;
       const LaunchShape keep = L.ls;
       for (int c : chunks)
-        for (int t : {128, 256, 384, 512}) {
-          if (e != cudaSuccess) break;
-          LaunchShape ls;
-          std::string msg;
-          if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
-          L.ls = ls;
-          e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
-                                       : residual<double>(mg, (int)l, mg.stream, 0);
-          if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
-          for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+        for (int t : {128, 256, 384, 512})
+          for (int staggered = 0; staggered < (c > 1 ? 2 : 1); ++staggered) {
+            if (e != cudaSuccess) break;
+            LaunchShape ls;
+            std::string msg;
+            if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
+            ls.stagger = staggered ? (c + 1) / 2 : 0;
+            L.ls = ls;
             e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
                                          : residual<double>(mg, (int)l, mg.stream, 0);
-          if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
-          if (e == cudaSuccess) e = cudaEventSynchronize(b);
-          float ms = 0.0f;
-          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-          if (e == cudaSuccess && ms < best_ms) {
-            best_ms = ms;
-            best_diag = false;
-            best_ls = ls;
+            if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+              e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
+                                           : residual<double>(mg, (int)l, mg.stream, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && ms < best_ms) {
+              best_ms = ms;
+              best_diag = false;
+              best_ls = ls;
+            }
           }
-        }
       L.ls = best_diag ? keep : best_ls;
     }
     L.use_diag = best_diag;

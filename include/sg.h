@@ -324,6 +324,17 @@ sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, doub
  * the order of the atomic additions. */
 sg_status sg_autotune(sg_ctx* ctx, int reps);
 
+/* sg_set_apply_shape - fix the apply launch shape of this context instead of
+ * the default or tuned one: `chunk` cells per shared-memory chunk, `threads`
+ * per CTA (a multiple of 32 within the kernel's launch bound, with
+ * threads * items_per_thread >= N_xi), and `stagger` cells in the first chunk
+ * of the upper half of the CTAs (0: a full chunk; at most `chunk`).  For
+ * reproducible launch shapes and tests; sg_get_info reports the shape.
+ * Returns SG_ERR_ARG, leaving the shape unchanged, when it does not fit the
+ * kernel or the device.  Results are unchanged up to the order of the atomic
+ * additions. */
+sg_status sg_set_apply_shape(sg_ctx* ctx, int chunk, int threads, int stagger);
+
 /* sg_set_exact - attach a manufactured finite-chaos solution (Sec. 4.3,
  * eqs. finite-exact-separated .. finite-chaos-coefficients)
  *     u(x, t, xi) = T(t) sum_{alpha in Lambda_q} c_alpha Phi_alpha(x) Psi_alpha(xi),

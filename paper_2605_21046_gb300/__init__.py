@@ -19,7 +19,7 @@ from . import _abi
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32, SG_PREC_BF16 = (_abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32,
                                                       _abi.SG_PREC_BF16)
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_apply_shape", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -432,6 +432,15 @@ def mc_solve_meshes(ctxs, xis, tile=64, mg_precision=SG_PREC_FP32, rtol=1e-8, ma
 def sg_autotune(ctx, reps=10):
     """Pick the fastest apply launch shape for this context (sg_autotune)."""
     _check(_abi.load().sg_autotune(ctx.handle, int(reps)), "sg_autotune")
+    ctx.info = sg_get_info(ctx)
+    return ctx.info
+
+
+def sg_set_apply_shape(ctx, chunk, threads, stagger=0):
+    """Fix the apply launch shape (sg_set_apply_shape): cells per chunk,
+    threads per CTA, first-chunk cells of the upper half of the CTAs."""
+    _check(_abi.load().sg_set_apply_shape(ctx.handle, int(chunk), int(threads), int(stagger)),
+           "sg_set_apply_shape")
     ctx.info = sg_get_info(ctx)
     return ctx.info
 

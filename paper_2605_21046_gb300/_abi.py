@@ -16,7 +16,7 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
                    "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch",
                    "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient",
-                   "sg_stat_errors", "mc_solve_meshes"])
+                   "sg_stat_errors", "mc_solve_meshes", "sg_set_apply_shape"])
 
 
 class sg_mesh(C.Structure):
@@ -116,6 +116,8 @@ def load():
     lib.sg_stat_errors.restype = C.c_int
     lib.sg_autotune.argtypes = [vp, C.c_int]
     lib.sg_autotune.restype = C.c_int
+    lib.sg_set_apply_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    lib.sg_set_apply_shape.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     lib.sg_apply_host_static.restype = C.c_int
     lib.sg_destroy.argtypes = [vp]

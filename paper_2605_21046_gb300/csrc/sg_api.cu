@@ -413,6 +413,19 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
   return SG_OK;
 }
 
+sg_status sg_set_apply_shape(sg_ctx* ctx, int chunk, int threads, int stagger) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_set_apply_shape: ctx is NULL");
+  if (chunk < 1 || threads < 1 || stagger < 0 || stagger > chunk)
+    return fail(SG_ERR_ARG, "sg_set_apply_shape: chunk, threads or stagger out of range");
+  sg::LaunchShape ls;
+  std::string msg;
+  const sg_status st = sg::plan_apply_shape(ctx->hp, chunk, threads, ls, msg);
+  if (st != SG_OK) return fail(SG_ERR_ARG, "sg_set_apply_shape: " + msg);
+  ls.stagger = stagger;
+  ctx->ls = ls;
+  return SG_OK;
+}
+
 sg_status sg_set_exact(sg_ctx* ctx, int q, const double* c, const int* freq, int t_degree, const double* t_coef) {
   if (!ctx) return fail(SG_ERR_ARG, "sg_set_exact: ctx is NULL");
   std::string msg;

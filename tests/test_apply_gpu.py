@@ -239,3 +239,45 @@ def test_autotune_keeps_parity(cuda, prec):
     want = operator.SGProblem(spec).apply(x).reshape(-1)
     ctx.destroy()
     assert _rel(got, want) < TOL, (before, info)
+
+
+# (cells per chunk, threads, first-chunk cells of the upper half of the CTAs)
+SHAPES = [(1, 128, 0), (2, 256, 1), (3, 384, 2), (4, 256, 2), (5, 512, 5), (7, 384, 4)]
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+@pytest.mark.parametrize("name", ["ragged-2d-q2-13x7", "3d-q2-4x3x5", "config-2d-q2-64x64"])
+def test_fixed_launch_shapes_keep_parity(cuda, name, prec):
+    """Every fixed launch shape, staggered or not, gives the oracle's apply
+    (both transposes): the chunk walk covers every cell exactly once."""
+    spec = FULL_CASES[name]
+    p = operator.SGProblem(spec)
+    x = I.random_vector(spec, seed=77)
+    want = {tr: p.apply(x, transpose=tr).reshape(-1) for tr in (False, True)}
+    ctx = sg.sg_setup_spec(spec, PRECISIONS[prec])
+    try:
+        for chunk, threads, stagger in SHAPES:
+            try:
+                info = sg.sg_set_apply_shape(ctx, chunk, threads, stagger)
+            except sg.SGError:
+                continue                      # shape does not fit this kernel / problem
+            assert (info["chunk"], info["threads"], info["stagger"]) == (chunk, threads, stagger)
+            for tr in (False, True):
+                got = gpu_apply(cuda, spec, x, transpose=tr, ctx=ctx)
+                assert _rel(got, want[tr]) < TOL, (name, prec, chunk, threads, stagger, tr)
+    finally:
+        ctx.destroy()
+
+
+def test_set_apply_shape_rejects_bad_shapes(cuda):
+    spec = FULL_CASES["ragged-2d-q2-13x7"]
+    ctx = sg.sg_setup_spec(spec)
+    try:
+        before = dict(ctx.info)
+        for chunk, threads, stagger in [(0, 256, 0), (2, 256, 3), (2, 256, -1), (2, 100, 0), (2, 4096, 0),
+                                        (10_000, 256, 0)]:
+            with pytest.raises(sg.SGError):
+                sg.sg_set_apply_shape(ctx, chunk, threads, stagger)
+        assert sg.sg_get_info(ctx) == before
+    finally:
+        ctx.destroy()

@@ -129,6 +129,30 @@ static cudaError_t multidot(const double* w, const double* V, int nvec, long lon
   return cudaGetLastError();
 }
 
+// Page-locked host staging for the scalars each Arnoldi step reads back (one
+// copy per step instead of several pageable ones), one buffer per host thread.
+struct PinnedStage {
+  double* p = nullptr;
+  size_t n = 0;
+  ~PinnedStage() {
+    if (p) cudaFreeHost(p);
+  }
+  double* get(size_t need) {
+    if (n >= need) return p;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&p), need * sizeof(double), cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return nullptr;
+    }
+    n = need;
+    return p;
+  }
+};
+thread_local PinnedStage t_stage;
+
 static cudaError_t norm2(const double* w, long long N, double* part, double* out, cudaStream_t s) {
   cudaError_t e = multidot(w, w, 1, N, part, out, s);
   if (e != cudaSuccess) return e;
@@ -171,7 +195,15 @@ sg_status fgmres_core(long long N, const double* b, double* x, double rtol, int 
       return SG_ERR_CUDA;                                          \
     }                                                              \
   } while (0)
-  double host2[2];
+  // h, h2 and nrm are adjacent in the workspace: one read-back per Arnoldi step
+  const size_t n_stage = 2 * (size_t)(m + 2) + 2;
+  std::vector<double> stage_fallback;
+  double* stage = t_stage.get(n_stage);
+  if (!stage) {
+    stage_fallback.assign(n_stage, 0.0);
+    stage = stage_fallback.data();
+  }
+  double* host2 = stage + 2 * (m + 2);     // mirrors ws.nrm
   CK(norm2(b, N, ws.part, ws.nrm, s));
   CK(cudaMemcpyAsync(host2, ws.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -198,7 +230,9 @@ sg_status fgmres_core(long long N, const double* b, double* x, double rtol, int 
   };
   double beta = 0.0;
   CK(true_residual(beta));
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(m + 2), hcol2(m + 2);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
+  const double* hcol = stage;              // mirrors ws.h
+  const double* hcol2 = stage + (m + 2);   // mirrors ws.h2
   sg_status status = SG_OK;
   while (true) {
     if (!std::isfinite(beta)) { status = SG_ERR_NONFINITE; msg = "non-finite residual"; break; }
@@ -226,9 +260,7 @@ sg_status fgmres_core(long long N, const double* b, double* x, double rtol, int 
       k_multiaxpy<<<grid_n(N), 256, 0, s>>>(ws.w, ws.V, ws.h2, j + 1, N);
       CK(norm2(ws.w, N, ws.part, ws.nrm, s));
       k_scale_by<<<grid_n(N), 256, 0, s>>>(ws.w, ws.V + (long long)(j + 1) * N, ws.nrm, N);
-      CK(cudaMemcpyAsync(hcol.data(), ws.h, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(hcol2.data(), ws.h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(host2, ws.nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(stage, ws.h, (2 * (size_t)(m + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       ++stats.iterations;
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i] + hcol2[i];

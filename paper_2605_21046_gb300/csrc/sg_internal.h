@@ -215,6 +215,7 @@ struct MGLevel {
   void* d_inv = nullptr;     // [class][cell][np][pitch] patch inverses (pitch = np rounded up to 8;
                              //  bf16 when MG::bf16), or coarsest [class][n_int][n_int]
   int vanka_chunk = 0;       // cells per Vanka chunk
+  int vanka_tile = 0;        // modes per Vanka tile on this level (0: the multigrid's tile)
   int* d_inner = nullptr;    // coarsest: dof offset (i * n_x + node) of every interior dof
   void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
   void* d_b = nullptr;

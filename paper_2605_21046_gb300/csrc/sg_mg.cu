@@ -733,18 +733,20 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
   return launch_apply(L.hp, L.ls, p, s);
 }
 
-// r = b on interior dofs, 0 on Dirichlet dofs: the residual of the initial
-// iterate (x = 0 inside, x = b on the boundary), without an apply.
+// The initial iterate (x = b on Dirichlet dofs, 0 inside) and its residual
+// (r = b inside, 0 on Dirichlet dofs) in one pass, without an apply.
 template <typename T>
-__global__ void mg_first_residual(const T* __restrict__ b, T* __restrict__ r, long long n_total, long long n_x,
-                                  int nnx, int nny, int nnz, int dim) {
+__global__ void mg_start(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, long long n_total,
+                         long long n_x, int nnx, int nny, int nnz, int dim) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long m = idx % n_x;
     const int ix = (int)(m % nnx), iy = (int)((m / nnx) % nny), iz = (int)(m / ((long long)nnx * nny));
     bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    r[idx] = bd ? T(0) : b[idx];
+    const T v = b[idx];
+    x[idx] = bd ? v : T(0);
+    r[idx] = bd ? T(0) : v;
   }
 }
 
@@ -787,9 +789,10 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   p.blk_alpha = mg.d_blk_alpha;
   p.n_blk = mg.n_blk;
   p.n_xi = L.hp.n_xi;
+  const int tile = L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile;
   p.chunk = L.vanka_chunk;
-  p.tile_modes = mg.vanka_tile;
-  p.n_tiles = (L.hp.n_xi + mg.vanka_tile - 1) / mg.vanka_tile;
+  p.tile_modes = tile;
+  p.n_tiles = (L.hp.n_xi + tile - 1) / tile;
   p.npp = vanka_row_pitch(L.np);
   p.n_x = L.hp.n_x;
   p.n_cells = L.hp.n_cells;
@@ -798,7 +801,7 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
     p.nn[d] = L.hp.nn[d];
   }
   p.omega = T(mg.omega);
-  const size_t smem = vanka_smem(L, mg.vanka_tile, L.vanka_chunk, sizeof(T));
+  const size_t smem = vanka_smem(L, tile, L.vanka_chunk, sizeof(T));
   const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
   const long long units = (long long)cpr * L.hp.cells[1] * L.hp.cells[2] * p.n_tiles;
   const int grid = (int)std::min<long long>(units, 152LL * 8);
@@ -902,9 +905,9 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
   MGLevel& L = mg.lv[l];
   const int V = L.hp.n_xi * L.hp.n_t;
   const long long n = (long long)V * L.hp.n_x;
-  mg_init_x<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x), n, L.hp.n_x,
-                                                L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
   if (L.coarsest) {
+    mg_init_x<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x), n, L.hp.n_x,
+                                                  L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
     const size_t smem = (size_t)L.n_int * sizeof(T);
     mg_coarse<T><<<L.hp.n_xi, 256, smem, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
                                               static_cast<const T*>(L.d_inv), mg.d_cls,
@@ -913,13 +916,11 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
     return cudaGetLastError();
   }
   cudaError_t e;
+  mg_start<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
+                                               static_cast<T*>(L.d_r), n, L.hp.n_x, L.hp.nn[0], L.hp.nn[1],
+                                               L.hp.nn[2], L.hp.dim);
   for (int it = 0; it < mg.nu; ++it) {
-    if (it == 0) {
-      mg_first_residual<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_r), n,
-                                                            L.hp.n_x, L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
-    } else if ((e = residual<T>(mg, l, s, trans)) != cudaSuccess) {
-      return e;
-    }
+    if (it > 0 && (e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
     if (!vanka<T>(mg, L, s, trans)) return cudaErrorInvalidValue;
   }
   if ((e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
@@ -1027,9 +1028,10 @@ static cudaError_t tune_level_applies(MG& mg) {
   return e;
 }
 
-// Picks the cells per Vanka chunk of every smoothed level by timing one sweep
-// for each candidate (1, 2, 4, 8 cells, within the shared-memory budget) on
-// the level's own buffers; keeps the fastest.
+// Picks the cells per Vanka chunk of every smoothed level, and with a single
+// diagonal class the modes per tile (the whole set, 16 or 8: smaller tiles give
+// the small levels more CTAs), by timing sweeps on the level's own buffers for
+// every candidate within the shared-memory budget; keeps the fastest.
 static cudaError_t tune_vanka(MG& mg) {
   const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -1037,33 +1039,45 @@ static cudaError_t tune_vanka(MG& mg) {
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   for (MGLevel& L : mg.lv) {
     if (L.coarsest || e != cudaSuccess) continue;
-    const int max_c = L.vanka_chunk;
     const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
     if ((e = cudaMemsetAsync(L.d_r, 0, n * vb, mg.stream)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
-    int best = max_c;
+    std::vector<int> tiles = {mg.vanka_tile};
+    if (mg.n_classes == 1)
+      for (int t : {16, 8})
+        if (t < mg.vanka_tile && t % kVankaVB == 0) tiles.push_back(t);
+    int best_c = L.vanka_chunk, best_t = 0;
     float best_ms = 1e30f;
-    std::vector<int> cand;
-    for (int c = 1; c <= max_c; c *= 2) cand.push_back(c);
-    if (cand.back() != max_c) cand.push_back(max_c);
-    for (int c : cand) {
-      if (e != cudaSuccess) break;
-      L.vanka_chunk = c;
-      float ms = 0.0f;
-      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-        if (rep == 1) e = cudaEventRecord(a, mg.stream);
-        const bool ok = vk_launch(mg, L, mg.stream);
-        if (!ok) e = cudaErrorInvalidValue;
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(b);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      if (e == cudaSuccess && ms < best_ms) {
-        best_ms = ms;
-        best = c;
+    for (int tile : tiles) {
+      const int max_c = vanka_chunk(L, tile, vb, tile == mg.vanka_tile ? std::max<size_t>(100 * 1024,
+                                                                                         vanka_smem(L, tile, L.vanka_chunk, vb))
+                                                                       : 100 * 1024);
+      if (max_c == 0) continue;
+      std::vector<int> cand;
+      for (int c = 1; c <= max_c; c *= 2) cand.push_back(c);
+      if (cand.back() != max_c) cand.push_back(max_c);
+      for (int c : cand) {
+        if (e != cudaSuccess) break;
+        L.vanka_chunk = c;
+        L.vanka_tile = tile == mg.vanka_tile ? 0 : tile;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+          if (rep == 1) e = cudaEventRecord(a, mg.stream);
+          const bool ok = vk_launch(mg, L, mg.stream);
+          if (!ok) e = cudaErrorInvalidValue;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best_c = c;
+          best_t = L.vanka_tile;
+        }
       }
     }
-    L.vanka_chunk = best;
+    L.vanka_chunk = best_c;
+    L.vanka_tile = best_t;
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);

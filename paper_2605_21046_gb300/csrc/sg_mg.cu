@@ -938,6 +938,26 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
 
 }  // namespace
 
+// Device time of one launch of a set-up candidate: a single timed launch when
+// it takes more than 2 ms (the large levels, where one launch is steady and
+// repeating it costs seconds), else the mean of three launches after it.
+template <class F>
+static float time_candidate(F&& launch, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, cudaError_t& e) {
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (e != cudaSuccess || ms > 2.0f) return ms;
+  if (e == cudaSuccess) e = cudaEventRecord(a, s);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  return ms / 3.0f;
+}
+
 // Picks, for every smoothed level of at least 256 cells, the faster residual
 // apply on the level's own buffers: the diagonal apply over (rows per tile x
 // cells per chunk) or, where it applies, the SG cell kernel over (cells per
@@ -950,6 +970,10 @@ static cudaError_t tune_level_applies(MG& mg) {
   for (size_t l = 0; l < mg.lv.size() && e == cudaSuccess; ++l) {
     MGLevel& L = mg.lv[l];
     if (L.coarsest || L.hp.n_cells < 256) continue;
+    auto res = [&]() {
+      return mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
+                                      : residual<double>(mg, (int)l, mg.stream, 0);
+    };
     const long long n = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
     if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(L.d_b, 0, n * vb, mg.stream)) != cudaSuccess) break;
@@ -966,16 +990,7 @@ static cudaError_t tune_level_applies(MG& mg) {
         if (e != cudaSuccess) break;
         if (level_diag_shape(L, ts, cmax, (int)vb) != SG_OK) continue;
         if (L.mc_chunk != cmax && cmax != 8) continue;           // the same shape as a larger cap
-        e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
-                                     : residual<double>(mg, (int)l, mg.stream, 0);
-        if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-          e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
-                                       : residual<double>(mg, (int)l, mg.stream, 0);
-        if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        const float ms = time_candidate(res, mg.stream, a, b, e);
         if (e == cudaSuccess && ms < best_ms) {
           best_ms = ms;
           best_ts = ts;
@@ -1003,16 +1018,7 @@ static cudaError_t tune_level_applies(MG& mg) {
             if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
             ls.stagger = staggered ? (c + 1) / 2 : 0;
             L.ls = ls;
-            e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
-                                         : residual<double>(mg, (int)l, mg.stream, 0);
-            if (e == cudaSuccess) e = cudaEventRecord(a, mg.stream);
-            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-              e = mg.precision == kPrecF32 ? residual<float>(mg, (int)l, mg.stream, 0)
-                                           : residual<double>(mg, (int)l, mg.stream, 0);
-            if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(b);
-            float ms = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            const float ms = time_candidate(res, mg.stream, a, b, e);
             if (e == cudaSuccess && ms < best_ms) {
               best_ms = ms;
               best_diag = false;
@@ -1029,8 +1035,8 @@ static cudaError_t tune_level_applies(MG& mg) {
 }
 
 // Picks the cells per Vanka chunk of every smoothed level, and with a single
-// diagonal class the modes per tile (the whole set, 16 or 8: smaller tiles give
-// the small levels more CTAs), by timing sweeps on the level's own buffers for
+// diagonal class on levels with few cells the modes per tile (the whole set,
+// 16 or 8: smaller tiles give them more CTAs), by timing sweeps on the level's own buffers for
 // every candidate within the shared-memory budget; keeps the fastest.
 static cudaError_t tune_vanka(MG& mg) {
   const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
@@ -1043,7 +1049,9 @@ static cudaError_t tune_vanka(MG& mg) {
     if ((e = cudaMemsetAsync(L.d_r, 0, n * vb, mg.stream)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
     std::vector<int> tiles = {mg.vanka_tile};
-    if (mg.n_classes == 1)
+    // smaller tiles only where one-cell chunks of whole tiles leave the GPU short of CTAs
+    const long long units1 = (long long)L.hp.n_cells * ((L.hp.n_xi + mg.vanka_tile - 1) / mg.vanka_tile);
+    if (mg.n_classes == 1 && units1 < 152LL * 16)
       for (int t : {16, 8})
         if (t < mg.vanka_tile && t % kVankaVB == 0) tiles.push_back(t);
     int best_c = L.vanka_chunk, best_t = 0;
@@ -1060,15 +1068,8 @@ static cudaError_t tune_vanka(MG& mg) {
         if (e != cudaSuccess) break;
         L.vanka_chunk = c;
         L.vanka_tile = tile == mg.vanka_tile ? 0 : tile;
-        float ms = 0.0f;
-        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-          if (rep == 1) e = cudaEventRecord(a, mg.stream);
-          const bool ok = vk_launch(mg, L, mg.stream);
-          if (!ok) e = cudaErrorInvalidValue;
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(b, mg.stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        const float ms = time_candidate(
+            [&]() { return vk_launch(mg, L, mg.stream) ? cudaSuccess : cudaErrorInvalidValue; }, mg.stream, a, b, e);
         if (e == cudaSuccess && ms < best_ms) {
           best_ms = ms;
           best_c = c;

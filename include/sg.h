@@ -206,6 +206,21 @@ sg_status sg_apply(sg_ctx* ctx, int slab, const double* x, double* y, int transp
 sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
                         int transpose);
 
+/* sg_apply_host_async - y_host = A^(n) x_host (or A^T) for PAGE-LOCKED host
+ * vectors, pipelined.  The call enqueues the copy of x_host into one of two
+ * device staging slots owned by the context (allocated on the first call),
+ * the apply and the copy back to y_host on three internal streams, makes
+ * `stream` wait for the copy back, and returns without waiting.  The copy in
+ * starts as soon as its slot is free, NOT after the prior work of `stream`:
+ * x_host must hold its values when the call is made.  Consecutive calls
+ * alternate slots, so one call's copies overlap the neighbouring calls'
+ * applies.  The caller must not write x_host or read y_host until `stream`
+ * has been synchronized (or has passed the call).  Errors: SG_ERR_ARG for
+ * null, overlapping or pageable vectors (use sg_apply_host for those) and a
+ * slab out of range, before anything is enqueued. */
+sg_status sg_apply_host_async(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
+                              int transpose, sg_stream stream);
+
 /* sg_mg_setup - build the block-Jacobi geometric-multigrid preconditioner
  * (the matrix-free remark after eq. local_rhs_tensor: every chaos mode alpha
  * is preconditioned by one V-cycle of its diagonal block

@@ -19,7 +19,7 @@ from . import _abi
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32, SG_PREC_BF16 = (_abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32,
                                                       _abi.SG_PREC_BF16)
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_apply_shape", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_apply_shape", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_apply_host_async", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -181,6 +181,22 @@ def sg_apply_host(ctx, slab, x, y=None, transpose=False):
         y = np.empty(n, dtype=np.float64)
     _check(lib.sg_apply_host(ctx.handle, int(slab), C.c_void_p(ptr(x)), C.c_void_p(ptr(y)),
                              int(bool(transpose))), "sg_apply_host")
+    return y
+
+
+def sg_apply_host_async(ctx, slab, x, y, transpose=False, stream=None):
+    """Pipelined host-buffer apply (sg_apply_host_async): page-locked torch CPU
+    float64 tensors ``x`` (read) and ``y`` (written); returns without waiting,
+    ``y`` is valid once ``stream`` (default: the current CUDA stream) is
+    synchronized."""
+    n = ctx.info["n_unknowns"]
+    for t in (x, y):
+        if (not hasattr(t, "is_pinned") or t.is_cuda or not t.is_pinned() or t.numel() != n
+                or not t.is_contiguous() or str(t.dtype) != "torch.float64"):
+            raise ValueError("page-locked contiguous float64 CPU tensors of n_unknowns elements expected")
+    _check(_abi.load().sg_apply_host_async(ctx.handle, int(slab), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                           int(bool(transpose)), C.c_void_p(_stream_handle(stream))),
+           "sg_apply_host_async")
     return y
 
 

@@ -16,7 +16,8 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_solve_slab", "sg_apply_host_static", "sg_autotune", "sg_set_exact",
                    "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch",
                    "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient",
-                   "sg_stat_errors", "mc_solve_meshes", "sg_set_apply_shape"])
+                   "sg_stat_errors", "mc_solve_meshes", "sg_set_apply_shape",
+                   "sg_apply_host_async"])
 
 
 class sg_mesh(C.Structure):
@@ -118,6 +119,8 @@ def load():
     lib.sg_autotune.restype = C.c_int
     lib.sg_set_apply_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.sg_set_apply_shape.restype = C.c_int
+    lib.sg_apply_host_async.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
+    lib.sg_apply_host_async.restype = C.c_int
     lib.sg_apply_host_static.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     lib.sg_apply_host_static.restype = C.c_int
     lib.sg_destroy.argtypes = [vp]

@@ -44,6 +44,20 @@ void free_ctx_device(sg_ctx* c) {
   cudaFree(c->d_ybuf);
   cudaFree(c->d_krylov);
   if (c->host_stream) cudaStreamDestroy(c->host_stream);
+  {
+    sg_ctx::HostPipe& p = c->pipe;
+    for (cudaStream_t st : {p.in, p.cmp, p.out})
+      if (st) cudaStreamSynchronize(st);
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(p.dx[i]);
+      cudaFree(p.dy[i]);
+      for (cudaEvent_t ev : {p.ev_in[i], p.ev_done[i], p.ev_out[i]})
+        if (ev) cudaEventDestroy(ev);
+    }
+    for (cudaStream_t st : {p.in, p.cmp, p.out})
+      if (st) cudaStreamDestroy(st);
+    p = sg_ctx::HostPipe();
+  }
   if (c->mg) {
     sg::mg_free(*c->mg);
     delete c->mg;
@@ -215,6 +229,65 @@ sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_h
   if (e != cudaSuccess) return cuda_fail(e, "sg_apply_host: copy out");
   e = cudaStreamSynchronize(ctx->host_stream);
   if (e != cudaSuccess) return cuda_fail(e, "sg_apply_host: synchronize");
+  return SG_OK;
+}
+
+static bool is_page_locked(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+sg_status sg_apply_host_async(sg_ctx* ctx, int slab, const double* x_host, double* y_host, int transpose,
+                              sg_stream stream) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_apply_host_async: ctx is NULL");
+  if (!x_host || !y_host) return fail(SG_ERR_ARG, "sg_apply_host_async: null vector");
+  if (slab < 0 || slab >= ctx->hp.n_slabs) return fail(SG_ERR_ARG, "sg_apply_host_async: slab out of range");
+  const size_t n = (size_t)ctx->hp.n_xi * ctx->hp.n_t * ctx->hp.n_x;
+  if (x_host < y_host + n && y_host < x_host + n) return fail(SG_ERR_ARG, "sg_apply_host_async: x and y overlap");
+  if (!is_page_locked(x_host) || !is_page_locked(y_host))
+    return fail(SG_ERR_ARG, "sg_apply_host_async: vectors must be page-locked host memory");
+  sg_ctx::HostPipe& p = ctx->pipe;
+  cudaError_t e = cudaSuccess;
+  if (!p.ready) {
+    for (cudaStream_t* st : {&p.in, &p.cmp, &p.out})
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      for (cudaEvent_t* ev : {&p.ev_in[i], &p.ev_done[i], &p.ev_out[i]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaMalloc(&p.dx[i], n * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&p.dy[i], n * sizeof(double));
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sg_apply_host_async: workspace");
+    p.ready = true;
+  }
+  const int s = p.slot;
+  cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+  // copy in once the apply that last read this slot is done (not after the
+  // caller's stream, which waits for every earlier call's copy back)
+  if (p.used[s]) e = cudaStreamWaitEvent(p.in, p.ev_done[s], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p.dx[s], x_host, n * sizeof(double), cudaMemcpyHostToDevice, p.in);
+  if (e == cudaSuccess) e = cudaEventRecord(p.ev_in[s], p.in);
+  // apply after the copy in and after the copy out that last read this slot's y
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p.cmp, p.ev_in[s], 0);
+  if (e == cudaSuccess && p.used[s]) e = cudaStreamWaitEvent(p.cmp, p.ev_out[s], 0);
+  if (e == cudaSuccess) {
+    sg::ApplyParams prm;
+    fill_params(ctx, p.dx[s], p.dy[s], transpose, prm);
+    e = sg::launch_apply(ctx->hp, ctx->ls, prm, p.cmp);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(p.ev_done[s], p.cmp);
+  // copy out, and make the caller's stream wait for it
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p.out, p.ev_done[s], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(y_host, p.dy[s], n * sizeof(double), cudaMemcpyDeviceToHost, p.out);
+  if (e == cudaSuccess) e = cudaEventRecord(p.ev_out[s], p.out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(us, p.ev_out[s], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "sg_apply_host_async");
+  p.used[s] = true;
+  p.slot = s ^ 1;
   return SG_OK;
 }
 

@@ -348,6 +348,17 @@ struct sg_ctx {
   double* d_xbuf = nullptr;   // workspaces of sg_apply_host (lazy)
   double* d_ybuf = nullptr;
   cudaStream_t host_stream = nullptr;
+  // pipelined host-buffer apply (sg_apply_host_async, lazy): copies in, applies
+  // and copies out on three streams, through two device staging slots
+  struct HostPipe {
+    cudaStream_t in = nullptr, cmp = nullptr, out = nullptr;
+    double* dx[2] = {nullptr, nullptr};
+    double* dy[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    bool used[2] = {false, false};
+    int slot = 0;
+    bool ready = false;
+  } pipe;
   sg::MG* mg = nullptr;       // multigrid preconditioner (sg_mg_setup)
   sg::ExactData* exact = nullptr;  // manufactured solution (sg_set_exact)
   double* d_krylov = nullptr; // FGMRES workspace (lazy): V, Z, w, r and partial sums

@@ -281,3 +281,45 @@ def test_set_apply_shape_rejects_bad_shapes(cuda):
         assert sg.sg_get_info(ctx) == before
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("name", ["ragged-2d-q2-13x7", "config-2d-q2-64x64"])
+def test_host_async_pipeline_matches_device_apply(cuda, name):
+    """Five consecutive pipelined host-buffer applies (alternating staging
+    slots, mixed transposes) on a side stream give the device apply of each
+    input once the stream is synchronized."""
+    torch = cuda
+    spec = FULL_CASES[name]
+    ctx = sg.sg_setup_spec(spec)
+    try:
+        n = ctx.info["n_unknowns"]
+        xs = [torch.from_numpy(I.random_vector(spec, seed=100 + k)).pin_memory() for k in range(5)]
+        ys = [torch.full((n,), float("nan"), dtype=torch.float64).pin_memory() for _ in range(5)]
+        side = torch.cuda.Stream()
+        for k in range(5):
+            sg.sg_apply_host_async(ctx, 0, xs[k], ys[k], transpose=bool(k % 2), stream=side)
+        side.synchronize()
+        for k in range(5):
+            want = gpu_apply(torch, spec, xs[k].numpy(), transpose=bool(k % 2), ctx=ctx)
+            assert _rel(ys[k].numpy(), want) < 1e-14, k
+        ref = operator.SGProblem(spec).apply(xs[0].numpy()).reshape(-1)
+        assert _rel(ys[0].numpy(), ref) < TOL
+    finally:
+        ctx.destroy()
+
+
+def test_host_async_refuses_pageable_vectors(cuda):
+    import ctypes as C
+    from paper_2605_21046_gb300 import _abi
+    spec = FULL_CASES["ragged-2d-q2-13x7"]
+    ctx = sg.sg_setup_spec(spec)
+    try:
+        n = ctx.info["n_unknowns"]
+        x, y = np.zeros(n), np.zeros(n)
+        lib = _abi.load()
+        st = lib.sg_apply_host_async(ctx.handle, 0, C.c_void_p(x.ctypes.data), C.c_void_p(y.ctypes.data), 0, None)
+        assert st == _abi.SG_ERR_ARG
+        with pytest.raises(ValueError):
+            sg.sg_apply_host_async(ctx, 0, cuda.zeros(n, dtype=cuda.float64), cuda.zeros(n, dtype=cuda.float64))
+    finally:
+        ctx.destroy()

@@ -66,6 +66,25 @@ class SGProblem:
         y[:, :, self.bmask] = x[:, :, self.bmask]
         return y
 
+    def apply_node_rows(self, x, rows):
+        """The entries of y = A^(n) x at the spatial nodes ``rows``, for every
+        (alpha, i): the sums of ``apply`` with M_x and K_mu restricted to those
+        rows (same Dirichlet treatment).  Shape (N_xi, N_t, len(rows))."""
+        x = np.asarray(x, dtype=np.float64).reshape(self.shape)
+        rows = np.asarray(rows, dtype=np.int64)
+        xm = x.copy()
+        xm[:, :, self.bmask] = 0.0
+        flat = xm.reshape(-1, self.n_x).T                  # (N_x, N_xi*N_t)
+        sub = (self.n_xi, self.n_t, rows.size)
+        MX = (self.Mx[rows] @ flat).T.reshape(sub)
+        y = np.einsum('ij,ajn->ain', self.At, MX)
+        for t in range(len(self.mus)):
+            KX = (self.K[t][rows] @ flat).T.reshape(sub)
+            y += np.einsum('ab,ij,bjn->ain', self.G[t], self.Bt, KX)
+        bd = self.bmask[rows]
+        y[:, :, bd] = x[:, :, rows[bd]]
+        return y
+
     def apply_rows(self, x, outputs):
         """Selected entries of y = A^(n) x, each computed from the rows of
         M_x and K_mu assembled on the cells around its node only.

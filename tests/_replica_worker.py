@@ -20,7 +20,7 @@ def replica(rank, world, port, out_q):
     res["max"] = bench.max_over_ranks(1.5 + r, w)
     # the reference arm: rank 0 times the oracle and prints one line, the others print nothing
     import argparse
-    args = argparse.Namespace(steps=1, warmup=0)
+    args = argparse.Namespace(steps=1, warmup=0, ref_seconds=2.0)
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(args, w, r)

@@ -152,3 +152,17 @@ def test_assembled_matrix_agrees():
     x = np.random.default_rng(5).uniform(-1, 1, p.shape)
     y = (p.assembled() @ x.reshape(-1)).reshape(p.shape)
     assert np.abs(y - p.apply(x)).max() < 1e-14
+
+
+def test_node_row_apply_is_the_row_restriction_of_apply():
+    """apply_node_rows (used to time bounded samples of the apply) returns
+    exactly the selected node rows of apply, boundary rows included."""
+    from paper_2605_21046_gb300 import inputs as I
+    spec = dict(I.config_small_2d_q1(), cells=(7, 5))
+    p = operator.SGProblem(spec)
+    x = I.random_vector(spec, seed=3)
+    full = p.apply(x)
+    for rows in (np.arange(p.n_x), np.arange(10, 30), np.array([0, 5, p.n_x - 1, 17])):
+        got = p.apply_node_rows(x, rows)
+        assert got.shape == (p.n_xi, p.n_t, rows.size)
+        assert np.allclose(got, full[:, :, rows], rtol=0, atol=1e-14 * np.abs(full).max())

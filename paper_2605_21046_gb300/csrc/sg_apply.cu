@@ -89,7 +89,8 @@ size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int coef_rows, int nn
                 + nqd * n_t * n_t                        // Amq
                 + n_t + 3                                // Tb, Rt
                 + (premul ? coef_rows : nnz);            // G value per pair / per entry
-  size_t ints = (n_xi + 1) + n_xi + (premul ? coef_rows : 0);   // Gr, Pm, pair terms
+  size_t ints = (n_xi + 1) + n_xi + (premul ? coef_rows : 0)    // Gr, Pm, pair terms
+                + (size_t)chunk * nqd;                          // nodes of the chunk's cells
   // values, then 8-byte coupling entries at a 16-byte boundary, then ints
   return ((vals * value_bytes + 15) / 16) * 16 + 8 * (size_t)nnz + ints * sizeof(int);
 }

@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
   int* Gr = reinterpret_cast<int*>(Ge + p.nnz);                 // [n_xi+1]
   int* Pm = Gr + n_xi + 1;                                      // [n_xi]
   int* Pt = Pm + n_xi;                                          // [n_pairs] term of each pair
+  int* Nd = Pt + (premul ? p.n_pairs : 0);                      // [C][NKD] node of y / x, -1 on the boundary
 
   if (premul) {
     for (int k = tid; k < p.n_pairs; k += nthr) {
@@ -308,10 +309,11 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
         for (int idx = tid; idx < nc * per_cell; idx += nthr) Cs[idx] = A::in(p.ctab[c0 * per_cell + idx]);
       }
     }
-    for (int idx = tid; idx < nc * V * NKD; idx += nthr) {
-      const int a = idx % NKD;
-      const int cv = idx / NKD;
-      const int v = cv % V, c = cv / V;
+    // the global node of every (cell, local node) of the chunk, once per
+    // chunk instead of once per vector (the integer divisions by the mesh
+    // extents would otherwise dominate the gather and scatter)
+    for (int i = tid; i < nc * NKD; i += nthr) {
+      const int c = i / NKD, a = i - c * NKD;
       const long long gc = c0 + c;
       const int cx = (int)(gc % p.cells[0]);
       const int cy = (int)((gc / p.cells[0]) % p.cells[1]);
@@ -319,9 +321,19 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
       const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
-      T val = A::zero();
-      if (interior) val = A::in(xin[(long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx]);
-      Qs[(size_t)cv * SLOT + a] = val;
+      Nd[i] = interior ? (int)(((long long)gz * nny + gy) * nnx + gx) : -1;
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      const int* nd = Nd + c * NKD;
+      T* qc = Qs + (size_t)c * V * SLOT;
+      for (int j = tid; j < V * NKD; j += nthr) {
+        const int v = j / NKD, a = j - v * NKD;
+        const int node = nd[a];
+        T val = A::zero();
+        if (node >= 0) val = A::in(xin[(long long)v * p.n_x + node]);
+        qc[(size_t)v * SLOT + a] = val;
+      }
     }
     __syncthreads();
     // ---------------------------------------------------------- phase 1
@@ -427,21 +439,17 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
     for (int it = tid; it < nc * V; it += nthr) backward_cell<A, DIM, K>(Qs + (size_t)it * SLOT);
     __syncthreads();
     // ---------------------------------------------------------- phase 4
-    for (int idx = tid; idx < nc * V * NKD; idx += nthr) {
-      const int a = idx % NKD;
-      const int cv = idx / NKD;
-      const int v = cv % V, c = cv / V;
-      const long long gc = c0 + c;
-      const int cx = (int)(gc % p.cells[0]);
-      const int cy = (int)((gc / p.cells[0]) % p.cells[1]);
-      const int cz = (int)(gc / ((long long)p.cells[0] * p.cells[1]));
-      const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
-      bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
-      if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
-      if (interior) {
-        T val = A::mul(Tb[v % NT], Qs[(size_t)cv * SLOT + a]);
-        if (p.mode == kApplyResidual) val = A::neg(val);
-        A::add_out(yout + (long long)v * p.n_x + ((long long)gz * nny + gy) * nnx + gx, val);
+    for (int c = 0; c < nc; ++c) {
+      const int* nd = Nd + c * NKD;
+      const T* qc = Qs + (size_t)c * V * SLOT;
+      for (int j = tid; j < V * NKD; j += nthr) {
+        const int v = j / NKD, a = j - v * NKD;
+        const int node = nd[a];
+        if (node >= 0) {
+          T val = A::mul(Tb[v % NT], qc[(size_t)v * SLOT + a]);
+          if (p.mode == kApplyResidual) val = A::neg(val);
+          A::add_out(yout + (long long)v * p.n_x + node, val);
+        }
       }
     }
   }

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
   T* Cs = Qs + (size_t)C * ts_max * NT * SLOT;                  // [C][term][NQD]
   T* Wt = Cs + (size_t)C * nterm * NQD;                         // [ts][term]
   T* Amq = Wt + (size_t)ts_max * nterm;                         // [NQD][NT][NT]
+  int* Nd = reinterpret_cast<int*>(Amq + NQD * NT * NT);        // [C][NKD] node, -1 on the boundary
   const long long u_begin = (long long)blockIdx.x * p.units / gridDim.x;
   const long long u_end = (long long)(blockIdx.x + 1) * p.units / gridDim.x;
   int cur_prob = -1, cur_tile = -1;
@@ -85,18 +86,27 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
     // phase 0: gather
     for (int idx = tid; idx < nc * nterm * NQD; idx += nthr)
       Cs[idx] = A::in(P.ctab[(size_t)cell0 * nterm * NQD + idx]);
-    for (int idx = tid; idx < nc * VT * NKD; idx += nthr) {
-      const int a = idx % NKD;
-      const int cv = idx / NKD;
-      const int v = cv % VT, c = cv / VT;
+    // global nodes of the chunk's cells, once per chunk (not per vector)
+    for (int i = tid; i < nc * NKD; i += nthr) {
+      const int c = i / NKD, a = i - c * NKD;
       const int gc = cell0 + c;
       const int cx = gc % P.cells[0], cy = (gc / P.cells[0]) % P.cells[1], cz = gc / (P.cells[0] * P.cells[1]);
       const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
-      T val = A::zero();
-      if (interior) val = A::in(xin[(long long)(s0 * NT + v) * P.n_x + ((long long)gz * nny + gy) * nnx + gx]);
-      Qs[(size_t)cv * SLOT + a] = val;
+      Nd[i] = interior ? (int)(((long long)gz * nny + gy) * nnx + gx) : -1;
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      const int* nd = Nd + c * NKD;
+      T* qc = Qs + (size_t)c * VT * SLOT;
+      for (int j = tid; j < VT * NKD; j += nthr) {
+        const int v = j / NKD, a = j - v * NKD;
+        const int node = nd[a];
+        T val = A::zero();
+        if (node >= 0) val = A::in(xin[(long long)(s0 * NT + v) * P.n_x + node]);
+        qc[(size_t)v * SLOT + a] = val;
+      }
     }
     __syncthreads();
     // phase 1: values and reference gradients at the Gauss points
@@ -153,19 +163,17 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
     for (int it = tid; it < nc * VT; it += nthr) backward_cell<A, DIM, K>(Qs + (size_t)it * SLOT);
     __syncthreads();
     // phase 4: scale by tau Bhat_ii and add into y
-    for (int idx = tid; idx < nc * VT * NKD; idx += nthr) {
-      const int a = idx % NKD;
-      const int cv = idx / NKD;
-      const int v = cv % VT, c = cv / VT;
-      const int gc = cell0 + c;
-      const int cx = gc % P.cells[0], cy = (gc / P.cells[0]) % P.cells[1], cz = gc / (P.cells[0] * P.cells[1]);
-      const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
-      bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
-      if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
-      if (interior) {
-        T val = A::mul(A::in(p.tb[v % NT]), Qs[(size_t)cv * SLOT + a]);
-        if (p.mode == kApplyResidual) val = A::neg(val);
-        A::add_out(yout + (long long)(s0 * NT + v) * P.n_x + ((long long)gz * nny + gy) * nnx + gx, val);
+    for (int c = 0; c < nc; ++c) {
+      const int* nd = Nd + c * NKD;
+      const T* qc = Qs + (size_t)c * VT * SLOT;
+      for (int j = tid; j < VT * NKD; j += nthr) {
+        const int v = j / NKD, a = j - v * NKD;
+        const int node = nd[a];
+        if (node >= 0) {
+          T val = A::mul(A::in(p.tb[v % NT]), qc[(size_t)v * SLOT + a]);
+          if (p.mode == kApplyResidual) val = A::neg(val);
+          A::add_out(yout + (long long)(s0 * NT + v) * P.n_x + node, val);
+        }
       }
     }
     u += nc;
@@ -191,7 +199,8 @@ size_t mc_smem_bytes(int dim, int k, int n_t, int ts, int n_terms, int chunk, in
   const size_t nqd = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
   const size_t vals = (size_t)chunk * ts * n_t * (1 + dim) * nqd + (size_t)chunk * n_terms * nqd +
                       (size_t)ts * n_terms + nqd * n_t * n_t;
-  return vals * value_bytes;
+  // values, then the chunk's node indices at a 4-byte boundary
+  return ((vals * value_bytes + 3) / 4) * 4 + (size_t)chunk * nqd * sizeof(int);
 }
 
 void mc_amq(const HostProblem& hp, const std::vector<double>& Tm, std::vector<double>& amq) {

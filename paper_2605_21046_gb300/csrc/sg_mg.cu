@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
   const int LN = LX * LYZ;
   T* Rl = reinterpret_cast<T*>(smem_raw);           // [tile vectors][LN]
   T* Zc = Rl + (size_t)VTM * LN;                    // [tile vectors][LN]
+  int* Gn = reinterpret_cast<int*>(Zc + (size_t)VTM * LN);   // [LN] global node, -1 outside / on the boundary
+  int* Gp = Gn + LN;                                         // [LN] 1 for nodes no other chunk touches
   const W* inv = static_cast<const W*>(p.inv);
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
   const int cpr = (p.cells[0] + C - 1) / C;         // chunks per row of cells
@@ -139,18 +141,26 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
     const int nc = min(C, p.cells[0] - cx0);
     const int lxn = nc * K + 1;
     __syncthreads();
-    // gather r on the chunk's node grid; clear the corrections
-    for (int idx = tid; idx < V * LN; idx += nthr) {
-      const int v = idx / LN, ln = idx - v * LN;
+    // the chunk's nodes: global index (or -1) and whether only this chunk touches them
+    for (int ln = tid; ln < LN; ln += nthr) {
       const int lx = ln % LX, lyz = ln / LX;
-      T val = T(0);
+      const int ly = lyz % N, lz = DIM == 3 ? lyz / N : 0;
+      int node = -1, priv = 0;
       if (lx < lxn) {
-        const int gx = cx0 * K + lx, gy = cy * K + lyz % N, gz = DIM == 3 ? cz * K + lyz / N : 0;
+        const int gx = cx0 * K + lx, gy = cy * K + ly, gz = DIM == 3 ? cz * K + lz : 0;
         bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
         if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
-        if (in) val = p.r[(voff + v) * p.n_x + ((long long)gz * nny + gy) * nnx + gx];
+        if (in) node = (int)(((long long)gz * nny + gy) * nnx + gx);
+        priv = lx > 0 && lx < lxn - 1 && ly > 0 && ly < K && (DIM == 2 || (lz > 0 && lz < K));
       }
-      Rl[idx] = val;
+      Gn[ln] = node;
+      Gp[ln] = priv;
+    }
+    __syncthreads();
+    // gather r on the chunk's node grid; clear the corrections
+    for (int idx = tid; idx < V * LN; idx += nthr) {
+      const int v = idx / LN, node = Gn[idx - v * LN];
+      Rl[idx] = node >= 0 ? p.r[(voff + v) * p.n_x + node] : T(0);
       Zc[idx] = T(0);
     }
     __syncthreads();
@@ -162,10 +172,9 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
       const int c = cb % nc, b = b0 + cb / nc;
       const int i = rho / NKD, a = rho - i * NKD;
       const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
-      const int gx = (cx0 + c) * K + ax, gy = cy * K + ay, gz = DIM == 3 ? cz * K + az : 0;
-      bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
-      if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
-      if (!in) continue;
+      const int lbase = c * K;                       // local x of the cell's first node
+      const int lna = (lbase + ax) + LX * (ay + (DIM == 3 ? N * az : 0));
+      if (Gn[lna] < 0) continue;                     // Dirichlet row
       const long long cell = ((long long)cz * p.cells[1] + cy) * p.cells[0] + cx0 + c;
       const W* M = inv + ((long long)p.blk_cls[b] * p.n_cells + cell) * NP * p.npp;
       int al[VB];
@@ -174,7 +183,6 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
       T acc[VB];
 #pragma unroll
       for (int u = 0; u < VB; ++u) acc[u] = T(0);
-      const int lbase = c * K;                       // local x of the cell's first node
       if constexpr (TRANS) {
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -208,9 +216,9 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
           }
         }
       }
-      const int mult = (gx % K == 0 ? 2 : 1) * (gy % K == 0 ? 2 : 1) * (DIM == 3 && gz % K == 0 ? 2 : 1);
+      // patches sharing the node (cell corners and faces: the local coordinate is 0 or K)
+      const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
       const T sc = p.omega / T(mult);
-      const int lna = (lbase + ax) + LX * (ay + (DIM == 3 ? N * az : 0));
 #pragma unroll
       for (int u = 0; u < VB; ++u)
         if (al[u] >= 0) atomicAdd(&Zc[(size_t)(al[u] * NT + i) * LN + lna], sc * acc[u]);
@@ -219,17 +227,11 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
     // write x: chunk-private nodes directly, shared outer nodes atomically
     for (int idx = tid; idx < V * LN; idx += nthr) {
       const int v = idx / LN, ln = idx - v * LN;
-      const int lx = ln % LX, lyz = ln / LX;
-      if (lx >= lxn) continue;
-      const int ly = lyz % N, lz = DIM == 3 ? lyz / N : 0;
-      const int gx = cx0 * K + lx, gy = cy * K + ly, gz = DIM == 3 ? cz * K + lz : 0;
-      bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
-      if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
-      if (!in) continue;
+      const int node = Gn[ln];
+      if (node < 0) continue;
       const T val = Zc[idx];
-      T* dst = p.x + (voff + v) * p.n_x + ((long long)gz * nny + gy) * nnx + gx;
-      const bool priv = lx > 0 && lx < lxn - 1 && ly > 0 && ly < K && (DIM == 2 || (lz > 0 && lz < K));
-      if (priv) *dst += val;
+      T* dst = p.x + (voff + v) * p.n_x + node;
+      if (Gp[ln]) *dst += val;
       else atomicAdd(dst, val);
     }
   }
@@ -765,18 +767,19 @@ sg_status level_diag_shape(MGLevel& L, int ts, int max_chunk, int vb) {
 }
 
 // Cells per Vanka chunk: up to 8, within the shared-memory budget.
-int vanka_chunk(const MGLevel& L, int tile_modes, size_t value_bytes, size_t budget) {
-  const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
-  const size_t V = (size_t)tile_modes * L.hp.n_t;
-  int best = 0;
-  for (int c = 1; c <= std::min(8, L.hp.cells[0]); ++c)
-    if (2 * V * (size_t)(c * L.hp.k + 1) * lyz * value_bytes <= budget) best = c;
-  return best;
-}
-
 size_t vanka_smem(const MGLevel& L, int tile_modes, int chunk, size_t value_bytes) {
   const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
-  return 2 * (size_t)tile_modes * L.hp.n_t * (size_t)(chunk * L.hp.k + 1) * lyz * value_bytes;
+  const size_t ln = (size_t)(chunk * L.hp.k + 1) * lyz;   // nodes of a chunk
+  // r and the corrections for every vector of the tile, then the nodes' global
+  // indices and private flags
+  return 2 * (size_t)tile_modes * L.hp.n_t * ln * value_bytes + 2 * ln * sizeof(int);
+}
+
+int vanka_chunk(const MGLevel& L, int tile_modes, size_t value_bytes, size_t budget) {
+  int best = 0;
+  for (int c = 1; c <= std::min(8, L.hp.cells[0]); ++c)
+    if (vanka_smem(L, tile_modes, c, value_bytes) <= budget) best = c;
+  return best;
 }
 
 template <typename T, typename W, int DIM, int K, int NT>

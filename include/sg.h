@@ -206,8 +206,9 @@ sg_status sg_apply(sg_ctx* ctx, int slab, const double* x, double* y, int transp
 sg_status sg_apply_host(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
                         int transpose);
 
-/* sg_apply_host_async - y_host = A^(n) x_host (or A^T) for PAGE-LOCKED host
- * vectors, pipelined.  The call enqueues the copy of x_host into one of two
+/* sg_apply_host_async - y_host = A^(n) x_host (eq. local_rhs_tensor; A^(n)^T
+ * when transpose != 0) for PAGE-LOCKED host vectors of n_unknowns doubles in
+ * the layout above, pipelined.  The call enqueues the copy of x_host into one of two
  * device staging slots owned by the context (allocated on the first call),
  * the apply and the copy back to y_host on three internal streams, makes
  * `stream` wait for the copy back, and returns without waiting.  The copy in
@@ -339,8 +340,9 @@ sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, doub
  * the order of the atomic additions. */
 sg_status sg_autotune(sg_ctx* ctx, int reps);
 
-/* sg_set_apply_shape - fix the apply launch shape of this context instead of
- * the default or tuned one: `chunk` cells per shared-memory chunk, `threads`
+/* sg_set_apply_shape - fix the launch shape of this context's apply (the
+ * operator of eq. local_rhs_tensor, as sg_apply) instead of the default or
+ * tuned one: `chunk` cells per shared-memory chunk, `threads`
  * per CTA (a multiple of 32 within the kernel's launch bound, with
  * threads * items_per_thread >= N_xi), and `stagger` cells in the first chunk
  * of the upper half of the CTAs (0: a full chunk; at most `chunk`).  For

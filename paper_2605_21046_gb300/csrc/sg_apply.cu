@@ -12,8 +12,10 @@
 // A chunk holds ALL N_xi * N_t vectors of its cells in shared memory, because
 // the Gauss-point work couples every chaos mode (through G_mu) and every time
 // node (through A_t):
-//   phase 0  gather the chunk's nodal values of every vector (Dirichlet
-//            nodes read as 0) and the coefficient values of its cells, as
+//   phase 0  compute the global node of every (cell, local node) of the
+//            chunk once into shared memory, gather the chunk's nodal values
+//            of every vector through it (Dirichlet nodes read as 0), and the
+//            coefficient values of its cells, as
 //            products G value x a_mu(x_q) for each distinct (mu, G value) pair
 //            of the coupling table (13 pairs for M = 4, P = 3: the mean term's
 //            1 and sqrt(1..3) for each xi_m), so the entries below need no

@@ -688,6 +688,56 @@ def next_applies(sg, torch, inputs, steps=100, warmup=10):
             "workloads": out}
 
 
+# the paper's own apply throughput on its discretisation (Table 2: G unknowns/s
+# on its CPU cluster, by chaos degree) - context beside the GPU figure, not a target
+PAPER_TABLE2_GUPS = {0: 1.265, 1: 0.434, 2: 0.286, 3: 0.237}
+
+
+def next_paper(sg, torch, inputs, steps=30, warmup=5):
+    """The FP64 apply on the paper's own benchmark discretisation (128x128 Q3 on
+    (-1, 1)^2, dG(3), M = 4, the squared coefficient with 11 modes) for chaos
+    degree 0..3 (148,225 nodes x 4 time nodes x 1..35 modes), autotuned shape,
+    rotating x/y pairs larger than L2, mean per-launch CUDA-event time."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for P in sorted(PAPER_TABLE2_GUPS):
+        spec = inputs.config_paper_q3(P=P)
+        ctx = sg.sg_setup_spec(spec, sg.SG_PREC_FP64)
+        try:
+            sg.sg_autotune(ctx, reps=5)
+            n = ctx.info["n_unknowns"]
+            R = max(2, math.ceil(2.2 * L2_BYTES / (16 * n)))
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(inputs.SEED_X)
+            X = [torch.rand(n, dtype=torch.float64, device=dev, generator=gen) * 2 - 1 for _ in range(R)]
+            Y = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(R)]
+            for k in range(warmup):
+                sg.sg_apply(ctx, 0, X[k % R], Y[k % R], False, stream)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with ClockSampler(torch.cuda.current_device()) as clk:
+                for k in range(steps):
+                    ev[k][0].record(stream)
+                    sg.sg_apply(ctx, 0, X[k % R], Y[k % R], False, stream)
+                    ev[k][1].record(stream)
+                torch.cuda.synchronize()
+            assert torch.isfinite(Y[0]).all()
+            t = statistics.mean(a.elapsed_time(b) for a, b in ev) / 1e3
+            out[f"P{P}"] = {"chaos_modes": ctx.info["n_xi"], "unknowns": n, "ms_per_apply": 1e3 * t,
+                            "value": n / t / 1e9, "unit": UNIT, "paper_table2_cpu_cluster": PAPER_TABLE2_GUPS[P],
+                            "launch": {"chunk_cells": ctx.info["chunk"], "grid": ctx.info["grid"],
+                                       "threads": ctx.info["threads"], "stagger": ctx.info["stagger"]},
+                            "clocks": clk.summary()}
+            del X, Y
+        finally:
+            ctx.destroy()
+            torch.cuda.empty_cache()
+    return {"row": "paper discretisation", "metric": METRIC, "unit": UNIT,
+            "workload": "128x128 Q3 on (-1,1)^2, dG(3), M=4, squared coefficient (11 modes)",
+            "paper_context": "Table 2 of the paper, its CPU cluster; context only", "degrees": out}
+
+
 def next_vcycle(sg, torch, inputs, profile_range=False):
     """One V-cycle of the block-Jacobi multigrid (all modes at once) on the
     64x64 Q2 P=3 and 32^3 Q2 P=3 workloads, per precision: device ms per
@@ -750,6 +800,8 @@ def run_next(args, world, rank, local):
                 out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range)
             elif row == "applies":
                 out = next_applies(sg, torch, inputs)
+            elif row == "paper":
+                out = next_paper(sg, torch, inputs)
             else:
                 raise ValueError(row)
         except sg.SGError as ex:
@@ -779,7 +831,7 @@ def main():
     ap.add_argument("--suite", choices=["apply", "next"], default="apply",
                     help="apply: the headline line; next: one line per solver-side row")
     ap.add_argument("--rows", default="mixed,mc,adjoint", help="rows of --suite next "
-                    "(mixed, mc, adjoint, vcycle, applies)")
+                    "(mixed, mc, adjoint, vcycle, applies, paper)")
     ap.add_argument("--mc-samples", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

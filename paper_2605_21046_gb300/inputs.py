@@ -60,6 +60,36 @@ def config_2d_q2_128(seed=128):
                 coef=linear_sine_coef(4, 2, 0.05, [(m, m) for m in range(1, 5)], a0_cells=a0))
 
 
+def paper_coefficient(d_min=0.2):
+    """The paper's benchmark coefficient d_min + (xi1 x1^2 + xi2 x1 x2 + xi3 x2^2 + xi4)^2
+    (Sec. 4, eq. diffusion_benchmark) written in the Hermite basis as separable
+    pieces: with g = (x1^2, x1 x2, x2^2, 1), the mean term d_min + sum_m g_m^2,
+    sqrt(2) g_m^2 on Psi_{2 e_m} and 2 g_m g_n on Psi_{e_m + e_n} (11 modes)."""
+    from math import sqrt
+    g = [[("pow", 2), ("one", 0)], [("pow", 1), ("pow", 1)], [("one", 0), ("pow", 2)], [("one", 0), ("one", 0)]]
+
+    def mul(f1, f2):
+        return [(("pow", (f1[d][1] if f1[d][0] == "pow" else 0) + (f2[d][1] if f2[d][0] == "pow" else 0)))
+                for d in range(2)]
+    M = 4
+    pieces = [dict(mu=(0,) * M, amp=d_min, factors=[("one", 0)] * 2)]
+    for m in range(M):
+        pieces.append(dict(mu=(0,) * M, amp=1.0, factors=mul(g[m], g[m])))
+        pieces.append(dict(mu=tuple(2 * (i == m) for i in range(M)), amp=sqrt(2.0), factors=mul(g[m], g[m])))
+    for m in range(M):
+        for n in range(m + 1, M):
+            pieces.append(dict(mu=tuple(int(i in (m, n)) for i in range(M)), amp=2.0, factors=mul(g[m], g[n])))
+    return pieces
+
+
+def config_paper_q3(cells=128, P=3, n_slabs=64):
+    """The paper's finite-chaos benchmark discretisation (Sec. 4.3-4.4): D = (-1, 1)^2,
+    Q3 in space, dG(3) in time, T = 1, M = 4, total degree P, the squared coefficient
+    above with d_min = 0.2; 128^2 cells and tau = 1/64 are the sizes of its tables."""
+    return dict(name=f"2d-q3-dg3-{cells}x{cells}-M4P{P}-paper", dim=2, cells=(cells, cells), lo=(-1.0, -1.0),
+                hi=(1.0, 1.0), k=3, r=3, n_slabs=n_slabs, T=1.0, M=4, P=P, coef=paper_coefficient())
+
+
 def config_adjoint_2d(cells=(4, 4), k=1, r=1, n_slabs=3, M=2, P=2, seed=None):
     """A small coefficient-gradient case: a = a0(x) + 0.2 x^2 + 0.1 xi_1
     sin(pi x) + 0.1 xi_2 sin(pi y) on the unit square, a0 a per-cell field

@@ -72,24 +72,7 @@ def test_apply_matches_oracle_full(cuda, name, prec):
         assert _rel(got, want) < TOL, (name, prec, tr, _rel(got, want))
 
 
-def paper_coefficient(d_min=0.2):
-    """The paper's benchmark coefficient d_min + (xi1 x1^2 + xi2 x1 x2 + xi3 x2^2 + xi4)^2
-    (Sec. 4, eq. diffusion_benchmark) in the Hermite basis: 11 modes of even degree."""
-    from math import sqrt
-    g = [[("pow", 2), ("one", 0)], [("pow", 1), ("pow", 1)], [("one", 0), ("pow", 2)], [("one", 0), ("one", 0)]]
-
-    def mul(f1, f2):
-        return [(("pow", (f1[d][1] if f1[d][0] == "pow" else 0) + (f2[d][1] if f2[d][0] == "pow" else 0)))
-                for d in range(2)]
-    M = 4
-    pieces = [dict(mu=(0,) * M, amp=d_min, factors=[("one", 0)] * 2)]
-    for m in range(M):
-        pieces.append(dict(mu=(0,) * M, amp=1.0, factors=mul(g[m], g[m])))
-        pieces.append(dict(mu=tuple(2 * (i == m) for i in range(M)), amp=sqrt(2.0), factors=mul(g[m], g[m])))
-    for m in range(M):
-        for n in range(m + 1, M):
-            pieces.append(dict(mu=tuple(int(i in (m, n)) for i in range(M)), amp=2.0, factors=mul(g[m], g[n])))
-    return pieces
+paper_coefficient = I.paper_coefficient   # the input spec lives with the other workloads
 
 
 @pytest.mark.parametrize("prec", list(PRECISIONS))

@@ -65,4 +65,9 @@ def test_setup_rejects_bad_arguments_without_device_work(lib):
     # NULL arguments
     assert lib.sg_apply(None, 0, None, None, 0, None) == _abi.SG_ERR_ARG
     assert lib.sg_get_info(None, None) == _abi.SG_ERR_ARG
+    assert lib.sg_apply_host(None, 0, None, None, 0) == _abi.SG_ERR_ARG
+    assert lib.sg_apply_host_async(None, 0, None, None, 0, None) == _abi.SG_ERR_ARG
+    assert b"sg_apply_host_async" in lib.sg_last_error()
+    assert lib.sg_set_apply_shape(None, 1, 32, 0) == _abi.SG_ERR_ARG
+    assert lib.sg_autotune(None, 3) == _abi.SG_ERR_ARG
     lib.sg_destroy(None)

@@ -150,7 +150,7 @@ def gradient(spec, exact, cell_piece=-1, nominal_spec=None):
     Us = march(op, man)
     J = energy_of(op, Us[-1])
     lams = adjoint_states(op, Us)
-    pieces = spec["coef"]
+    pieces = op.spec["coef"]
     mus = coeff.terms(pieces)
     g_amp = np.zeros(len(pieces))
     for j, piece in enumerate(pieces):

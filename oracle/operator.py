@@ -27,10 +27,12 @@ class SGProblem:
     """All assembled factors of the slab operator for one problem spec.
 
     spec keys: dim, cells, lo, hi, k (FE degree), r (time degree), n_slabs, T,
-    M, P (chaos order), coef (list of separable pieces, see ``oracle.coeff``).
+    M, P (chaos order), coef (list of separable pieces, or a ``square_of_linear``
+    description; see ``oracle.coeff``).
     ``assemble_space=False`` skips the global M_x/K_mu (for sampled rows)."""
 
     def __init__(self, spec, assemble_space=True):
+        spec = dict(spec, coef=coeff.as_pieces(spec["coef"], int(spec["M"])))
         self.spec = spec
         self.mesh = space_fe.Mesh(spec["dim"], spec["cells"], spec["lo"], spec["hi"], spec["k"])
         self.tau = float(spec["T"]) / int(spec["n_slabs"])

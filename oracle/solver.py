@@ -43,6 +43,7 @@ def direct_solve(problem, b):
 
 def coarse_specs(spec):
     """The spec of every multigrid level, finest first."""
+    spec = dict(spec, coef=coeff.as_pieces(spec["coef"], int(spec["M"])))
     out = [spec]
     cur = spec
     while all(c % 2 == 0 and c > 2 for c in cur["cells"][: cur["dim"]]):

@@ -14,7 +14,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import _abi
+from . import _abi, coefficients
 
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32, SG_PREC_BF16 = (_abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32,
                                                       _abi.SG_PREC_BF16)
@@ -86,6 +86,7 @@ def mesh_spec(dim, cells, lo, hi):
 
 
 def _coeff_struct(pieces, M, dim):
+    pieces = coefficients.pieces(pieces, M)
     n = len(pieces)
     mu = np.zeros((n, M), dtype=np.int32)
     amp = np.zeros(n, dtype=np.float64)
@@ -120,7 +121,8 @@ def _coeff_struct(pieces, M, dim):
 def sg_setup(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef, precision=0):
     """sg_setup of include/sg.h.  ``mesh`` is an sg_mesh or a dict with
     dim/cells/lo/hi; ``coef`` a list of separable pieces
-    {"mu", "amp", "factors": [(kind, k) per direction], "cell_scale"}."""
+    {"mu", "amp", "factors": [(kind, k) per direction], "cell_scale"} or a
+    ``square_of_linear`` description (``coefficients``)."""
     lib = _abi.load()
     if isinstance(mesh, dict):
         mesh = mesh_spec(mesh["dim"], mesh["cells"], mesh["lo"], mesh["hi"])
@@ -129,7 +131,7 @@ def sg_setup(mesh, fe_degree, time_degree, n_slabs, T, M, chaos_order, coef, pre
     _check(lib.sg_setup(C.byref(mesh), fe_degree, time_degree, n_slabs, float(T), M, chaos_order,
                         C.byref(cs), precision, C.byref(h)), "sg_setup")
     del keep
-    return SGContext(h.value, len(coef))
+    return SGContext(h.value, cs.n_pieces)
 
 
 def sg_setup_spec(spec, precision=0):

@@ -3,9 +3,14 @@ the random vectors fed to the operator.  Plain data only - no part of the
 method is computed here; the library and the oracle each discretise a spec
 on their own.
 
-Spec format: dict(dim, cells, lo, hi, k, r, n_slabs, T, M, P, coef), coef a
-list of separable pieces {"mu", "amp", "factors": [(kind, k) per direction],
-"cell_scale": None | per-cell values} describing a(x, xi) = sum_mu a_mu(x) Psi_mu(xi).
+Spec format: dict(dim, cells, lo, hi, k, r, n_slabs, T, M, P, coef), coef
+either a list of separable pieces {"mu", "amp", "factors": [(kind, k) per
+direction], "cell_scale": None | per-cell values} describing
+a(x, xi) = sum_mu a_mu(x) Psi_mu(xi) when every mu is a first-degree or zero
+index (then Psi_mu is xi_m or 1 and the pieces are the coefficient as
+written), or {"form": "square_of_linear", "d_min", "g"} for
+a = d_min + (sum_m xi_m g_m(x))^2, which the library and the oracle each
+expand on the chaos themselves.
 """
 import numpy as np
 
@@ -62,24 +67,12 @@ def config_2d_q2_128(seed=128):
 
 def paper_coefficient(d_min=0.2):
     """The paper's benchmark coefficient d_min + (xi1 x1^2 + xi2 x1 x2 + xi3 x2^2 + xi4)^2
-    (Sec. 4, eq. diffusion_benchmark) written in the Hermite basis as separable
-    pieces: with g = (x1^2, x1 x2, x2^2, 1), the mean term d_min + sum_m g_m^2,
-    sqrt(2) g_m^2 on Psi_{2 e_m} and 2 g_m g_n on Psi_{e_m + e_n} (11 modes)."""
-    from math import sqrt
-    g = [[("pow", 2), ("one", 0)], [("pow", 1), ("pow", 1)], [("one", 0), ("pow", 2)], [("one", 0), ("one", 0)]]
-
-    def mul(f1, f2):
-        return [(("pow", (f1[d][1] if f1[d][0] == "pow" else 0) + (f2[d][1] if f2[d][0] == "pow" else 0)))
-                for d in range(2)]
-    M = 4
-    pieces = [dict(mu=(0,) * M, amp=d_min, factors=[("one", 0)] * 2)]
-    for m in range(M):
-        pieces.append(dict(mu=(0,) * M, amp=1.0, factors=mul(g[m], g[m])))
-        pieces.append(dict(mu=tuple(2 * (i == m) for i in range(M)), amp=sqrt(2.0), factors=mul(g[m], g[m])))
-    for m in range(M):
-        for n in range(m + 1, M):
-            pieces.append(dict(mu=tuple(int(i in (m, n)) for i in range(M)), amp=2.0, factors=mul(g[m], g[n])))
-    return pieces
+    (Sec. 4, eq. diffusion_benchmark) in its physical form: d_min and the four
+    functions g = (x1^2, x1 x2, x2^2, 1) multiplying xi_1..xi_4.  Each side
+    writes it on the Hermite chaos with its own code."""
+    one = ("one", 0)
+    g = [[("pow", 2), one], [("pow", 1), ("pow", 1)], [one, ("pow", 2)], [one, one]]
+    return dict(form="square_of_linear", d_min=float(d_min), g=g)
 
 
 def config_paper_q3(cells=128, P=3, n_slabs=64):

@@ -72,15 +72,12 @@ def test_apply_matches_oracle_full(cuda, name, prec):
         assert _rel(got, want) < TOL, (name, prec, tr, _rel(got, want))
 
 
-paper_coefficient = I.paper_coefficient   # the input spec lives with the other workloads
-
-
 @pytest.mark.parametrize("prec", list(PRECISIONS))
 def test_paper_squared_coefficient(cuda, prec):
     # Q3 / dG(3) on (-1, 1)^2 with the paper's coefficient
     M = 4
     spec = dict(name="paper", dim=2, cells=(6, 6), lo=(-1.0, -1.0), hi=(1.0, 1.0), k=3, r=3, n_slabs=16, T=1.0,
-                M=M, P=2, coef=paper_coefficient())
+                M=M, P=2, coef=I.paper_coefficient())
     p = operator.SGProblem(spec)
     assert len(p.mus) == 11
     x = I.random_vector(spec, seed=5)

@@ -15,7 +15,7 @@ import paper_2605_21046_gb300 as sg
 from paper_2605_21046_gb300 import inputs as I
 from oracle import hermite, manufactured, operator
 
-from test_apply_gpu import paper_coefficient
+from paper_2605_21046_gb300.inputs import paper_coefficient
 
 pytestmark = pytest.mark.gpu
 RHS_TOL = 1e-9

@@ -19,8 +19,7 @@ import pytest
 
 from oracle import hermite, manufactured, operator
 from paper_2605_21046_gb300 import inputs as I
-
-from test_apply_gpu import paper_coefficient
+from paper_2605_21046_gb300.inputs import paper_coefficient
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

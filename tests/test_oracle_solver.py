@@ -91,7 +91,7 @@ def test_diagonal_classes():
     keys, cls = solver.diagonal_classes(p.G)
     assert len(keys) == 1                      # xi-linear: every diagonal block is the mean block
     # the paper's even coefficient: different diagonal blocks
-    from test_apply_gpu import paper_coefficient
+    from paper_2605_21046_gb300.inputs import paper_coefficient
     s = dict(dim=2, cells=(2, 2), lo=(-1.0, -1.0), hi=(1.0, 1.0), k=1, r=1, n_slabs=4, T=1.0, M=4, P=2,
              coef=paper_coefficient())
     q = operator.SGProblem(s)

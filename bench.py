@@ -28,8 +28,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SG operator applies"
 UNIT = "GDoF*modes/s"
-# FP64 FMA peak: 152 SMs x 2 FP64 FMA lanes per clock x 2 flop x 2070 MHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 FMA peak: SMs x 2 FP64 FMA lanes per SM per clock x 2 flop x maximum SM
+# clock; on GB300 152 SMs at 2070 MHz give 1.259 TFLOP/s.  fp64_peak_tflops()
+# reads the SM count and the maximum clock of the device that runs the bench.
+FP64_FMA_PER_SM_CLOCK = 2
+FP64_PEAK_TFLOPS = 152 * FP64_FMA_PER_SM_CLOCK * 2 * 2.070e9 / 1e12
+
+
+def fp64_peak_tflops(sm_max_mhz=None):
+    """The FP64 FMA peak of cuda:0 (SM count from the device, the maximum SM
+    clock sampled by nvidia-smi when given, else MEASURED_PEAKS.json's)."""
+    global FP64_PEAK_TFLOPS
+    try:
+        import torch
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        return FP64_PEAK_TFLOPS
+    mhz = sm_max_mhz or peaks().get("sm_max_mhz") or 2070.0
+    FP64_PEAK_TFLOPS = n_sm * FP64_FMA_PER_SM_CLOCK * 2 * float(mhz) * 1e6 / 1e12
+    return FP64_PEAK_TFLOPS
 # algorithmic work of the sum-factorised apply per unknown (FP64 flop) and
 # the algorithmic HBM bytes per unknown (read x, write y once)
 FLOP_PER_UNKNOWN = 166.0
@@ -340,6 +357,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     elapsed_ms, t_launch, clocks = time_applies(sg, torch, ctx, X, Y, args.steps, args.warmup, stream,
                                                 world, True, local, profile_range=args.profile_range)
+    fp64_peak_tflops((clocks or {}).get("sm_max_mhz"))
     value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
     assert torch.isfinite(Y[0]).all()
     y64 = Y[0].clone()

@@ -322,11 +322,14 @@ sg_status sg_adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int checkpoi
  * process exits): at most 2,097,152 unknowns, larger problems get SG_ERR_ARG.
  * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
  * routine).  Its first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current: make that first call before
- * any stream capture.  The context's device must be current.  Every call uses
- * the same array, which keeps the last call's contents (each call overwrites
- * what it reads); calls that overlap on the GPU, from several threads or
- * contexts, race on it.  Synchronous; runs on the legacy default stream. */
+ * (cudaGetSymbolAddress) with that device current, and looks it up again when
+ * the device's CUDA context has been replaced since (after cudaDeviceReset,
+ * for instance): make that first call before any stream capture.  The
+ * context's device must be current.  Every call uses the same array, which
+ * keeps the last call's contents (each call overwrites what it reads); calls
+ * that overlap on the GPU, from several threads or contexts, race on it.
+ * Synchronous: it copies with cudaMemcpy and launches on the legacy default
+ * stream, and returns once y is on the host. */
 sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
                                int transpose);
 

@@ -377,9 +377,7 @@ sg_status adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int K, int cell
   bp.out_sum = d_out;
   bp.out_cell = cell_piece >= 0 ? d_out + n_tab : nullptr;
   const size_t bsmem = bilin_smem(hp.dim, hp.k, nt, hp.n_xi, bp.nnz, n_tab, bchunk);
-  int n_sm = 152;
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, 0);
-  const int bgrid = (int)std::min<long long>((long long)n_sm * 2, hp.n_cells);
+  const int bgrid = (int)std::min<long long>(sg::sm_count() * 2, hp.n_cells);
   // J alone (no gradient asked): no backward sweep
   const bool want_grad = g_amp || (g_cell && cell_piece >= 0);
   for (int seg = n_ck - 1; want_grad && seg >= 0 && e == cudaSuccess && status == SG_OK; --seg) {
@@ -408,7 +406,7 @@ sg_status adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int K, int cell
       ++stats.adjoint_solves;
       stats.max_iterations = std::max(stats.max_iterations, ss.iterations);
       if (status != SG_OK) break;
-      k_zero_boundary<<<(int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, s>>>(lam, n, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
+      k_zero_boundary<<<(int)std::min<long long>((n + 255) / 256, sg::sm_count() * 16), 256, 0, s>>>(lam, n, hp.n_x, hp.nn[0], hp.nn[1], hp.nn[2], hp.dim);
       bp.lam = lam;
       bp.u = d_seg + (size_t)(slab - s0) * n;
       void* args[] = {&bp};

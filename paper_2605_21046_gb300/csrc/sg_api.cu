@@ -1,6 +1,8 @@
 // The extern "C" entry points of libsg declared in include/sg.h.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -89,6 +91,20 @@ void fill_params(const sg_ctx* c, const void* x, void* y, int transpose, sg::App
 
 namespace sg {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+long long sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cached[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev >= kMaxDev) dev = kMaxDev - 1;
+  int n = cached[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cached[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
 }  // namespace sg
 
 namespace sg {

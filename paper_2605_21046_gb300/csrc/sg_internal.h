@@ -313,6 +313,9 @@ sg_status stat_errors(const HostProblem& hp, const ExactData& E, const double* m
                       double t, double err[2], std::string& msg);
 // Records the message sg_last_error() returns on this thread.
 void set_last_error(const std::string& msg);
+// Streaming multiprocessors of the current device (read once per device;
+// grid caps of the grid-stride kernels are multiples of it).
+long long sm_count();
 sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
                  cudaStream_t s, std::string& msg,
                  cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t), int trans = 0);

@@ -94,7 +94,7 @@ __global__ void k_sub_from(const double* __restrict__ b, double* __restrict__ r,
 
 __global__ void k_sqrt_inplace(double* v) { v[0] = sqrt(v[0]); }
 
-int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, sg::sm_count() * 16)); }
 
 struct Ws {
   double *V, *Z, *w, *r, *part, *h, *h2, *nrm, *y;

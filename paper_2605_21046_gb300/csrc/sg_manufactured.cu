@@ -58,7 +58,7 @@ __global__ void k_moments(const double* __restrict__ u, double* __restrict__ mea
   }
 }
 
-int grid_of(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+int grid_of(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, sg::sm_count() * 16)); }
 
 double poly(const std::vector<double>& c, double t) {
   double s = 0.0;

@@ -74,7 +74,7 @@ __global__ void k_mc_finish(double* __restrict__ m2, long long n_x, double n) {
     m2[m] = n > 1 ? m2[m] / (n - 1) : 0.0;
 }
 
-int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
+int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, sg::sm_count() * 16)); }
 
 double psi(int n, double y) {
   // He_n(y) / sqrt(n!) by the three-term recurrence of the normalised polynomials
@@ -462,7 +462,7 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
       base.chunk = chunk;
       base.units = units;
       for (int i = 0; i < nt; ++i) base.tb[i] = h0.tau * h0.B_hat[i * nt + i];
-      grid = (int)std::max<long long>(1, std::min<long long>(units / chunk, 152LL * 2));
+      grid = (int)std::max<long long>(1, std::min<long long>(units / chunk, sg::sm_count() * 2));
     };
     build_base();
     auto mc_launch = [&](const double* x, double* y, const double* b, int mode, bool transfer) -> cudaError_t {

@@ -337,7 +337,7 @@ __global__ void mg_coarse(const T* __restrict__ b, T* __restrict__ x, const T* _
 // ------------------------------------------------------------------ host set-up
 
 int grid_for(long long n, int block) {
-  return (int)std::max<long long>(1, std::min<long long>((n + block - 1) / block, 152LL * 32));
+  return (int)std::max<long long>(1, std::min<long long>((n + block - 1) / block, sg::sm_count() * 32));
 }
 
 // In-place inverse of a dense n x n matrix (Gauss-Jordan, partial pivoting).
@@ -762,7 +762,7 @@ sg_status level_diag_shape(MGLevel& L, int ts, int max_chunk, int vb) {
   if (L.mc_chunk == 0) return SG_ERR_UNSUPPORTED;
   L.mc_smem = mc_smem_bytes(L.hp.dim, L.hp.k, L.hp.n_t, L.mc_ts, L.hp.n_terms, L.mc_chunk, vb);
   const long long units = (long long)((L.hp.n_xi + L.mc_ts - 1) / L.mc_ts) * L.hp.n_cells;
-  L.mc_grid = (int)std::max<long long>(1, std::min<long long>(units / std::max(1, L.mc_chunk), 152LL * 4));
+  L.mc_grid = (int)std::max<long long>(1, std::min<long long>(units / std::max(1, L.mc_chunk), sg::sm_count() * 4));
   return SG_OK;
 }
 
@@ -807,7 +807,7 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   const size_t smem = vanka_smem(L, tile, L.vanka_chunk, sizeof(T));
   const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
   const long long units = (long long)cpr * L.hp.cells[1] * L.hp.cells[2] * p.n_tiles;
-  const int grid = (int)std::min<long long>(units, 152LL * 8);
+  const int grid = (int)std::min<long long>(units, sg::sm_count() * 8);
   auto kern = trans ? &mg_vanka<T, W, DIM, K, NT, true> : &mg_vanka<T, W, DIM, K, NT, false>;
   kern<<<grid, 256, smem, s>>>(p);
   return cudaGetLastError();
@@ -1054,7 +1054,7 @@ static cudaError_t tune_vanka(MG& mg) {
     std::vector<int> tiles = {mg.vanka_tile};
     // smaller tiles only where one-cell chunks of whole tiles leave the GPU short of CTAs
     const long long units1 = (long long)L.hp.n_cells * ((L.hp.n_xi + mg.vanka_tile - 1) / mg.vanka_tile);
-    if (mg.n_classes == 1 && units1 < 152LL * 16)
+    if (mg.n_classes == 1 && units1 < sg::sm_count() * 16)
       for (int t : {16, 8})
         if (t < mg.vanka_tile && t % kVankaVB == 0) tiles.push_back(t);
     int best_c = L.vanka_chunk, best_t = 0;

@@ -24,7 +24,39 @@ static __device__ __align__(256) double g_static_scratch[2 * kStaticUnknowns];
 
 constexpr int kMaxDevices = 64;
 double* g_scratch_ptr[kMaxDevices] = {};
+// Identifier of the CUDA context the cached address belongs to: a device
+// reset (cudaDeviceReset) tears the primary context down, and the array gets
+// a new address in the next one, so the address is looked up again whenever
+// the current context is not the one it was taken in.
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context (0 if none or if the
+// driver cannot tell), through the driver's cuCtxGetCurrent / cuCtxGetId.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  void* c = nullptr;
+  if (get_current(&c) != 0 || !c) return 0;
+  unsigned long long id = 0;
+  return get_id(c, &id) == 0 ? id : 0;
+}
 
 sg_status fail(sg_status s, const char* m) {
   sg::set_last_error(m);
@@ -48,17 +80,19 @@ sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, doub
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev != ctx->device || dev < 0 || dev >= kMaxDevices)
     return fail(SG_ERR_ARG, "sg_apply_host_static: the context's device must be current");
-  // Once per device, with that device current: the device address of the
-  // static array (its host-side name is only a stand-in and must never be
-  // handed to a kernel).
+  // Once per device (and again after the device's context was replaced),
+  // with that device current: the device address of the static array (its
+  // host-side name is only a stand-in and must never be handed to a kernel).
   double* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long cid = current_context_id();
+    if (!g_scratch_ptr[dev] || cid == 0 || cid != g_scratch_ctx[dev]) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_static_scratch);
       if (e != cudaSuccess || !p) return fail(SG_ERR_CUDA, "sg_apply_host_static: cudaGetSymbolAddress failed");
       g_scratch_ptr[dev] = static_cast<double*>(p);
+      g_scratch_ctx[dev] = current_context_id();
     }
     base = g_scratch_ptr[dev];
   }

@@ -35,6 +35,23 @@ FP64_FMA_PER_SM_CLOCK = 2
 FP64_PEAK_TFLOPS = 152 * FP64_FMA_PER_SM_CLOCK * 2 * 2.070e9 / 1e12
 
 
+# FP32 FMA lanes per SM per clock (the FP32 pipe) and FP32 instructions one
+# double-word multiply-add takes (product with its exact error, TwoSum, two adds)
+FP32_FMA_PER_SM_CLOCK = 128
+DW_FP32_INSTR_PER_FMA = 12
+
+
+def fp32_peak_tflops(sm_max_mhz=None):
+    """FP32 FMA peak of cuda:0: SMs x 128 lanes x 2 flop x maximum SM clock."""
+    try:
+        import torch
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        n_sm = 152
+    mhz = sm_max_mhz or peaks().get("sm_max_mhz") or 2070.0
+    return n_sm * FP32_FMA_PER_SM_CLOCK * 2 * float(mhz) * 1e6 / 1e12
+
+
 def fp64_peak_tflops(sm_max_mhz=None):
     """The FP64 FMA peak of cuda:0 (SM count from the device, the maximum SM
     clock sampled by nvidia-smi when given, else MEASURED_PEAKS.json's)."""
@@ -356,7 +373,8 @@ def run_ours(args, world, rank, local):
     Y = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(R)]
     stream = torch.cuda.current_stream(dev)
     elapsed_ms, t_launch, clocks = time_applies(sg, torch, ctx, X, Y, args.steps, args.warmup, stream,
-                                                world, True, local, profile_range=args.profile_range)
+                                                world, True, local,
+                                                profile_range=args.profile_range and args.profile_variant == "fp64")
     fp64_peak_tflops((clocks or {}).get("sm_max_mhz"))
     value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
     assert torch.isfinite(Y[0]).all()
@@ -368,7 +386,8 @@ def run_ours(args, world, rank, local):
         ctx_dw = sg.sg_setup_spec(spec, sg.SG_PREC_DW)
         if not args.no_autotune:
             sg.sg_autotune(ctx_dw, reps=10)
-        e_dw, t_dw, _ = time_applies(sg, torch, ctx_dw, X, Y, args.steps, args.warmup, stream, world, False, local)
+        e_dw, t_dw, _ = time_applies(sg, torch, ctx_dw, X, Y, args.steps, args.warmup, stream, world, False, local,
+                                     profile_range=args.profile_range and args.profile_variant == "dw")
         sg.sg_apply(ctx_dw, 0, X[0], Y[0], False, stream)
         torch.cuda.synchronize()
         err = float((Y[0] - y64).abs().max() / y64.abs().max())
@@ -416,6 +435,17 @@ def run_ours(args, world, rank, local):
         sg.sg_apply_host(ctx, 0, xh[0], yh[0])
     e2e_sync = world * n * k_e2e / max_over_ranks(time.perf_counter() - t0, world) / 1e9
 
+    # the NEXT rows on their own workloads (single-GPU runs only)
+    next_rows = None
+    if world == 1 and not args.no_next:
+        next_rows = {}
+        for key, fn in (("mixed_precision", next_mixed_precision), ("mc_vs_sg", next_mc_vs_sg),
+                        ("adjoint", next_adjoint)):
+            t0 = time.perf_counter()
+            next_rows[key] = fn(sg, torch, inputs)
+            next_rows[key]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+
     pk = peaks()
     achieved_tf = FLOP_PER_UNKNOWN * n / t_launch / 1e12
     hbm_gbs = BYTES_PER_UNKNOWN * n / t_launch / 1e9
@@ -458,7 +488,18 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "variants": {"dw": dw, "l2_hot": hot},
             "solve": solve,
+            "next": next_rows,
         }
+        if dw is not None:
+            # the double-word apply runs on the FP32 pipe: 12 FP32 instructions per
+            # FP64-equivalent multiply-add, so its ceiling is the FP32 FMA peak / 12
+            fp32_peak = fp32_peak_tflops((clocks or {}).get("sm_max_mhz"))
+            dw_tf = dw["fp64_equivalent_tflops"]
+            line["roofline"]["dw"] = {"bound": "alu", "achieved": dw_tf, "peak": fp32_peak / DW_FP32_INSTR_PER_FMA,
+                                      "unit": "TFLOP/s (FP64-equivalent)",
+                                      "frac": dw_tf / (fp32_peak / DW_FP32_INSTR_PER_FMA),
+                                      "fp32_fma_peak_tflops": fp32_peak,
+                                      "fp32_instr_per_fp64_fma": DW_FP32_INSTR_PER_FMA}
         print(json.dumps(line), flush=True)
     ctx.destroy()
 
@@ -706,8 +747,10 @@ def next_applies(sg, torch, inputs, steps=100, warmup=10):
             "workloads": out}
 
 
-# the paper's own apply throughput on its discretisation (Table 2: G unknowns/s
-# on its CPU cluster, by chaos degree) - context beside the GPU figure, not a target
+# the paper's own apply throughput on its discretisation, by chaos degree, on its
+# CPU cluster - context beside the GPU figure, not a target.  The paper prints no
+# rate: each figure is N_SG x vmult calls / accumulated apply seconds, taken from
+# the columns of its solver-performance table (Sec. 6), in G unknowns/s.
 PAPER_TABLE2_GUPS = {0: 1.265, 1: 0.434, 2: 0.286, 3: 0.237}
 
 
@@ -843,6 +886,10 @@ def main():
     ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--no-dw", action="store_true", help="skip the double-word variant")
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
+    ap.add_argument("--profile-variant", choices=["fp64", "dw"], default="fp64",
+                    help="which timed apply loop --profile-range brackets")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the NEXT rows (mixed precision, Monte-Carlo vs SG, adjoint) of the default line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed FP64 applies with cudaProfilerStart/Stop")

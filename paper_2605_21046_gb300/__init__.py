@@ -19,7 +19,7 @@ from . import _abi, coefficients
 SG_PREC_FP64, SG_PREC_DW, SG_PREC_FP32, SG_PREC_BF16 = (_abi.SG_PREC_FP64, _abi.SG_PREC_DW, _abi.SG_PREC_FP32,
                                                       _abi.SG_PREC_BF16)
 
-__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_apply_shape", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_apply_host_async", "sg_get_info",
+__all__ = ["SG_PREC_FP64", "SG_PREC_DW", "SG_PREC_FP32", "SG_PREC_BF16", "sg_mg_setup", "sg_mg_level_info", "sg_mg_set_level_variant", "sg_mg_patch_inverse", "sg_vcycle", "sg_solve_slab", "sg_autotune", "sg_set_apply_shape", "sg_set_exact", "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch", "SGError", "SGContext", "sg_setup", "sg_setup_spec", "sg_apply", "sg_apply_host", "sg_apply_host_async", "sg_get_info",
            "sg_get_multi_indices", "sg_destroy", "sg_status_string", "mesh_spec"]
 
 _KIND = {"one": _abi.SG_F_ONE, "sin": _abi.SG_F_SIN, "pow": _abi.SG_F_POW}
@@ -214,6 +214,30 @@ def _check_vec(ctx, *ts):
 def sg_mg_setup(ctx, mg_precision=SG_PREC_FP64, nu=2, omega=0.7):
     """Build the block-Jacobi multigrid preconditioner (sg_mg_setup)."""
     _check(_abi.load().sg_mg_setup(ctx.handle, int(mg_precision), int(nu), float(omega)), "sg_mg_setup")
+
+
+def sg_mg_level_info(ctx, level):
+    """The choices of the preconditioner on one level (sg_mg_level_info)."""
+    info = (C.c_int * 8)()
+    _check(_abi.load().sg_mg_level_info(ctx.handle, int(level), info), "sg_mg_level_info")
+    keys = ("levels", "cells", "coarsest", "residual", "vanka_chunk", "vanka_tile", "np", "classes")
+    return dict(zip(keys, list(info)))
+
+
+def sg_mg_set_level_variant(ctx, level=-1, residual_kind=-1, vanka_chunk=0, vanka_tile=-1):
+    """Force the residual kind / Vanka chunk / Vanka tile of one smoothed
+    level or of all of them (sg_mg_set_level_variant)."""
+    _check(_abi.load().sg_mg_set_level_variant(ctx.handle, int(level), int(residual_kind), int(vanka_chunk),
+                                               int(vanka_tile)), "sg_mg_set_level_variant")
+
+
+def sg_mg_patch_inverse(ctx, level, alpha, cell):
+    """The stored inverse of one Vanka patch as an (np, np) numpy array."""
+    info = sg_mg_level_info(ctx, level)
+    out = np.zeros((info["np"], info["np"]), dtype=np.float64)
+    _check(_abi.load().sg_mg_patch_inverse(ctx.handle, int(level), int(alpha), int(cell),
+                                           out.ctypes.data_as(C.POINTER(C.c_double))), "sg_mg_patch_inverse")
+    return out
 
 
 def sg_vcycle(ctx, r, z, stream=None):

@@ -17,7 +17,8 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_rhs", "sg_moments", "sg_qoi_errors", "mc_solve_batch",
                    "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient",
                    "sg_stat_errors", "mc_solve_meshes", "sg_set_apply_shape",
-                   "sg_apply_host_async"])
+                   "sg_apply_host_async", "sg_mg_level_info", "sg_mg_set_level_variant",
+                   "sg_mg_patch_inverse"])
 
 
 class sg_mesh(C.Structure):
@@ -85,6 +86,12 @@ def load():
     lib.sg_mg_setup.restype = C.c_int
     lib.sg_vcycle.argtypes = [vp, vp, vp, vp]
     lib.sg_vcycle.restype = C.c_int
+    lib.sg_mg_level_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+    lib.sg_mg_level_info.restype = C.c_int
+    lib.sg_mg_set_level_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.sg_mg_set_level_variant.restype = C.c_int
+    lib.sg_mg_patch_inverse.argtypes = [vp, C.c_int, C.c_int, C.c_longlong, C.POINTER(C.c_double)]
+    lib.sg_mg_patch_inverse.restype = C.c_int
     lib.sg_solve_slab.argtypes = [vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int,
                                   C.POINTER(sg_solve_stats), vp]
     lib.sg_solve_slab.restype = C.c_int

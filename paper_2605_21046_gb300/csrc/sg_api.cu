@@ -367,6 +367,34 @@ sg_status sg_set_coefficient(sg_ctx* ctx, const sg_coeff* coef) {
   return SG_OK;
 }
 
+sg_status sg_mg_level_info(sg_ctx* ctx, int level, int* info) {
+  if (!ctx || !info) return fail(SG_ERR_ARG, "sg_mg_level_info: null argument");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_mg_level_info: call sg_mg_setup first");
+  std::string msg;
+  const sg_status st = sg::mg_level_info(*ctx->mg, level, info, msg);
+  return st == SG_OK ? SG_OK : fail(st, "sg_mg_level_info: " + msg);
+}
+
+sg_status sg_mg_set_level_variant(sg_ctx* ctx, int level, int residual_kind, int vanka_chunk, int vanka_tile) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_mg_set_level_variant: ctx is NULL");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_mg_set_level_variant: call sg_mg_setup first");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sg_mg_set_level_variant: synchronize");
+  std::string msg;
+  const sg_status st = sg::mg_force_variant(*ctx->mg, level, residual_kind, vanka_chunk, vanka_tile, msg);
+  return st == SG_OK ? SG_OK : fail(st, "sg_mg_set_level_variant: " + msg);
+}
+
+sg_status sg_mg_patch_inverse(sg_ctx* ctx, int level, int alpha, long long cell, double* out_host) {
+  if (!ctx || !out_host) return fail(SG_ERR_ARG, "sg_mg_patch_inverse: null argument");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_mg_patch_inverse: call sg_mg_setup first");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "sg_mg_patch_inverse: synchronize");
+  std::string msg;
+  const sg_status st = sg::mg_patch_inverse(*ctx->mg, level, alpha, cell, out_host, msg);
+  return st == SG_OK ? SG_OK : fail(st, "sg_mg_patch_inverse: " + msg);
+}
+
 sg_status sg_vcycle(sg_ctx* ctx, const double* r, double* z, sg_stream stream) {
   if (!ctx) return fail(SG_ERR_ARG, "sg_vcycle: ctx is NULL");
   if (!ctx->mg) return fail(SG_ERR_ARG, "sg_vcycle: call sg_mg_setup first");

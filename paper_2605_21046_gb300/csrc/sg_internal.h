@@ -264,6 +264,23 @@ sg_status mg_build_mc(const HostProblem& fine, int precision, int nu, double ome
                       int ts, MG& mg, std::string& msg);
 size_t krylov_bytes(long long N, int m);
 void mg_free(MG& mg);
+// Per-level choices of a built multigrid: info = {levels, cells, coarsest,
+// residual (0 SG cell kernel, 1 diagonal apply, -1 none), Vanka cells per
+// chunk, Vanka modes per tile, patch size, diagonal classes}.
+sg_status mg_level_info(const MG& mg, int level, int info[8], std::string& msg);
+// Forces the level residual kind (-1 keep, 0 cell kernel, 1 diagonal apply),
+// the Vanka cells per chunk (0 keep) and modes per tile (-1 keep, 0 all) on
+// one smoothed level (or every one with level = -1); drops the captured graphs.
+sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int tile, std::string& msg);
+// The stored inverse of the Vanka patch of (mode alpha's class, cell) on a
+// smoothed level, as np x np doubles (host).
+sg_status mg_patch_inverse(const MG& mg, int level, int alpha, long long cell, double* out, std::string& msg);
+// Vanka patch inverses of one multigrid level, assembled and inverted in FP64
+// on the device (Gauss-Jordan, partial pivoting) for every class and cell:
+// out[class][cell][np][npp] as double (out_kind 0), float (1) or bf16 (2).
+// Synchronous on stream s; singular is set if any patch has no inverse.
+cudaError_t vanka_factor(const HostProblem& hp, const double* d_ctab, const std::vector<std::vector<double>>& class_diag,
+                         int out_kind, void* d_out, int npp, bool& singular, cudaStream_t s);
 // z = P^{-1} r for one slab vector (double in, double out) on a stream; with
 // trans != 0 the V-cycle of the transposed blocks A_alpha^T.
 cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans = 0);

@@ -64,17 +64,27 @@ __global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long
 // (cell, alpha), patch = the cell's nodes x all time nodes (Dirichlet rows
 // skipped), mult = number of cells that hold the node.
 //
-// A CTA takes a chunk of C cells that are consecutive in x and shares their
-// nodes: it gathers r on the chunk's node grid for all V vectors into shared
-// memory (coalesced along x), computes every patch product from there, sums
-// the corrections of neighbouring cells in shared memory, and writes x once:
-// a plain update for nodes that only this chunk holds, an atomic add for the
-// chunk's outer nodes.  One thread owns one patch row rho of one cell for a
-// block of up to VB modes of one diagonal class (modes are pre-sorted into
-// such blocks), so the inverse row is read once per block and the patch
-// values are shared-memory broadcasts.  Inverses are stored [class][cell][NP]
-// [NPP] in W (double, float or bf16; NPP = NP rounded up to 8).
-constexpr int kVankaVB = 8;
+// Per (cell, diagonal class) the step is a dense product Z = inv * R with
+// inv the NP x NP patch inverse and R the patch values of the class's modes
+// (NP x modes).  A CTA takes a chunk of C cells that are consecutive in x:
+//   * it gathers r on the chunk's node grid into shared memory as
+//     [time node][node][slot], slots = the tile's modes grouped by class
+//     (blocks of kVankaVB, zero padded), so that the modes of one node are
+//     contiguous (coalesced along x on the global side);
+//   * per class, it stages the chunk's inverses (contiguous in memory: cells
+//     consecutive in x) into shared memory in the vector precision, rows
+//     padded so that consecutive rows fall in different banks;
+//   * every thread accumulates a register block of kVankaR patch rows x
+//     kVankaU slots: per patch column one broadcast 16-byte load per 4 (FP32)
+//     or 2 (FP64) slots and one inverse value per row, kVankaR * kVankaU FMAs;
+//   * the damped, multiplicity-weighted corrections of neighbouring cells are
+//     summed in shared memory, and x is written once per node: a plain update
+//     for nodes only this chunk holds, an atomic add on its outer nodes.
+// Inverses are stored [class][cell][NP][npp] in W (double, float or bf16;
+// npp = NP rounded up to 8).
+constexpr int kVankaVB = 4;      // slots per mode block (modes of one class)
+constexpr int kVankaU = 8;       // slots per thread
+constexpr int kVankaR = 2;       // patch rows per thread
 
 template <typename T>
 struct VankaParams {
@@ -83,63 +93,89 @@ struct VankaParams {
   const void* inv;
   const int* blk_cls;       // [n_blk] class of every mode block
   const int* blk_alpha;     // [n_blk][kVankaVB] modes, -1 padded
-  int n_blk, n_xi, chunk, npp;
-  int tile_modes, n_tiles;  // modes per tile (single class when n_tiles > 1)
+  int n_blk, chunk, npp;
+  int tile_blocks, n_tiles; // mode blocks per tile
   long long n_x, n_cells;
   int cells[3], nn[3];
   T omega;
 };
 
-template <typename W>
-__device__ __forceinline__ float to_f(W w) { return (float)w; }
+// Row stride (in values) of a staged inverse: NP rounded up to 4 values, an
+// odd multiple of 4 so that 16-byte row loads of 8 consecutive rows use all
+// 32 banks (FP32).
+__host__ __device__ constexpr int vanka_inv_stride(int np) {
+  return ((np + 3) / 4 % 2 == 0) ? (np + 3) / 4 * 4 + 4 : (np + 3) / 4 * 4;
+}
+// Slots per node in shared memory for a tile of `blocks` mode blocks: the
+// blocks plus one thread block of padding (a thread reads kVankaU slots).
+__host__ __device__ constexpr int vanka_slots(int blocks) { return blocks * kVankaVB + kVankaU; }
+
+template <typename T>
+struct Vec16;
 template <>
-__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
+struct Vec16<float> {
+  static constexpr int n = 4;
+  __device__ static void load(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct Vec16<double> {
+  static constexpr int n = 2;
+  __device__ static void load(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
 
 template <typename T, typename W>
-__device__ __forceinline__ T conv(W w) { return (T)w; }
+__device__ __forceinline__ T widen(W w) { return (T)w; }
 template <>
-__device__ __forceinline__ float conv<float, __nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
-
-template <typename T, typename W>
-__device__ __forceinline__ T wval(const W* p) { return (T)to_f<W>(*p); }
-template <>
-__device__ __forceinline__ double wval<double, double>(const double* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float wval<float, float>(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
 
 template <typename T, typename W, int DIM, int K, int NT, bool TRANS>
 __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
   constexpr int N = K + 1;
   constexpr int NKD = DIM == 2 ? N * N : N * N * N;
   constexpr int NP = NT * NKD;
-  constexpr int VB = kVankaVB;
+  constexpr int NPH = (NP + kVankaR - 1) / kVankaR;   // row groups per cell
+  constexpr int IS = vanka_inv_stride(NP);
+  constexpr int VB = kVankaVB, U = kVankaU, R = kVankaR;
+  constexpr int VN = Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int VTM = p.tile_modes * NT, C = p.chunk;
-  const int LX = C * K + 1;                         // chunk nodes along x
-  constexpr int LYZ = DIM == 2 ? N : N * N;         // nodes across y (and z)
+  const int C = p.chunk;
+  const int LX = C * K + 1;                          // chunk nodes along x
+  constexpr int LYZ = DIM == 2 ? N : N * N;          // nodes across y (and z)
   const int LN = LX * LYZ;
-  T* Rl = reinterpret_cast<T*>(smem_raw);           // [tile vectors][LN]
-  T* Zc = Rl + (size_t)VTM * LN;                    // [tile vectors][LN]
-  int* Gn = reinterpret_cast<int*>(Zc + (size_t)VTM * LN);   // [LN] global node, -1 outside / on the boundary
-  int* Gp = Gn + LN;                                         // [LN] 1 for nodes no other chunk touches
+  const int SL = vanka_slots(p.tile_blocks);
+  T* Rl = reinterpret_cast<T*>(smem_raw);            // [NT][LN][SL]
+  T* Zc = Rl + (size_t)NT * LN * SL;                 // [NT][LN][SL]
+  T* Is = Zc + (size_t)NT * LN * SL;                 // [C][NP][IS] inverses of one class
+  int* Gn = reinterpret_cast<int*>(Is + (size_t)C * NP * IS);   // [LN] global node, -1 outside / boundary
+  int* Gp = Gn + LN;                                 // [LN] 1 for nodes no other chunk touches
+  int* Sm = Gp + LN;                                 // [SL] mode of every slot, -1 padding
+  int* Qo = Sm + SL;                                 // [NP] offset of patch column q in Rl (first cell)
+  for (int q = tid; q < NP; q += nthr) {
+    const int iq = q / NKD, aq = q - iq * NKD;
+    const int ln = aq % N + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
+    Qo[q] = (iq * LN + ln) * SL;
+  }
   const W* inv = static_cast<const W*>(p.inv);
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
-  const int cpr = (p.cells[0] + C - 1) / C;         // chunks per row of cells
+  const int cpr = (p.cells[0] + C - 1) / C;          // chunks per row of cells
   const long long n_chunks = (long long)cpr * p.cells[1] * p.cells[2];
   for (long long unit = blockIdx.x; unit < n_chunks * p.n_tiles; unit += gridDim.x) {
     const long long ch = unit % n_chunks;
     const int tile = (int)(unit / n_chunks);
-    const int m0 = tile * p.tile_modes, tm = min(p.tile_modes, p.n_xi - m0);
-    const int V = tm * NT;                          // this tile's vectors, from m0 * NT on
-    const int nb = p.n_tiles == 1 ? p.n_blk : (tm + VB - 1) / VB;
-    const int b0 = p.n_tiles == 1 ? 0 : m0 / VB;
-    const long long voff = (long long)m0 * NT;
+    const int b0 = tile * p.tile_blocks, nb = min(p.tile_blocks, p.n_blk - b0);
     const int cx0 = (int)(ch % cpr) * C;
     const long long row = ch / cpr;
     const int cy = (int)(row % p.cells[1]), cz = (int)(row / p.cells[1]);
     const int nc = min(C, p.cells[0] - cx0);
     const int lxn = nc * K + 1;
+    const long long cell0 = ((long long)cz * p.cells[1] + cy) * p.cells[0] + cx0;
     __syncthreads();
     // the chunk's nodes: global index (or -1) and whether only this chunk touches them
     for (int ln = tid; ln < LN; ln += nthr) {
@@ -156,90 +192,126 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
       Gn[ln] = node;
       Gp[ln] = priv;
     }
+    for (int sl = tid; sl < SL; sl += nthr) Sm[sl] = sl < nb * VB ? p.blk_alpha[b0 * VB + sl] : -1;
     __syncthreads();
-    // gather r on the chunk's node grid; clear the corrections
-    for (int idx = tid; idx < V * LN; idx += nthr) {
-      const int v = idx / LN, node = Gn[idx - v * LN];
-      Rl[idx] = node >= 0 ? p.r[(voff + v) * p.n_x + node] : T(0);
-      Zc[idx] = T(0);
+    // gather r on the chunk's node grid (slot-major, node fastest); clear the corrections
+    for (int idx = tid; idx < SL * NT * LN; idx += nthr) {
+      const int sl = idx / (NT * LN), rem = idx - sl * (NT * LN);
+      const int i = rem / LN, ln = rem - i * LN;
+      const int mode = Sm[sl], node = Gn[ln];
+      const size_t at = (size_t)(i * LN + ln) * SL + sl;
+      Rl[at] = mode >= 0 && node >= 0 ? p.r[((long long)mode * NT + i) * p.n_x + node] : T(0);
+      Zc[at] = T(0);
     }
-    __syncthreads();
-    // patch rows
-    const int items = nc * NP * nb;
-    for (int it = tid; it < items; it += nthr) {
-      const int rho = it % NP;
-      const int cb = it / NP;
-      const int c = cb % nc, b = b0 + cb / nc;
-      const int i = rho / NKD, a = rho - i * NKD;
-      const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
-      const int lbase = c * K;                       // local x of the cell's first node
-      const int lna = (lbase + ax) + LX * (ay + (DIM == 3 ? N * az : 0));
-      if (Gn[lna] < 0) continue;                     // Dirichlet row
-      const long long cell = ((long long)cz * p.cells[1] + cy) * p.cells[0] + cx0 + c;
-      const W* M = inv + ((long long)p.blk_cls[b] * p.n_cells + cell) * NP * p.npp;
-      int al[VB];
-#pragma unroll
-      for (int u = 0; u < VB; ++u) al[u] = p.blk_alpha[b * VB + u] < 0 ? -1 : p.blk_alpha[b * VB + u] - m0;
-      T acc[VB];
-#pragma unroll
-      for (int u = 0; u < VB; ++u) acc[u] = T(0);
-      if constexpr (TRANS) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          const int iq = q / NKD, aq = q - iq * NKD;
-          const int ln = (lbase + aq % N) + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
-          const T w = wval<T, W>(M + (size_t)q * p.npp + rho);
-          const T* rq = Rl + (size_t)iq * LN + ln;
-#pragma unroll
-          for (int u = 0; u < VB; ++u)
-            if (al[u] >= 0) acc[u] += w * rq[(size_t)al[u] * NT * LN];
-        }
-      } else {
-        // the row in 16-byte pieces (rows are padded to a multiple of 8 values)
+    // runs of consecutive blocks of one class
+    for (int rb = 0; rb < nb;) {
+      const int cls = p.blk_cls[b0 + rb];
+      int re = rb + 1;
+      while (re < nb && p.blk_cls[b0 + re] == cls) ++re;
+      const int sa = rb * VB, se = re * VB;
+      rb = re;
+      __syncthreads();
+      // the chunk's inverses of this class, widened to T
+      {
         constexpr int QV = 16 / (int)sizeof(W);
-        const uint4* mrow = reinterpret_cast<const uint4*>(M + (size_t)rho * p.npp);
-#pragma unroll
-        for (int q0 = 0; q0 < NP; q0 += QV) {
-          const uint4 raw = __ldg(mrow + q0 / QV);
+        const uint4* src = reinterpret_cast<const uint4*>(inv + ((long long)cls * p.n_cells + cell0) * NP * p.npp);
+        const int per_row = p.npp / QV;
+        const int keep = min(p.npp, IS);
+        for (int idx = tid; idx < nc * NP * per_row; idx += nthr) {
+          const int rr = idx / per_row, piece = idx - rr * per_row;
+          const uint4 raw = __ldg(src + idx);
           const W* wv = reinterpret_cast<const W*>(&raw);
+          T* dst = Is + (size_t)rr * IS + piece * QV;
 #pragma unroll
-          for (int k = 0; k < QV; ++k) {
-            const int q = q0 + k;
-            if (q >= NP) break;
-            const int iq = q / NKD, aq = q - iq * NKD;
-            const int ln = (lbase + aq % N) + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
-            const T w = conv<T, W>(wv[k]);
-            const T* rq = Rl + (size_t)iq * LN + ln;
-#pragma unroll
-            for (int u = 0; u < VB; ++u)
-              if (al[u] >= 0) acc[u] += w * rq[(size_t)al[u] * NT * LN];
-          }
+          for (int k = 0; k < QV; ++k)
+            if (piece * QV + k < keep) dst[k] = widen<T, W>(wv[k]);
         }
       }
-      // patches sharing the node (cell corners and faces: the local coordinate is 0 or K)
-      const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
-      const T sc = p.omega / T(mult);
+      __syncthreads();
+      const int ng = (se - sa + U - 1) / U;
+      const int items = nc * ng * NPH;
+      for (int it = tid; it < items; it += nthr) {
+        const int rp = it % NPH, cg = it / NPH;
+        const int g = cg % ng, c = cg / ng;
+        const int s0 = sa + g * U;
+        int rows[R];
 #pragma unroll
-      for (int u = 0; u < VB; ++u)
-        if (al[u] >= 0) atomicAdd(&Zc[(size_t)(al[u] * NT + i) * LN + lna], sc * acc[u]);
+        for (int k = 0; k < R; ++k) rows[k] = rp + k * NPH;
+        T acc[R][U];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+          for (int u = 0; u < U; ++u) acc[k][u] = T(0);
+        const T* rbase = Rl + (size_t)c * K * SL + s0;
+        const T* ibase = Is + (size_t)c * NP * IS;
+        if constexpr (!TRANS) {
+          const T* ir[R];
+#pragma unroll
+          for (int k = 0; k < R; ++k) ir[k] = ibase + (size_t)min(rows[k], NP - 1) * IS;
+#pragma unroll
+          for (int q0 = 0; q0 < NP; q0 += VN) {
+            T w[R][VN];
+#pragma unroll
+            for (int k = 0; k < R; ++k) Vec16<T>::load(ir[k] + q0, w[k]);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) {
+              if (q0 + j >= NP) break;
+              const T* pv = rbase + Qo[q0 + j];
+              T v[U];
+#pragma unroll
+              for (int u = 0; u < U; u += VN) Vec16<T>::load(pv + u, v + u);
+#pragma unroll
+              for (int k = 0; k < R; ++k)
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[k][u] = fma(w[k][j], v[u], acc[k][u]);
+            }
+          }
+        } else {
+#pragma unroll 6
+          for (int q = 0; q < NP; ++q) {
+            const T* pv = rbase + Qo[q];
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; u += VN) Vec16<T>::load(pv + u, v + u);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+              const T w = ibase[(size_t)q * IS + min(rows[k], NP - 1)];
+#pragma unroll
+              for (int u = 0; u < U; ++u) acc[k][u] = fma(w, v[u], acc[k][u]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const int rho = rows[k];
+          if (rho >= NP) continue;
+          const int i = rho / NKD, a = rho - i * NKD;
+          const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
+          const int lna = c * K + ax + LX * (ay + (DIM == 3 ? N * az : 0));
+          if (Gn[lna] < 0) continue;                 // Dirichlet row
+          // patches sharing the node (cell corners and faces: the local coordinate is 0 or K)
+          const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
+          const T sc = p.omega / T(mult);
+          T* z = Zc + (size_t)(i * LN + lna) * SL + s0;
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (s0 + u < se) atomicAdd(z + u, sc * acc[k][u]);
+        }
+      }
     }
     __syncthreads();
     // write x: chunk-private nodes directly, shared outer nodes atomically
-    for (int idx = tid; idx < V * LN; idx += nthr) {
-      const int v = idx / LN, ln = idx - v * LN;
-      const int node = Gn[ln];
-      if (node < 0) continue;
-      const T val = Zc[idx];
-      T* dst = p.x + (voff + v) * p.n_x + node;
+    for (int idx = tid; idx < nb * VB * NT * LN; idx += nthr) {
+      const int sl = idx / (NT * LN), rem = idx - sl * (NT * LN);
+      const int i = rem / LN, ln = rem - i * LN;
+      const int mode = Sm[sl], node = Gn[ln];
+      if (mode < 0 || node < 0) continue;
+      const T val = Zc[(size_t)(i * LN + ln) * SL + sl];
+      T* dst = p.x + ((long long)mode * NT + i) * p.n_x + node;
       if (Gp[ln]) *dst += val;
       else atomicAdd(dst, val);
     }
   }
-}
-
-__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = __float2bfloat16_rn(a[i]);
 }
 
 // x_fine += P e_coarse: gather over the (k+1)^d nodes of the coarse cell that
@@ -465,76 +537,6 @@ bool node_interior(const HostProblem& hp, const int g[3]) {
 // rows for bf16, float and double).
 int vanka_row_pitch(int np) { return (np + 7) / 8 * 8; }
 
-// Vanka patch inverses of one level and class: [cell][np][pitch].
-bool patch_inverses(const HostProblem& hp, const ElementData& e, const std::vector<double>& diag,
-                    std::vector<double>& out) {
-  const int n = hp.k + 1, nkd = e.nkd, nt = hp.n_t, np = nt * nkd, npp = vanka_row_pitch(np);
-  std::vector<std::vector<double>> Kc(hp.n_cells);
-  for (long long c = 0; c < hp.n_cells; ++c) element_stiffness(hp, e, diag, c, Kc[c]);
-  out.assign((size_t)hp.n_cells * np * npp, 0.0);
-  bool ok = true;
-#pragma omp parallel for schedule(dynamic, 64) reduction(&& : ok)
-  for (long long c = 0; c < hp.n_cells; ++c) {
-    int cc[3];
-    cell_coords(hp, c, cc);
-    std::vector<double> Mg((size_t)nkd * nkd, 0.0), Kg((size_t)nkd * nkd, 0.0);
-    int gi[64][3];
-    for (int a = 0; a < nkd; ++a) {
-      const int ai[3] = {a % n, (a / n) % n, a / (n * n)};
-      for (int d = 0; d < 3; ++d) gi[a][d] = d < hp.dim ? cc[d] * hp.k + ai[d] : 0;
-    }
-    const int span = hp.dim == 3 ? 1 : 0;
-    for (int oz = -span; oz <= span; ++oz)
-      for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-          const int nc[3] = {cc[0] + ox, cc[1] + oy, cc[2] + oz};
-          bool valid = true;
-          for (int d = 0; d < hp.dim; ++d) valid = valid && nc[d] >= 0 && nc[d] < hp.cells[d];
-          if (!valid) continue;
-          const long long cn = ((long long)nc[2] * hp.cells[1] + nc[1]) * hp.cells[0] + nc[0];
-          int loc[64];
-          for (int a = 0; a < nkd; ++a) {
-            loc[a] = -1;
-            int l = 0, stride = 1;
-            bool in = true;
-            for (int d = 0; d < hp.dim; ++d) {
-              const int off = gi[a][d] - nc[d] * hp.k;
-              if (off < 0 || off > hp.k) { in = false; break; }
-              l += off * stride;
-              stride *= n;
-            }
-            if (in) loc[a] = l;
-          }
-          for (int a = 0; a < nkd; ++a) {
-            if (loc[a] < 0) continue;
-            for (int b = 0; b < nkd; ++b) {
-              if (loc[b] < 0) continue;
-              Mg[(size_t)a * nkd + b] += e.mass[(size_t)loc[a] * nkd + loc[b]];
-              Kg[(size_t)a * nkd + b] += Kc[cn][(size_t)loc[a] * nkd + loc[b]];
-            }
-          }
-        }
-    std::vector<double> P((size_t)np * np, 0.0);
-    for (int i = 0; i < nt; ++i)
-      for (int a = 0; a < nkd; ++a) {
-        const int row = i * nkd + a;
-        if (!node_interior(hp, gi[a])) { P[(size_t)row * np + row] = 1.0; continue; }
-        for (int j = 0; j < nt; ++j)
-          for (int b = 0; b < nkd; ++b) {
-            if (!node_interior(hp, gi[b])) continue;
-            double v = hp.A_hat[i * nt + j] * Mg[(size_t)a * nkd + b];
-            if (i == j) v += hp.tau * hp.B_hat[i * nt + i] * Kg[(size_t)a * nkd + b];
-            P[(size_t)row * np + j * nkd + b] = v;
-          }
-      }
-    if (!invert(P, np)) ok = false;
-    for (int row = 0; row < np; ++row)
-      std::copy(P.begin() + (size_t)row * np, P.begin() + (size_t)(row + 1) * np,
-                out.begin() + ((size_t)c * np + row) * npp);
-  }
-  return ok;
-}
-
 // Coarsest level: dense inverse of the interior block of one class.
 bool coarse_inverse(const HostProblem& hp, const ElementData& e, const std::vector<double>& diag,
                     const std::vector<long long>& node_of, std::vector<double>& out) {
@@ -626,23 +628,6 @@ cudaError_t upload_values(void** dst, const std::vector<double>& src, int precis
     return upload_vec(reinterpret_cast<float**>(dst), f);
   }
   return upload_vec(reinterpret_cast<double**>(dst), src);
-}
-
-// bf16 copy of src (rounded to float, then to the nearest bf16 on the device).
-cudaError_t upload_bf16(void** dst, const std::vector<double>& src) {
-  float* tmp = nullptr;
-  std::vector<float> f(src.begin(), src.end());
-  cudaError_t e = upload_vec(&tmp, f);
-  if (e == cudaSuccess) e = cudaMalloc(dst, std::max<size_t>(1, f.size()) * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) {
-    const long long n = (long long)f.size();
-    k_to_bf16<<<(int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096)), 256>>>(
-        tmp, static_cast<__nv_bfloat16*>(*dst), n);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  }
-  cudaFree(tmp);
-  return e;
 }
 
 // The diagonal (block-Jacobi) coupling table: row alpha keeps its own column.
@@ -766,19 +751,24 @@ sg_status level_diag_shape(MGLevel& L, int ts, int max_chunk, int vb) {
   return SG_OK;
 }
 
-// Cells per Vanka chunk: up to 8, within the shared-memory budget.
-size_t vanka_smem(const MGLevel& L, int tile_modes, int chunk, size_t value_bytes) {
+// Shared memory of a Vanka chunk: r and the corrections of the tile's slots,
+// the staged inverses of one class, then the nodes' global indices and
+// private flags, the slot modes and the patch-column offsets.
+size_t vanka_smem(const MGLevel& L, int n_blk, int tile_slots, int chunk, size_t value_bytes) {
   const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
   const size_t ln = (size_t)(chunk * L.hp.k + 1) * lyz;   // nodes of a chunk
-  // r and the corrections for every vector of the tile, then the nodes' global
-  // indices and private flags
-  return 2 * (size_t)tile_modes * L.hp.n_t * ln * value_bytes + 2 * ln * sizeof(int);
+  const int blocks = std::min(n_blk, std::max(1, tile_slots / kVankaVB));
+  const size_t sl = (size_t)vanka_slots(blocks);
+  const size_t is = (size_t)vanka_inv_stride(L.np);
+  return (2 * (size_t)L.hp.n_t * ln * sl + (size_t)chunk * L.np * is) * value_bytes +
+         (2 * ln + sl + (size_t)L.np) * sizeof(int);
 }
 
-int vanka_chunk(const MGLevel& L, int tile_modes, size_t value_bytes, size_t budget) {
+// Cells per Vanka chunk: up to 8, within the shared-memory budget.
+int vanka_chunk(const MGLevel& L, int n_blk, int tile_slots, size_t value_bytes, size_t budget) {
   int best = 0;
   for (int c = 1; c <= std::min(8, L.hp.cells[0]); ++c)
-    if (vanka_smem(L, tile_modes, c, value_bytes) <= budget) best = c;
+    if (vanka_smem(L, n_blk, tile_slots, c, value_bytes) <= budget) best = c;
   return best;
 }
 
@@ -791,11 +781,10 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   p.blk_cls = mg.d_blk_cls;
   p.blk_alpha = mg.d_blk_alpha;
   p.n_blk = mg.n_blk;
-  p.n_xi = L.hp.n_xi;
   const int tile = L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile;
   p.chunk = L.vanka_chunk;
-  p.tile_modes = tile;
-  p.n_tiles = (L.hp.n_xi + tile - 1) / tile;
+  p.tile_blocks = std::min(mg.n_blk, std::max(1, tile / kVankaVB));
+  p.n_tiles = (mg.n_blk + p.tile_blocks - 1) / p.tile_blocks;
   p.npp = vanka_row_pitch(L.np);
   p.n_x = L.hp.n_x;
   p.n_cells = L.hp.n_cells;
@@ -804,7 +793,7 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
     p.nn[d] = L.hp.nn[d];
   }
   p.omega = T(mg.omega);
-  const size_t smem = vanka_smem(L, tile, L.vanka_chunk, sizeof(T));
+  const size_t smem = vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, sizeof(T));
   const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
   const long long units = (long long)cpr * L.hp.cells[1] * L.hp.cells[2] * p.n_tiles;
   const int grid = (int)std::min<long long>(units, sg::sm_count() * 8);
@@ -1053,16 +1042,17 @@ static cudaError_t tune_vanka(MG& mg) {
     if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
     std::vector<int> tiles = {mg.vanka_tile};
     // smaller tiles only where one-cell chunks of whole tiles leave the GPU short of CTAs
-    const long long units1 = (long long)L.hp.n_cells * ((L.hp.n_xi + mg.vanka_tile - 1) / mg.vanka_tile);
-    if (mg.n_classes == 1 && units1 < sg::sm_count() * 16)
+    const long long units1 = (long long)L.hp.n_cells * ((mg.n_blk * kVankaVB + mg.vanka_tile - 1) / mg.vanka_tile);
+    if (units1 < sg::sm_count() * 16)
       for (int t : {16, 8})
         if (t < mg.vanka_tile && t % kVankaVB == 0) tiles.push_back(t);
     int best_c = L.vanka_chunk, best_t = 0;
     float best_ms = 1e30f;
     for (int tile : tiles) {
-      const int max_c = vanka_chunk(L, tile, vb, tile == mg.vanka_tile ? std::max<size_t>(100 * 1024,
-                                                                                         vanka_smem(L, tile, L.vanka_chunk, vb))
-                                                                       : 100 * 1024);
+      const int max_c = vanka_chunk(L, mg.n_blk, tile, vb,
+                                    tile == mg.vanka_tile
+                                        ? std::max<size_t>(100 * 1024, vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, vb))
+                                        : 100 * 1024);
       if (max_c == 0) continue;
       std::vector<int> cand;
       for (int c = 1; c <= max_c; c *= 2) cand.push_back(c);
@@ -1162,7 +1152,9 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     }
   }
   mg.n_blk = (int)blk_cls.size();
-  if (mg.vanka_tile <= 0 || !single_class) mg.vanka_tile = fine.n_xi;
+  // slots per Vanka tile: every block, or (Monte-Carlo batches) the requested
+  // number of samples
+  if (mg.vanka_tile <= 0 || !mg.mc || mg.vanka_tile > mg.n_blk * kVankaVB) mg.vanka_tile = mg.n_blk * kVankaVB;
   // level problems
   std::vector<HostProblem> hps;
   hps.push_back(fine);
@@ -1228,9 +1220,9 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     const int n = L.hp.k + 1;
     const int nkd = L.hp.dim == 2 ? n * n : n * n * n;
     L.np = L.hp.n_t * nkd;
-    const ElementData ed = element_data(L.hp);
-    std::vector<double> inv;
     if (L.coarsest) {
+      const ElementData ed = element_data(L.hp);
+      std::vector<double> inv;
       std::vector<long long> node_of;
       for (long long m = 0; m < L.hp.n_x; ++m) {
         const int g[3] = {(int)(m % L.hp.nn[0]), (int)((m / L.hp.nn[0]) % L.hp.nn[1]),
@@ -1251,31 +1243,36 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
         inv.insert(inv.end(), ci.begin(), ci.end());
       }
       if ((e = upload_vec(reinterpret_cast<long long**>(&L.d_inner), inner_dofs)) != cudaSuccess) break;
-    } else {
-      for (int c = 0; c < mg.n_classes; ++c) {
-        std::vector<double> pi;
-        if (!patch_inverses(L.hp, ed, class_diag[c], pi)) { msg = "singular Vanka patch"; return SG_ERR_ARG; }
-        inv.insert(inv.end(), pi.begin(), pi.end());
-      }
+      if ((e = upload_values(&L.d_inv, inv, precision)) != cudaSuccess) break;
     }
-    if (!L.coarsest && mg.bf16) e = upload_bf16(&L.d_inv, inv);
-    else e = upload_values(&L.d_inv, inv, precision);
-    if (e != cudaSuccess) break;
+    // level apply tables (coefficient stays double; vectors use the MG precision)
+    if ((e = upload_vec(reinterpret_cast<double**>(&L.d_ctab), L.hp.ctab)) != cudaSuccess) break;
     if (!L.coarsest) {
+      // Vanka patch inverses, assembled and factored on the device
+      const int npp = vanka_row_pitch(L.np);
+      const int kind = mg.bf16 ? 2 : precision == kPrecF32 ? 1 : 0;
+      const size_t wb = kind == 2 ? sizeof(__nv_bfloat16) : kind == 1 ? sizeof(float) : sizeof(double);
+      if ((e = cudaMalloc(&L.d_inv, (size_t)mg.n_classes * L.hp.n_cells * L.np * npp * wb)) != cudaSuccess) break;
+      bool singular = false;
+      if ((e = vanka_factor(L.hp, static_cast<const double*>(L.d_ctab), class_diag, kind, L.d_inv, npp, singular,
+                            0)) != cudaSuccess)
+        break;
+      if (singular) {
+        msg = "singular Vanka patch";
+        return SG_ERR_ARG;
+      }
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       const size_t vb = precision == kPrecF32 ? 4 : 8;
-      L.vanka_chunk = vanka_chunk(L, mg.vanka_tile, vb, 100 * 1024);
-      if (L.vanka_chunk == 0) L.vanka_chunk = vanka_chunk(L, mg.vanka_tile, vb, (size_t)optin - 1024);
+      L.vanka_chunk = vanka_chunk(L, mg.n_blk, mg.vanka_tile, vb, 100 * 1024);
+      if (L.vanka_chunk == 0) L.vanka_chunk = vanka_chunk(L, mg.n_blk, mg.vanka_tile, vb, (size_t)optin - 1024);
       if (L.vanka_chunk == 0) {
         msg = "Vanka smoother: one cell with all rows does not fit in shared memory (fewer samples per batch)";
         return SG_ERR_UNSUPPORTED;
       }
       if ((e = prepare_vanka(L.hp.dim, L.hp.k, L.hp.n_t, precision == kPrecF32, mg.bf16)) != cudaSuccess) break;
     }
-    // level apply tables (coefficient stays double; vectors use the MG precision)
-    if ((e = upload_vec(reinterpret_cast<double**>(&L.d_ctab), L.hp.ctab)) != cudaSuccess) break;
     if ((e = upload_vec(&L.d_grow, L.hp.g.row)) != cudaSuccess) break;
     if ((e = upload_vec(&L.d_gcol, L.hp.g.col)) != cudaSuccess) break;
     if ((e = upload_vec(&L.d_gterm, L.hp.g.term)) != cudaSuccess) break;
@@ -1348,6 +1345,116 @@ sg_status mg_build_mc(const HostProblem& fine, int precision, int nu, double ome
     return SG_ERR_CUDA;
   }
   return mg_build(fine, precision, nu, omega, mg, msg, true);
+}
+
+sg_status mg_level_info(const MG& mg, int level, int info[8], std::string& msg) {
+  if (level < 0 || level >= (int)mg.lv.size()) {
+    msg = "level out of range";
+    return SG_ERR_ARG;
+  }
+  const MGLevel& L = mg.lv[level];
+  info[0] = (int)mg.lv.size();
+  info[1] = (int)L.hp.n_cells;
+  info[2] = L.coarsest ? 1 : 0;
+  info[3] = L.coarsest ? -1 : (L.use_diag ? 1 : 0);
+  info[4] = L.coarsest ? 0 : L.vanka_chunk;
+  info[5] = L.coarsest ? 0 : (L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile);
+  info[6] = L.np;
+  info[7] = mg.n_classes;
+  return SG_OK;
+}
+
+sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int tile, std::string& msg) {
+  if (level < -1 || level >= (int)mg.lv.size()) {
+    msg = "level out of range";
+    return SG_ERR_ARG;
+  }
+  if (residual_kind < -1 || residual_kind > 1 || chunk < 0 || chunk > 8 || tile < -1) {
+    msg = "variant out of range";
+    return SG_ERR_ARG;
+  }
+  const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // check every level first, then change them
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int l = 0; l < (int)mg.lv.size(); ++l) {
+      if (level >= 0 && l != level) continue;
+      MGLevel& L = mg.lv[l];
+      if (L.coarsest) {
+        if (level >= 0) {
+          msg = "the coarsest level has no smoother";
+          return SG_ERR_ARG;
+        }
+        continue;
+      }
+      if (residual_kind == 0 && !L.chunk_ok) {
+        msg = "the SG cell kernel has no launch shape on this level";
+        return SG_ERR_UNSUPPORTED;
+      }
+      const int t = tile < 0 ? (L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile) : (tile == 0 ? mg.vanka_tile : tile);
+      if (t != mg.vanka_tile && (t % kVankaVB != 0 || t > mg.vanka_tile)) {
+        msg = "mode tiles are multiples of 4 slots, at most all of them";
+        return SG_ERR_ARG;
+      }
+      const int c = chunk > 0 ? std::min(chunk, L.hp.cells[0]) : L.vanka_chunk;
+      if (vanka_smem(L, mg.n_blk, t, c, vb) > (size_t)optin - 1024) {
+        msg = "Vanka chunk does not fit in shared memory";
+        return SG_ERR_UNSUPPORTED;
+      }
+      if (pass == 1) {
+        if (residual_kind >= 0) L.use_diag = residual_kind == 1;
+        L.vanka_chunk = c;
+        L.vanka_tile = t == mg.vanka_tile ? 0 : t;
+      }
+    }
+  }
+  // the captured V-cycles hold the old launches
+  for (int t = 0; t < 2; ++t) {
+    if (mg.exec_t[t]) cudaGraphExecDestroy(mg.exec_t[t]);
+    if (mg.graph_t[t]) cudaGraphDestroy(mg.graph_t[t]);
+    mg.exec_t[t] = nullptr;
+    mg.graph_t[t] = nullptr;
+  }
+  return SG_OK;
+}
+
+sg_status mg_patch_inverse(const MG& mg, int level, int alpha, long long cell, double* out, std::string& msg) {
+  if (level < 0 || level >= (int)mg.lv.size() || mg.lv[level].coarsest) {
+    msg = "level out of range (or the coarsest level)";
+    return SG_ERR_ARG;
+  }
+  const MGLevel& L = mg.lv[level];
+  if (alpha < 0 || alpha >= (int)mg.cls.size() || cell < 0 || cell >= L.hp.n_cells) {
+    msg = "mode or cell out of range";
+    return SG_ERR_ARG;
+  }
+  const int np = L.np, npp = vanka_row_pitch(np);
+  const size_t off = ((size_t)mg.cls[alpha] * L.hp.n_cells + (size_t)cell) * np * npp;
+  const size_t cnt = (size_t)np * npp;
+  std::vector<double> row(cnt);
+  cudaError_t e;
+  if (mg.bf16) {
+    std::vector<__nv_bfloat16> v(cnt);
+    e = cudaMemcpy(v.data(), static_cast<const __nv_bfloat16*>(L.d_inv) + off, cnt * sizeof(__nv_bfloat16),
+                   cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < cnt; ++i) row[i] = (double)__bfloat162float(v[i]);
+  } else if (mg.precision == kPrecF32) {
+    std::vector<float> v(cnt);
+    e = cudaMemcpy(v.data(), static_cast<const float*>(L.d_inv) + off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    for (size_t i = 0; i < cnt; ++i) row[i] = v[i];
+  } else {
+    e = cudaMemcpy(row.data(), static_cast<const double*>(L.d_inv) + off, cnt * sizeof(double),
+                   cudaMemcpyDeviceToHost);
+  }
+  if (e != cudaSuccess) {
+    msg = cudaGetErrorString(e);
+    return SG_ERR_CUDA;
+  }
+  for (int r = 0; r < np; ++r)
+    for (int c = 0; c < np; ++c) out[(size_t)r * np + c] = row[(size_t)r * npp + c];
+  return SG_OK;
 }
 
 cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans) {

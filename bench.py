@@ -561,6 +561,7 @@ def next_mixed_precision(sg, torch, inputs):
         t0 = time.perf_counter()
         sg.sg_mg_setup(ctx, mp, MG_NU, MG_OMEGA)
         setup_ms = 1e3 * (time.perf_counter() - t0)
+        setup_split = sg.sg_mg_setup_times(ctx)
         march(sg, torch, ctx, 1e-8, slabs=1)                     # warm-up: graphs, workspaces
         u, ms, its = march(sg, torch, ctx, 1e-8)
         err = sg.sg_qoi_errors(ctx, u, spec["n_slabs"] - 1)
@@ -568,6 +569,7 @@ def next_mixed_precision(sg, torch, inputs):
             ref = u.clone()
         diff = float((u - ref).abs().max() / ref.abs().max())
         out[name] = {"march_ms": ms, "ms_per_slab": ms / spec["n_slabs"], "mg_setup_ms": setup_ms,
+                     "mg_setup_split_ms": setup_split, "march_plus_setup_ms": ms + setup_ms,
                      "iterations_mean": sum(its) / len(its), "iterations_max": max(its),
                      "max_rel_diff_vs_fp64": diff,
                      "qoi_errors_T": err}
@@ -576,6 +578,7 @@ def next_mixed_precision(sg, torch, inputs):
         torch.cuda.empty_cache()
     for k in out:
         out[k]["time_ratio_vs_fp64"] = out[k]["march_ms"] / out["fp64"]["march_ms"]
+        out[k]["time_ratio_vs_fp64_with_setup"] = out[k]["march_plus_setup_ms"] / out["fp64"]["march_plus_setup_ms"]
     return {"row": "mixed precision", "workload": spec["name"], "unknowns_per_slab": inputs.n_unknowns(spec),
             "slabs": spec["n_slabs"], "rtol": 1e-8, "exact": "finite chaos q=2, eta=0.35, T(t)=t+t^2",
             "splits": out}

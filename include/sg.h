@@ -248,6 +248,12 @@ sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega);
  * level out of range. */
 sg_status sg_mg_level_info(sg_ctx* ctx, int level, int* info);
 
+/* sg_mg_setup_times - wall times (HOST doubles out, ms) of the last
+ * sg_mg_setup: the whole set-up, the device factorisation of the Vanka
+ * patches (every level) and the timing of the level variants (the launch
+ * shapes set-up picks).  SG_ERR_ARG without sg_mg_setup. */
+sg_status sg_mg_setup_times(sg_ctx* ctx, double* total_ms, double* factor_ms, double* tune_ms);
+
 /* sg_mg_set_level_variant - replace set-up's timed choices on one smoothed
  * level (level >= 0) or on all of them (level = -1): residual_kind -1 keeps,
  * 0 forces the SG cell kernel, 1 the diagonal apply; vanka_chunk 0 keeps, else
@@ -359,6 +365,26 @@ sg_status sg_adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int checkpoi
  * stream, and returns once y is on the host. */
 sg_status sg_apply_host_static(sg_ctx* ctx, int slab, const double* x_host, double* y_host,
                                int transpose);
+
+/* sg_debug_bounds - the device bounds records of the debug build.  The
+ * library built with -DSG_DEBUG_BOUNDS (libsg_debug.so) tests the index of
+ * every instrumented global and shared-memory access of the apply, Monte-Carlo
+ * apply, Vanka, patch-factorisation and grid-transfer kernels against the
+ * extent of its array; an index outside it is skipped (never accessed), the
+ * first one is recorded and all are counted.  Nothing traps.  Out (HOST):
+ * enabled = 1 in that build (0 in the release build, where everything else
+ * is 0 and no device call is made), count = violations since the last call,
+ * site / index / limit of the first one.  Reading clears the records.
+ * Synchronizes the device (debug build).  The paper has no counterpart. */
+sg_status sg_debug_bounds(int* enabled, unsigned int* count, int* site, long long* index, long long* limit);
+
+/* sg_debug_bounds_probe - self-test of the record path: one thread writes
+ * element `index` of a 16-element device array if the bounds check against
+ * `limit` (1..16) lets it through.  The debug build records an index outside
+ * [0, limit) as site 901 and skips the write; the release build, which has
+ * no device check, refuses such an index with SG_ERR_ARG before any launch.
+ * Synchronous. */
+sg_status sg_debug_bounds_probe(long long index, long long limit);
 
 /* sg_autotune - time the apply kernel of this context over candidate launch
  * shapes (cells per shared-memory chunk x threads per CTA x whether the upper

@@ -216,12 +216,34 @@ def sg_mg_setup(ctx, mg_precision=SG_PREC_FP64, nu=2, omega=0.7):
     _check(_abi.load().sg_mg_setup(ctx.handle, int(mg_precision), int(nu), float(omega)), "sg_mg_setup")
 
 
+def sg_debug_bounds():
+    """The device bounds records of the debug build (sg_debug_bounds): a dict
+    with enabled, count and the first violation's site, index and limit."""
+    en, cnt, site, idx, lim = C.c_int(), C.c_uint(), C.c_int(), C.c_longlong(), C.c_longlong()
+    _check(_abi.load().sg_debug_bounds(C.byref(en), C.byref(cnt), C.byref(site), C.byref(idx), C.byref(lim)),
+           "sg_debug_bounds")
+    return {"enabled": en.value, "count": cnt.value, "site": site.value, "index": idx.value, "limit": lim.value}
+
+
+def sg_debug_bounds_probe(index, limit):
+    """Self-test of the bounds record path (sg_debug_bounds_probe)."""
+    _check(_abi.load().sg_debug_bounds_probe(int(index), int(limit)), "sg_debug_bounds_probe")
+
+
 def sg_mg_level_info(ctx, level):
     """The choices of the preconditioner on one level (sg_mg_level_info)."""
     info = (C.c_int * 8)()
     _check(_abi.load().sg_mg_level_info(ctx.handle, int(level), info), "sg_mg_level_info")
     keys = ("levels", "cells", "coarsest", "residual", "vanka_chunk", "vanka_tile", "np", "classes")
     return dict(zip(keys, list(info)))
+
+
+def sg_mg_setup_times(ctx):
+    """Wall times of the last sg_mg_setup in ms: total, patch factorisation and
+    variant timing (sg_mg_setup_times)."""
+    t, f, u = C.c_double(), C.c_double(), C.c_double()
+    _check(_abi.load().sg_mg_setup_times(ctx.handle, C.byref(t), C.byref(f), C.byref(u)), "sg_mg_setup_times")
+    return {"total_ms": t.value, "factor_ms": f.value, "tune_ms": u.value}
 
 
 def sg_mg_set_level_variant(ctx, level=-1, residual_kind=-1, vanka_chunk=0, vanka_tile=-1):

@@ -4,6 +4,8 @@ import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsg.so")
+# the build with device bounds checks (loaded instead when SG_DEBUG_BOUNDS=1)
+LIB_DEBUG_PATH = os.path.join(PKG, "libsg_debug.so")
 
 SG_OK, SG_ERR_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 SG_ERR_NOT_CONVERGED, SG_ERR_NONFINITE, SG_ERR_TIMEOUT = 5, 6, 7
@@ -18,7 +20,7 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_solve_slab_adjoint", "sg_adjoint_gradient", "sg_set_coefficient",
                    "sg_stat_errors", "mc_solve_meshes", "sg_set_apply_shape",
                    "sg_apply_host_async", "sg_mg_level_info", "sg_mg_set_level_variant",
-                   "sg_mg_patch_inverse"])
+                   "sg_mg_patch_inverse", "sg_debug_bounds", "sg_debug_bounds_probe", "sg_mg_setup_times"])
 
 
 class sg_mesh(C.Structure):
@@ -67,9 +69,10 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"libsg.so is not built ({LIB_PATH}); run paper_2605_21046_gb300.build.build()")
-    lib = C.CDLL(LIB_PATH)
+    path = LIB_DEBUG_PATH if os.environ.get("SG_DEBUG_BOUNDS") == "1" else LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} is not built ({path}); run paper_2605_21046_gb300.build.build()")
+    lib = C.CDLL(path)
     vp = C.c_void_p
     lib.sg_setup.argtypes = [C.POINTER(sg_mesh), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
                              C.POINTER(sg_coeff), C.c_int, C.POINTER(vp)]
@@ -86,6 +89,13 @@ def load():
     lib.sg_mg_setup.restype = C.c_int
     lib.sg_vcycle.argtypes = [vp, vp, vp, vp]
     lib.sg_vcycle.restype = C.c_int
+    lib.sg_debug_bounds.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_uint), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    lib.sg_debug_bounds.restype = C.c_int
+    lib.sg_debug_bounds_probe.argtypes = [C.c_longlong, C.c_longlong]
+    lib.sg_debug_bounds_probe.restype = C.c_int
+    lib.sg_mg_setup_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.sg_mg_setup_times.restype = C.c_int
     lib.sg_mg_level_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     lib.sg_mg_level_info.restype = C.c_int
     lib.sg_mg_set_level_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]

@@ -45,6 +45,7 @@ void free_ctx_device(sg_ctx* c) {
   cudaFree(c->d_xbuf);
   cudaFree(c->d_ybuf);
   cudaFree(c->d_krylov);
+  for (sg::KrylovGraph& g : c->kgraph) sg::krylov_graph_free(g);
   if (c->host_stream) cudaStreamDestroy(c->host_stream);
   {
     sg_ctx::HostPipe& p = c->pipe;
@@ -328,6 +329,7 @@ sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega) {
     return fail(st, "sg_mg_setup: " + msg);
   }
   ctx->mg = mg;
+  ++ctx->gen;
   return SG_OK;
 }
 
@@ -375,6 +377,15 @@ sg_status sg_mg_level_info(sg_ctx* ctx, int level, int* info) {
   return st == SG_OK ? SG_OK : fail(st, "sg_mg_level_info: " + msg);
 }
 
+sg_status sg_mg_setup_times(sg_ctx* ctx, double* total_ms, double* factor_ms, double* tune_ms) {
+  if (!ctx || !total_ms || !factor_ms || !tune_ms) return fail(SG_ERR_ARG, "sg_mg_setup_times: null argument");
+  if (!ctx->mg) return fail(SG_ERR_ARG, "sg_mg_setup_times: call sg_mg_setup first");
+  *total_ms = ctx->mg->setup_ms;
+  *factor_ms = ctx->mg->factor_ms;
+  *tune_ms = ctx->mg->tune_ms;
+  return SG_OK;
+}
+
 sg_status sg_mg_set_level_variant(sg_ctx* ctx, int level, int residual_kind, int vanka_chunk, int vanka_tile) {
   if (!ctx) return fail(SG_ERR_ARG, "sg_mg_set_level_variant: ctx is NULL");
   if (!ctx->mg) return fail(SG_ERR_ARG, "sg_mg_set_level_variant: call sg_mg_setup first");
@@ -382,6 +393,7 @@ sg_status sg_mg_set_level_variant(sg_ctx* ctx, int level, int residual_kind, int
   if (e != cudaSuccess) return cuda_fail(e, "sg_mg_set_level_variant: synchronize");
   std::string msg;
   const sg_status st = sg::mg_force_variant(*ctx->mg, level, residual_kind, vanka_chunk, vanka_tile, msg);
+  ++ctx->gen;
   return st == SG_OK ? SG_OK : fail(st, "sg_mg_set_level_variant: " + msg);
 }
 
@@ -504,6 +516,7 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
         if (sg::plan_apply_shape(ctx->hp, c, t, ls, msg) != SG_OK) continue;
         ls.stagger = staggered ? (c + 1) / 2 : 0;
         ctx->ls = ls;
+  ++ctx->gen;
         sg::ApplyParams p;
         fill_params(ctx, x, y, 0, p);
         for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = sg::launch_apply(ctx->hp, ls, p, s);
@@ -521,6 +534,7 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
       }
   }
   ctx->ls = e == cudaSuccess ? best : orig;
+  ++ctx->gen;
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   if (s) cudaStreamDestroy(s);
@@ -540,6 +554,7 @@ sg_status sg_set_apply_shape(sg_ctx* ctx, int chunk, int threads, int stagger) {
   if (st != SG_OK) return fail(SG_ERR_ARG, "sg_set_apply_shape: " + msg);
   ls.stagger = stagger;
   ctx->ls = ls;
+  ++ctx->gen;
   return SG_OK;
 }
 

@@ -15,3 +15,5 @@ void* select_kernel_f64(int dim, int k, int n_t) {
 }
 
 }  // namespace sg
+
+SG_BOUNDS_FETCH(bounds_fetch_apply_f64)

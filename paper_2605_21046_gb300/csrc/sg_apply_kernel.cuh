@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "sg_arith.h"
+#include "sg_bounds.h"
 #include "sg_internal.h"
 #include "sg_shape_tables.h"
 
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
   }
   for (int e = tid; e < p.nnz; e += nthr) {
     CoupleEntry ce;
-    ce.off = p.g_col[e] * NT * SLOT;
+    ce.off = SG_IN(p.g_col[e], n_xi, 105) ? p.g_col[e] * NT * SLOT : 0;
     const int t = p.g_term[e];
     if (premul) {
       const double v = p.g_val[e];
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
       while (k < p.n_pairs && !(p.pair_term[k] == t && p.pair_val[k] == v)) ++k;
       ce.tq = k < p.n_pairs ? k * NQD : -1 - e;
     } else {
-      ce.tq = t * NQD;
+      ce.tq = SG_IN(t, p.n_terms, 106) ? t * NQD : 0;
     }
     Ge[e] = ce;
   }
@@ -303,10 +304,12 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
         for (int idx = tid; idx < nc * per_row; idx += nthr) {
           const int c = idx / per_row, r = idx - c * per_row;
           const int k = r / NQD, q = r - k * NQD;
-          Cs[idx] = A::fin(A::mul(Gv[k], A::in(p.ctab[(c0 + c) * per_cell + Pt[k] * NQD + q])));
+          const long long at = (c0 + c) * per_cell + Pt[k] * NQD + q;
+          if (SG_IN(at, p.n_cells * per_cell, 101)) Cs[idx] = A::fin(A::mul(Gv[k], A::in(p.ctab[at])));
         }
       } else {
-        for (int idx = tid; idx < nc * per_cell; idx += nthr) Cs[idx] = A::in(p.ctab[c0 * per_cell + idx]);
+        for (int idx = tid; idx < nc * per_cell; idx += nthr)
+          if (SG_IN(c0 * per_cell + idx, p.n_cells * per_cell, 101)) Cs[idx] = A::in(p.ctab[c0 * per_cell + idx]);
       }
     }
     // the global node of every (cell, local node) of the chunk, once per
@@ -321,7 +324,8 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
       const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;
-      Nd[i] = interior ? (int)(((long long)gz * nny + gy) * nnx + gx) : -1;
+      const long long node = ((long long)gz * nny + gy) * nnx + gx;
+      Nd[i] = interior && SG_IN(node, p.n_x, 102) ? (int)node : -1;
     }
     __syncthreads();
     for (int c = 0; c < nc; ++c) {
@@ -331,8 +335,9 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
         const int v = j / NKD, a = j - v * NKD;
         const int node = nd[a];
         T val = A::zero();
-        if (node >= 0) val = A::in(xin[(long long)v * p.n_x + node]);
-        qc[(size_t)v * SLOT + a] = val;
+        if (node >= 0 && SG_IN((long long)v * p.n_x + node, (long long)V * p.n_x, 103))
+          val = A::in(xin[(long long)v * p.n_x + node]);
+        if (SG_IN((size_t)c * V * SLOT + (size_t)v * SLOT + a, (size_t)C * V * SLOT, 104)) qc[(size_t)v * SLOT + a] = val;
       }
     }
     __syncthreads();
@@ -403,7 +408,8 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
                   couple(cq[ce.tq], ce.off);
                 } else {
                   const int ee = -1 - ce.tq;
-                  const double a_q = p.ctab[(c0 + c) * p.n_terms * NQD + p.g_term[ee] * NQD + q];
+                  const long long at = (c0 + c) * p.n_terms * NQD + p.g_term[ee] * NQD + q;
+                  const double a_q = SG_IN(at, p.n_cells * p.n_terms * NQD, 108) ? p.ctab[at] : 0.0;
                   couple(A::fin(A::mul(A::in(p.g_val[ee]), A::in(a_q))), ce.off);
                 }
               }
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
       for (int j = tid; j < V * NKD; j += nthr) {
         const int v = j / NKD, a = j - v * NKD;
         const int node = nd[a];
-        if (node >= 0) {
+        if (node >= 0 && SG_IN((long long)v * p.n_x + node, (long long)V * p.n_x, 107)) {
           T val = A::mul(Tb[v % NT], qc[(size_t)v * SLOT + a]);
           if (p.mode == kApplyResidual) val = A::neg(val);
           A::add_out(yout + (long long)v * p.n_x + node, val);

@@ -251,6 +251,8 @@ struct MG {
   cudaGraph_t graph_t[2] = {nullptr, nullptr};       // V-cycle of A (0) and of A^T (1)
   cudaGraphExec_t exec_t[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
+  double factor_ms = 0.0;         // Vanka patch factorisation (device, all levels)
+  double tune_ms = 0.0;           // timing of the level residual and Vanka variants
 };
 
 // single_class: precondition every row with the block of the mean coefficient
@@ -284,6 +286,9 @@ cudaError_t vanka_factor(const HostProblem& hp, const double* d_ctab, const std:
 // z = P^{-1} r for one slab vector (double in, double out) on a stream; with
 // trans != 0 the V-cycle of the transposed blocks A_alpha^T.
 cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans = 0);
+// The same V-cycle launched kernel by kernel on `stream` (no graph launch), so
+// that it can be recorded into an enclosing graph.
+cudaError_t mg_issue(MG& mg, const double* r, double* z, cudaStream_t stream, int trans = 0);
 
 }  // namespace sg
 
@@ -337,11 +342,31 @@ sg_status fgmres(sg_ctx* ctx, const double* b, double* x, double rtol, int max_i
                  cudaStream_t s, std::string& msg,
                  cudaError_t (*apply)(sg_ctx*, const double*, double*, cudaStream_t), int trans = 0);
 cudaError_t apply_device_ctx_t(sg_ctx* c, const double* x, double* y, cudaStream_t s);
-// Restarted right-preconditioned FGMRES on N unknowns with caller-given apply
-// and preconditioner (both on stream s); workspace of krylov_bytes(N, m).
-sg_status fgmres_core(long long N, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
-                      cudaStream_t s, std::string& msg, const std::function<cudaError_t(const double*, double*)>& apply,
-                      const std::function<cudaError_t(const double*, double*)>& prec, double* workspace);
+// A stream-ordered operation on N-vectors that launches kernels only (no host
+// synchronisation, no graph launch), so that it can be captured.
+using IssueFn = std::function<cudaError_t(const double*, double*, cudaStream_t)>;
+// One FGMRES solve recorded as a CUDA graph (fgmres_graph) and what it was
+// recorded for.
+struct KrylovGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr, bs = nullptr, is = nullptr;   // capture streams
+  double* host = nullptr;                                  // page-locked state mirror
+  double* ws = nullptr;
+  long long N = 0;
+  int m = 0;
+  unsigned long long key = 0;
+};
+void krylov_graph_free(KrylovGraph& G);
+// Restarted right-preconditioned FGMRES(m) on N unknowns with caller-given
+// apply and preconditioner, the whole solve (start, every Arnoldi step, the
+// restarts) in one CUDA graph with device-side convergence tests; the graph
+// works on workspace copies of b and x, is recorded on the first call for
+// (N, m, workspace, key) and replayed afterwards.  apply and prec are
+// captured into it.
+sg_status fgmres_graph(long long N, const double* b, double* x, double rtol, int max_it, int m, sg_solve_stats* st,
+                       cudaStream_t s, std::string& msg, const IssueFn& apply, const IssueFn& prec, double* workspace,
+                       KrylovGraph& G, unsigned long long key);
 // rhs = F^(n) (+ B_0 on slab 0) for hp.n_xi rows of E's load tables (no transfer term).
 cudaError_t exact_rhs_load(const HostProblem& hp, ExactData& E, int slab, double* rhs, cudaStream_t s);
 // Value of a coefficient factor (SG_F_ONE / SIN / POW) at one coordinate.
@@ -384,4 +409,9 @@ struct sg_ctx {
   double* d_krylov = nullptr; // FGMRES workspace (lazy): V, Z, w, r and partial sums
   size_t krylov_bytes = 0;
   int krylov_restart = 0;
+  // recorded FGMRES solves (A and A^T) and the set-up generation they were
+  // recorded in: anything that changes a launch (preconditioner, launch
+  // shape, coefficient) increments gen and so forces a new recording
+  sg::KrylovGraph kgraph[2];
+  unsigned long long gen = 1;
 };

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
     }
     // phase 0: gather
     for (int idx = tid; idx < nc * nterm * NQD; idx += nthr)
-      Cs[idx] = A::in(P.ctab[(size_t)cell0 * nterm * NQD + idx]);
+      if (SG_IN((long long)cell0 * nterm * NQD + idx, (long long)P.n_cells * nterm * NQD, 401))
+        Cs[idx] = A::in(P.ctab[(size_t)cell0 * nterm * NQD + idx]);
     // global nodes of the chunk's cells, once per chunk (not per vector)
     for (int i = tid; i < nc * NKD; i += nthr) {
       const int c = i / NKD, a = i - c * NKD;
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
         const int v = j / NKD, a = j - v * NKD;
         const int node = nd[a];
         T val = A::zero();
-        if (node >= 0) val = A::in(xin[(long long)(s0 * NT + v) * P.n_x + node]);
+        if (node >= 0 && SG_IN((long long)(s0 * NT + v) * P.n_x + node, (long long)P.S * NT * P.n_x, 402))
+          val = A::in(xin[(long long)(s0 * NT + v) * P.n_x + node]);
         qc[(size_t)v * SLOT + a] = val;
       }
     }
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
       for (int j = tid; j < VT * NKD; j += nthr) {
         const int v = j / NKD, a = j - v * NKD;
         const int node = nd[a];
-        if (node >= 0) {
+        if (node >= 0 && SG_IN((long long)(s0 * NT + v) * P.n_x + node, (long long)P.S * NT * P.n_x, 403)) {
           T val = A::mul(A::in(p.tb[v % NT]), qc[(size_t)v * SLOT + a]);
           if (p.mode == kApplyResidual) val = A::neg(val);
           A::add_out(yout + (long long)(s0 * NT + v) * P.n_x + node, val);
@@ -252,3 +254,5 @@ cudaError_t launch_mc_apply(int precision, int dim, int k, int n_t, const McPara
 }
 
 }  // namespace sg
+
+SG_BOUNDS_FETCH(bounds_fetch_mc_apply)

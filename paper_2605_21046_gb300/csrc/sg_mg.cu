@@ -29,6 +29,7 @@
 #include <map>
 #include <type_traits>
 
+#include "sg_bounds.h"
 #include "sg_internal.h"
 
 namespace sg {
@@ -67,24 +68,27 @@ __global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long
 // Per (cell, diagonal class) the step is a dense product Z = inv * R with
 // inv the NP x NP patch inverse and R the patch values of the class's modes
 // (NP x modes).  A CTA takes a chunk of C cells that are consecutive in x:
-//   * it gathers r on the chunk's node grid into shared memory as
-//     [time node][node][slot], slots = the tile's modes grouped by class
-//     (blocks of kVankaVB, zero padded), so that the modes of one node are
-//     contiguous (coalesced along x on the global side);
-//   * per class, it stages the chunk's inverses (contiguous in memory: cells
-//     consecutive in x) into shared memory in the vector precision, rows
-//     padded so that consecutive rows fall in different banks;
-//   * every thread accumulates a register block of kVankaR patch rows x
-//     kVankaU slots: per patch column one broadcast 16-byte load per 4 (FP32)
-//     or 2 (FP64) slots and one inverse value per row, kVankaR * kVankaU FMAs;
+//   * it copies the chunk's inverses of the first class (contiguous in
+//     memory: cells consecutive in x) into shared memory with asynchronous
+//     16-byte copies, rows padded to an odd number of 16-byte pieces so that
+//     the rows of 8 consecutive threads fall in different banks, and while
+//     they are in flight gathers r on the chunk's node grid as
+//     [time node][node][slot], slots = the tile's modes grouped by class in
+//     blocks of kVankaVB (zero padded), coalesced along x on the global side;
+//   * every thread accumulates a register block of kVankaR patch rows x one
+//     block of kVankaVB slots: per patch column one broadcast 16-byte load
+//     of the patch values and kVankaR x kVankaVB FMAs, the inverse rows read
+//     16 bytes at a time (bf16 widened in registers);
 //   * the damped, multiplicity-weighted corrections of neighbouring cells are
-//     summed in shared memory, and x is written once per node: a plain update
-//     for nodes only this chunk holds, an atomic add on its outer nodes.
-// Inverses are stored [class][cell][NP][npp] in W (double, float or bf16;
-// npp = NP rounded up to 8).
-constexpr int kVankaVB = 4;      // slots per mode block (modes of one class)
-constexpr int kVankaU = 8;       // slots per thread
-constexpr int kVankaR = 2;       // patch rows per thread
+//     summed in shared memory and added into x once per node with reductions
+//     (no thread waits on a load of x).
+// The gather and the write-back walk their (slot, node) pairs with per-thread
+// increments instead of divisions; the gather keeps kVankaG loads in flight
+// per thread.  Inverses are stored
+// [class][cell][NP][npp] in W (double, float or bf16; npp = NP rounded up to 8).
+constexpr int kVankaVB = 4;      // slots per mode block (modes of one class); slots per thread
+constexpr int kVankaR = 4;       // patch rows per thread
+constexpr int kVankaG = 8;       // gather loads in flight per thread
 
 template <typename T>
 struct VankaParams {
@@ -96,36 +100,66 @@ struct VankaParams {
   int n_blk, chunk, npp;
   int tile_blocks, n_tiles; // mode blocks per tile
   long long n_x, n_cells;
+  long long n_vec_x;        // values per vector set (rows x time nodes x nodes; bounds checks)
+  long long inv_count;      // stored inverse values (bounds checks)
+  size_t smem_values;       // bytes below the index tables in shared memory (bounds checks)
   int cells[3], nn[3];
   T omega;
 };
 
-// Row stride (in values) of a staged inverse: NP rounded up to 4 values, an
-// odd multiple of 4 so that 16-byte row loads of 8 consecutive rows use all
-// 32 banks (FP32).
-__host__ __device__ constexpr int vanka_inv_stride(int np) {
-  return ((np + 3) / 4 % 2 == 0) ? (np + 3) / 4 * 4 + 4 : (np + 3) / 4 * 4;
+// 16-byte pieces per shared-memory row of a staged inverse of NP values of
+// `bytes` each: the pieces the row needs, made odd (bank spread).
+__host__ __device__ constexpr int vanka_row_pieces(int np, int bytes) {
+  return ((np * bytes + 15) / 16) % 2 == 0 ? (np * bytes + 15) / 16 + 1 : (np * bytes + 15) / 16;
 }
-// Slots per node in shared memory for a tile of `blocks` mode blocks: the
-// blocks plus one thread block of padding (a thread reads kVankaU slots).
-__host__ __device__ constexpr int vanka_slots(int blocks) { return blocks * kVankaVB + kVankaU; }
+// Slots per node in shared memory for a tile of `blocks` mode blocks.
+__host__ __device__ constexpr int vanka_slots(int blocks) { return blocks * kVankaVB; }
 
 template <typename T>
-struct Vec16;
+struct Vec4;
 template <>
-struct Vec16<float> {
-  static constexpr int n = 4;
+struct Vec4<float> {
   __device__ static void load(const float* p, float* o) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
   }
 };
 template <>
-struct Vec16<double> {
+struct Vec4<double> {
+  __device__ static void load(const double* p, double* o) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+
+// One 16-byte piece of an inverse row, widened to T.
+template <typename T, typename W>
+struct Piece16;
+template <>
+struct Piece16<float, float> {
+  static constexpr int n = 4;
+  __device__ static void load(const float* p, float* o) { Vec4<float>::load(p, o); }
+};
+template <>
+struct Piece16<double, double> {
   static constexpr int n = 2;
   __device__ static void load(const double* p, double* o) {
-    const double2 v = *reinterpret_cast<const double2*>(p);
-    o[0] = v.x; o[1] = v.y;
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    o[0] = a.x; o[1] = a.y;
+  }
+};
+template <>
+struct Piece16<float, __nv_bfloat16> {
+  static constexpr int n = 8;
+  __device__ static void load(const __nv_bfloat16* p, float* o) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const unsigned int w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
   }
 };
 
@@ -134,38 +168,47 @@ __device__ __forceinline__ T widen(W w) { return (T)w; }
 template <>
 __device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 w) { return __bfloat162float(w); }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename T, typename W, int DIM, int K, int NT, bool TRANS>
-__global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
+__global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
   constexpr int N = K + 1;
   constexpr int NKD = DIM == 2 ? N * N : N * N * N;
   constexpr int NP = NT * NKD;
-  constexpr int NPH = (NP + kVankaR - 1) / kVankaR;   // row groups per cell
-  constexpr int IS = vanka_inv_stride(NP);
-  constexpr int VB = kVankaVB, U = kVankaU, R = kVankaR;
-  constexpr int VN = Vec16<T>::n;
+  constexpr int R = kVankaR, VB = kVankaVB;
+  constexpr int NRG = (NP + R - 1) / R;                        // row groups per cell
+  constexpr int RP = vanka_row_pieces(NP, (int)sizeof(W));     // 16-byte pieces per staged row
+  constexpr int RW = RP * 16 / (int)sizeof(W);                 // values per staged row
+  constexpr int QV = Piece16<T, W>::n;                         // values per piece
+  constexpr int NQC = (NP + QV - 1) / QV;                      // pieces a row product reads
+  constexpr int LYZ = DIM == 2 ? N : N * N;                    // nodes across y (and z)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int C = p.chunk;
-  const int LX = C * K + 1;                          // chunk nodes along x
-  constexpr int LYZ = DIM == 2 ? N : N * N;          // nodes across y (and z)
+  const int LX = C * K + 1;                                    // chunk nodes along x
   const int LN = LX * LYZ;
   const int SL = vanka_slots(p.tile_blocks);
-  T* Rl = reinterpret_cast<T*>(smem_raw);            // [NT][LN][SL]
-  T* Zc = Rl + (size_t)NT * LN * SL;                 // [NT][LN][SL]
-  T* Is = Zc + (size_t)NT * LN * SL;                 // [C][NP][IS] inverses of one class
-  int* Gn = reinterpret_cast<int*>(Is + (size_t)C * NP * IS);   // [LN] global node, -1 outside / boundary
-  int* Gp = Gn + LN;                                 // [LN] 1 for nodes no other chunk touches
-  int* Sm = Gp + LN;                                 // [SL] mode of every slot, -1 padding
-  int* Qo = Sm + SL;                                 // [NP] offset of patch column q in Rl (first cell)
-  for (int q = tid; q < NP; q += nthr) {
-    const int iq = q / NKD, aq = q - iq * NKD;
-    const int ln = aq % N + LX * ((aq / N) % N + (DIM == 3 ? N * (aq / (N * N)) : 0));
-    Qo[q] = (iq * LN + ln) * SL;
-  }
+  const int E = NT * LN;                                       // (time node, node) pairs per slot
+  T* Rl = reinterpret_cast<T*>(smem_raw);                      // [NT][LN][SL]
+  T* Zc = Rl + (size_t)E * SL;                                 // [NT][LN][SL]
+  W* Is = reinterpret_cast<W*>(Zc + (size_t)E * SL);           // [C][NP][RW] inverses of one class
+  int* Gn = reinterpret_cast<int*>(Is + (size_t)C * NP * RW);  // [LN] global node, -1 outside / boundary
+  int* Sm = Gn + LN;                                           // [SL] mode of every slot, -1 padding
   const W* inv = static_cast<const W*>(p.inv);
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
-  const int cpr = (p.cells[0] + C - 1) / C;          // chunks per row of cells
+  const int cpr = (p.cells[0] + C - 1) / C;                    // chunks per row of cells
   const long long n_chunks = (long long)cpr * p.cells[1] * p.cells[2];
+  // (slot, pair) walk of the gather and the write-back: start and increments
+  const int w_sl0 = tid / E, w_e0 = tid - (tid / E) * E;
+  const int w_dq = nthr / E, w_dr = nthr - (nthr / E) * E;
+  const int LNSL = LN * SL, LXSL = LX * SL;
   for (long long unit = blockIdx.x; unit < n_chunks * p.n_tiles; unit += gridDim.x) {
     const long long ch = unit % n_chunks;
     const int tile = (int)(unit / n_chunks);
@@ -177,107 +220,114 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
     const int lxn = nc * K + 1;
     const long long cell0 = ((long long)cz * p.cells[1] + cy) * p.cells[0] + cx0;
     __syncthreads();
-    // the chunk's nodes: global index (or -1) and whether only this chunk touches them
+    // the global index of every node of the chunk (-1 outside the mesh or on the boundary)
     for (int ln = tid; ln < LN; ln += nthr) {
       const int lx = ln % LX, lyz = ln / LX;
       const int ly = lyz % N, lz = DIM == 3 ? lyz / N : 0;
-      int node = -1, priv = 0;
+      int node = -1;
       if (lx < lxn) {
         const int gx = cx0 * K + lx, gy = cy * K + ly, gz = DIM == 3 ? cz * K + lz : 0;
         bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
         if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
         if (in) node = (int)(((long long)gz * nny + gy) * nnx + gx);
-        priv = lx > 0 && lx < lxn - 1 && ly > 0 && ly < K && (DIM == 2 || (lz > 0 && lz < K));
       }
       Gn[ln] = node;
-      Gp[ln] = priv;
     }
     for (int sl = tid; sl < SL; sl += nthr) Sm[sl] = sl < nb * VB ? p.blk_alpha[b0 * VB + sl] : -1;
     __syncthreads();
-    // gather r on the chunk's node grid (slot-major, node fastest); clear the corrections
-    for (int idx = tid; idx < SL * NT * LN; idx += nthr) {
-      const int sl = idx / (NT * LN), rem = idx - sl * (NT * LN);
-      const int i = rem / LN, ln = rem - i * LN;
-      const int mode = Sm[sl], node = Gn[ln];
-      const size_t at = (size_t)(i * LN + ln) * SL + sl;
-      Rl[at] = mode >= 0 && node >= 0 ? p.r[((long long)mode * NT + i) * p.n_x + node] : T(0);
-      Zc[at] = T(0);
-    }
     // runs of consecutive blocks of one class
     for (int rb = 0; rb < nb;) {
       const int cls = p.blk_cls[b0 + rb];
       int re = rb + 1;
       while (re < nb && p.blk_cls[b0 + re] == cls) ++re;
-      const int sa = rb * VB, se = re * VB;
-      rb = re;
-      __syncthreads();
-      // the chunk's inverses of this class, widened to T
+      const int nbr = re - rb;
+      const int sa = rb * VB;
+      if (rb > 0) __syncthreads();                             // the previous run is done with Is
+      // the chunk's inverses of this class, 16-byte asynchronous copies
       {
-        constexpr int QV = 16 / (int)sizeof(W);
-        const uint4* src = reinterpret_cast<const uint4*>(inv + ((long long)cls * p.n_cells + cell0) * NP * p.npp);
-        const int per_row = p.npp / QV;
-        const int keep = min(p.npp, IS);
-        for (int idx = tid; idx < nc * NP * per_row; idx += nthr) {
-          const int rr = idx / per_row, piece = idx - rr * per_row;
-          const uint4 raw = __ldg(src + idx);
-          const W* wv = reinterpret_cast<const W*>(&raw);
-          T* dst = Is + (size_t)rr * IS + piece * QV;
-#pragma unroll
-          for (int k = 0; k < QV; ++k)
-            if (piece * QV + k < keep) dst[k] = widen<T, W>(wv[k]);
+        const long long ibeg = ((long long)cls * p.n_cells + cell0) * NP * p.npp;
+        for (int idx = tid; idx < nc * NP * RP; idx += nthr) {
+          const int rr = idx / RP, piece = idx - rr * RP;
+          if (piece * 16 >= p.npp * (int)sizeof(W)) continue;  // the padding piece of a row
+          const long long g = ibeg + (long long)rr * p.npp + piece * (16 / (int)sizeof(W));
+          if (!SG_IN(g + 16 / (int)sizeof(W) - 1, p.inv_count, 202)) continue;
+          if (!SG_IN((size_t)2 * E * SL * sizeof(T) + ((size_t)rr * RW + piece * (16 / sizeof(W))) * sizeof(W),
+                     p.smem_values, 203))
+            continue;
+          cp_async16(Is + (size_t)rr * RW + piece * (16 / (int)sizeof(W)), inv + g);
         }
       }
+      if (rb == 0) {
+        // gather r on the chunk's node grid (slot-major, node fastest); clear the corrections
+        int sl = w_sl0, e = w_e0;
+        while (sl < SL) {
+          int i = 0;
+#pragma unroll
+          for (int j = 1; j < NT; ++j) i += e >= j * LN;
+          const int ln = e - i * LN;
+          const int mode = Sm[sl], node = Gn[ln];
+          const long long gi = ((long long)mode * NT + i) * p.n_x + node;
+          const size_t at = (size_t)e * SL + sl;
+          Rl[at] = mode >= 0 && node >= 0 && SG_IN(gi, p.n_vec_x, 201) ? p.r[gi] : T(0);
+          Zc[at] = T(0);
+          e += w_dr;
+          sl += w_dq;
+          if (e >= E) { e -= E; ++sl; }
+        }
+      }
+      cp_async_wait_all();
       __syncthreads();
-      const int ng = (se - sa + U - 1) / U;
-      const int items = nc * ng * NPH;
+      const int items = nc * NRG * nbr;
       for (int it = tid; it < items; it += nthr) {
-        const int rp = it % NPH, cg = it / NPH;
-        const int g = cg % ng, c = cg / ng;
-        const int s0 = sa + g * U;
+        const int rg = it % NRG, cb = it / NRG;
+        const int bl = cb % nbr, c = cb / nbr;
+        const int s0 = sa + bl * VB;
         int rows[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) rows[k] = rp + k * NPH;
-        T acc[R][U];
+        for (int k = 0; k < R; ++k) rows[k] = rg + k * NRG;
+        T acc[R][VB];
 #pragma unroll
         for (int k = 0; k < R; ++k)
 #pragma unroll
-          for (int u = 0; u < U; ++u) acc[k][u] = T(0);
-        const T* rbase = Rl + (size_t)c * K * SL + s0;
-        const T* ibase = Is + (size_t)c * NP * IS;
+          for (int u = 0; u < VB; ++u) acc[k][u] = T(0);
+        const T* pb = Rl + (size_t)(c * K) * SL + s0;
+        const W* ib = Is + (size_t)c * NP * RW;
         if constexpr (!TRANS) {
-          const T* ir[R];
+          const W* ir[R];
 #pragma unroll
-          for (int k = 0; k < R; ++k) ir[k] = ibase + (size_t)min(rows[k], NP - 1) * IS;
+          for (int k = 0; k < R; ++k) ir[k] = ib + (size_t)min(rows[k], NP - 1) * RW;
 #pragma unroll
-          for (int q0 = 0; q0 < NP; q0 += VN) {
-            T w[R][VN];
+          for (int qc = 0; qc < NQC; ++qc) {
+            T w[R][QV];
 #pragma unroll
-            for (int k = 0; k < R; ++k) Vec16<T>::load(ir[k] + q0, w[k]);
+            for (int k = 0; k < R; ++k) Piece16<T, W>::load(ir[k] + qc * QV, w[k]);
 #pragma unroll
-            for (int j = 0; j < VN; ++j) {
-              if (q0 + j >= NP) break;
-              const T* pv = rbase + Qo[q0 + j];
-              T v[U];
-#pragma unroll
-              for (int u = 0; u < U; u += VN) Vec16<T>::load(pv + u, v + u);
+            for (int j = 0; j < QV; ++j) {
+              const int q = qc * QV + j;
+              if (q >= NP) break;
+              const int iq = q / NKD, aq = q - iq * NKD;
+              const int ax = aq % N, ayz = aq / N;
+              T v[VB];
+              Vec4<T>::load(pb + iq * LNSL + ayz * LXSL + ax * SL, v);
 #pragma unroll
               for (int k = 0; k < R; ++k)
 #pragma unroll
-                for (int u = 0; u < U; ++u) acc[k][u] = fma(w[k][j], v[u], acc[k][u]);
+                for (int u = 0; u < VB; ++u) acc[k][u] = fma(w[k][j], v[u], acc[k][u]);
             }
           }
         } else {
 #pragma unroll 6
           for (int q = 0; q < NP; ++q) {
-            const T* pv = rbase + Qo[q];
-            T v[U];
-#pragma unroll
-            for (int u = 0; u < U; u += VN) Vec16<T>::load(pv + u, v + u);
+            const int iq = q / NKD, aq = q - iq * NKD;
+            const int ax = aq % N, ayz = aq / N;
+            T v[VB];
+            Vec4<T>::load(pb + iq * LNSL + ayz * LXSL + ax * SL, v);
+            const W* iqrow = ib + (size_t)q * RW;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-              const T w = ibase[(size_t)q * IS + min(rows[k], NP - 1)];
+              const T w = widen<T, W>(iqrow[min(rows[k], NP - 1)]);
 #pragma unroll
-              for (int u = 0; u < U; ++u) acc[k][u] = fma(w, v[u], acc[k][u]);
+              for (int u = 0; u < VB; ++u) acc[k][u] = fma(w, v[u], acc[k][u]);
             }
           }
         }
@@ -292,24 +342,35 @@ __global__ void __launch_bounds__(256) mg_vanka(const VankaParams<T> p) {
           // patches sharing the node (cell corners and faces: the local coordinate is 0 or K)
           const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
           const T sc = p.omega / T(mult);
-          T* z = Zc + (size_t)(i * LN + lna) * SL + s0;
+          const size_t zo = (size_t)(i * LN + lna) * SL + s0;
 #pragma unroll
-          for (int u = 0; u < U; ++u)
-            if (s0 + u < se) atomicAdd(z + u, sc * acc[k][u]);
+          for (int u = 0; u < VB; ++u)
+            if (SG_IN(zo + u, (size_t)E * SL, 204)) atomicAdd(Zc + zo + u, sc * acc[k][u]);
         }
       }
+      rb = re;
     }
     __syncthreads();
-    // write x: chunk-private nodes directly, shared outer nodes atomically
-    for (int idx = tid; idx < nb * VB * NT * LN; idx += nthr) {
-      const int sl = idx / (NT * LN), rem = idx - sl * (NT * LN);
-      const int i = rem / LN, ln = rem - i * LN;
-      const int mode = Sm[sl], node = Gn[ln];
-      if (mode < 0 || node < 0) continue;
-      const T val = Zc[(size_t)(i * LN + ln) * SL + sl];
-      T* dst = p.x + ((long long)mode * NT + i) * p.n_x + node;
-      if (Gp[ln]) *dst += val;
-      else atomicAdd(dst, val);
+    // add the corrections into x: reductions without a returned value, so
+    // that no thread waits on a load of x
+    {
+      const int SLW = nb * VB;
+      int sl = w_sl0, e = w_e0;
+      while (sl < SLW) {
+        int i = 0;
+#pragma unroll
+        for (int j = 1; j < NT; ++j) i += e >= j * LN;
+        const int ln = e - i * LN;
+        const int mode = Sm[sl], node = Gn[ln];
+        if (mode >= 0 && node >= 0) {
+          const T val = Zc[(size_t)e * SL + sl];
+          const long long gi = ((long long)mode * NT + i) * p.n_x + node;
+          if (SG_IN(gi, p.n_vec_x, 205)) atomicAdd(p.x + gi, val);
+        }
+        e += w_dr;
+        sl += w_dq;
+        if (e >= E) { e -= E; ++sl; }
+      }
     }
   }
 }
@@ -342,7 +403,8 @@ __global__ void mg_prolong_add(const T* __restrict__ ec, T* __restrict__ xf, int
         for (int a = 0; a < N; ++a) {
           const T wx = pwx[ix * N + a];
           if (wx == T(0)) continue;
-          s += wz * wy * wx * e[(jz * ncy + jy) * ncx + pcx[ix] * K + a];
+          const long long ci = (jz * ncy + jy) * ncx + pcx[ix] * K + a;
+          if (SG_IN(ci, nc, 501)) s += wz * wy * wx * e[ci];
         }
       }
     }
@@ -374,7 +436,8 @@ __global__ void mg_restrict(const T* __restrict__ rf, T* __restrict__ bc, int V,
       for (int ty = ptry[jy]; ty < ptry[jy + 1]; ++ty) {
         const T w2 = w3 * wy[ty];
         const long long row = (iz * nfy + idxy[ty]) * nfx;
-        for (int tx = ptrx[jx]; tx < ptrx[jx + 1]; ++tx) s += w2 * wx[tx] * r[row + idxx[tx]];
+        for (int tx = ptrx[jx]; tx < ptrx[jx + 1]; ++tx)
+          if (SG_IN(row + idxx[tx], nf, 502)) s += w2 * wx[tx] * r[row + idxx[tx]];
       }
     }
     bc[idx] = s;
@@ -754,21 +817,23 @@ sg_status level_diag_shape(MGLevel& L, int ts, int max_chunk, int vb) {
 // Shared memory of a Vanka chunk: r and the corrections of the tile's slots,
 // the staged inverses of one class, then the nodes' global indices and
 // private flags, the slot modes and the patch-column offsets.
-size_t vanka_smem(const MGLevel& L, int n_blk, int tile_slots, int chunk, size_t value_bytes) {
+size_t vanka_smem(const MGLevel& L, int n_blk, int tile_slots, int chunk, size_t value_bytes, size_t inv_bytes) {
   const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
   const size_t ln = (size_t)(chunk * L.hp.k + 1) * lyz;   // nodes of a chunk
   const int blocks = std::min(n_blk, std::max(1, tile_slots / kVankaVB));
   const size_t sl = (size_t)vanka_slots(blocks);
-  const size_t is = (size_t)vanka_inv_stride(L.np);
-  return (2 * (size_t)L.hp.n_t * ln * sl + (size_t)chunk * L.np * is) * value_bytes +
-         (2 * ln + sl + (size_t)L.np) * sizeof(int);
+  const size_t row = (size_t)vanka_row_pieces(L.np, (int)inv_bytes) * 16;
+  return 2 * (size_t)L.hp.n_t * ln * sl * value_bytes + (size_t)chunk * L.np * row + (ln + sl) * sizeof(int);
 }
 
+// Bytes of one stored patch-inverse value.
+size_t inv_value_bytes(const MG& mg) { return mg.bf16 ? 2 : (mg.precision == kPrecF32 ? 4 : 8); }
+
 // Cells per Vanka chunk: up to 8, within the shared-memory budget.
-int vanka_chunk(const MGLevel& L, int n_blk, int tile_slots, size_t value_bytes, size_t budget) {
+int vanka_chunk(const MGLevel& L, int n_blk, int tile_slots, size_t value_bytes, size_t inv_bytes, size_t budget) {
   int best = 0;
   for (int c = 1; c <= std::min(8, L.hp.cells[0]); ++c)
-    if (vanka_smem(L, n_blk, tile_slots, c, value_bytes) <= budget) best = c;
+    if (vanka_smem(L, n_blk, tile_slots, c, value_bytes, inv_bytes) <= budget) best = c;
   return best;
 }
 
@@ -793,7 +858,15 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
     p.nn[d] = L.hp.nn[d];
   }
   p.omega = T(mg.omega);
-  const size_t smem = vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, sizeof(T));
+  const size_t smem = vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, sizeof(T), sizeof(W));
+  p.n_vec_x = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
+  p.inv_count = (long long)mg.n_classes * L.hp.n_cells * L.np * p.npp;
+  {
+    const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
+    const size_t ln = (size_t)(L.vanka_chunk * L.hp.k + 1) * lyz;
+    p.smem_values = 2 * (size_t)L.hp.n_t * ln * vanka_slots(p.tile_blocks) * sizeof(T) +
+                    (size_t)L.vanka_chunk * L.np * vanka_row_pieces(L.np, (int)sizeof(W)) * 16;
+  }
   const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
   const long long units = (long long)cpr * L.hp.cells[1] * L.hp.cells[2] * p.n_tiles;
   const int grid = (int)std::min<long long>(units, sg::sm_count() * 8);
@@ -1049,9 +1122,10 @@ static cudaError_t tune_vanka(MG& mg) {
     int best_c = L.vanka_chunk, best_t = 0;
     float best_ms = 1e30f;
     for (int tile : tiles) {
-      const int max_c = vanka_chunk(L, mg.n_blk, tile, vb,
+      const int max_c = vanka_chunk(L, mg.n_blk, tile, vb, inv_value_bytes(mg),
                                     tile == mg.vanka_tile
-                                        ? std::max<size_t>(100 * 1024, vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, vb))
+                                        ? std::max<size_t>(100 * 1024, vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, vb,
+                                                                                 inv_value_bytes(mg)))
                                         : 100 * 1024);
       if (max_c == 0) continue;
       std::vector<int> cand;
@@ -1254,9 +1328,11 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
       const size_t wb = kind == 2 ? sizeof(__nv_bfloat16) : kind == 1 ? sizeof(float) : sizeof(double);
       if ((e = cudaMalloc(&L.d_inv, (size_t)mg.n_classes * L.hp.n_cells * L.np * npp * wb)) != cudaSuccess) break;
       bool singular = false;
+      const auto tf = std::chrono::steady_clock::now();
       if ((e = vanka_factor(L.hp, static_cast<const double*>(L.d_ctab), class_diag, kind, L.d_inv, npp, singular,
                             0)) != cudaSuccess)
         break;
+      mg.factor_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf).count();
       if (singular) {
         msg = "singular Vanka patch";
         return SG_ERR_ARG;
@@ -1265,8 +1341,9 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       const size_t vb = precision == kPrecF32 ? 4 : 8;
-      L.vanka_chunk = vanka_chunk(L, mg.n_blk, mg.vanka_tile, vb, 100 * 1024);
-      if (L.vanka_chunk == 0) L.vanka_chunk = vanka_chunk(L, mg.n_blk, mg.vanka_tile, vb, (size_t)optin - 1024);
+      L.vanka_chunk = vanka_chunk(L, mg.n_blk, mg.vanka_tile, vb, inv_value_bytes(mg), 100 * 1024);
+      if (L.vanka_chunk == 0)
+        L.vanka_chunk = vanka_chunk(L, mg.n_blk, mg.vanka_tile, vb, inv_value_bytes(mg), (size_t)optin - 1024);
       if (L.vanka_chunk == 0) {
         msg = "Vanka smoother: one cell with all rows does not fit in shared memory (fewer samples per batch)";
         return SG_ERR_UNSUPPORTED;
@@ -1318,8 +1395,10 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_cls, blk_cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_alpha, blk_alpha);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
+  const auto tt = std::chrono::steady_clock::now();
   if (e == cudaSuccess) e = tune_level_applies(mg);
   if (e == cudaSuccess) e = tune_vanka(mg);
+  mg.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tt).count();
   if (e != cudaSuccess) {
     msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
@@ -1399,7 +1478,7 @@ sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int 
         return SG_ERR_ARG;
       }
       const int c = chunk > 0 ? std::min(chunk, L.hp.cells[0]) : L.vanka_chunk;
-      if (vanka_smem(L, mg.n_blk, t, c, vb) > (size_t)optin - 1024) {
+      if (vanka_smem(L, mg.n_blk, t, c, vb, inv_value_bytes(mg)) > (size_t)optin - 1024) {
         msg = "Vanka chunk does not fit in shared memory";
         return SG_ERR_UNSUPPORTED;
       }
@@ -1457,6 +1536,26 @@ sg_status mg_patch_inverse(const MG& mg, int level, int alpha, long long cell, d
   return SG_OK;
 }
 
+cudaError_t mg_issue(MG& mg, const double* r, double* z, cudaStream_t stream, int trans) {
+  MGLevel& L0 = mg.lv[0];
+  const long long n = (long long)L0.hp.n_xi * L0.hp.n_t * L0.hp.n_x;
+  const bool f32 = mg.precision == kPrecF32;
+  const int t = trans ? 1 : 0;
+  cudaError_t e;
+  if (f32)
+    mg_convert<double, float><<<grid_for(n, 256), 256, 0, stream>>>(r, static_cast<float*>(L0.d_b), n);
+  else
+    mg_convert<double, double><<<grid_for(n, 256), 256, 0, stream>>>(r, static_cast<double*>(L0.d_b), n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = f32 ? issue_vcycle<float>(mg, 0, stream, t) : issue_vcycle<double>(mg, 0, stream, t)) != cudaSuccess)
+    return e;
+  if (f32)
+    mg_convert<float, double><<<grid_for(n, 256), 256, 0, stream>>>(static_cast<const float*>(L0.d_x), z, n);
+  else
+    mg_convert<double, double><<<grid_for(n, 256), 256, 0, stream>>>(static_cast<const double*>(L0.d_x), z, n);
+  return cudaGetLastError();
+}
+
 cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, int trans) {
   MGLevel& L0 = mg.lv[0];
   const long long n = (long long)L0.hp.n_xi * L0.hp.n_t * L0.hp.n_x;
@@ -1485,3 +1584,5 @@ cudaError_t mg_apply(MG& mg, const double* r, double* z, cudaStream_t stream, in
 }
 
 }  // namespace sg
+
+SG_BOUNDS_FETCH(bounds_fetch_mg)

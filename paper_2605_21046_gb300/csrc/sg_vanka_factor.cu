@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "sg_bounds.h"
 #include "sg_internal.h"
 
 namespace sg {
@@ -89,7 +90,9 @@ __global__ void __launch_bounds__(256) vanka_factor_kernel(const FactorParams p)
         const long long cn = ((long long)nz * p.cells[1] + ny) * p.cells[0] + nx;
         const double* ct = p.ctab + cn * p.n_terms * NQD + q;
         const double* dg = p.diag + (size_t)cls * p.n_terms;
-        for (int t = 0; t < p.n_terms; ++t) c += dg[t] * ct[(size_t)t * NQD];
+        for (int t = 0; t < p.n_terms; ++t)
+          if (SG_IN(cn * p.n_terms * NQD + q + (long long)t * NQD, p.n_cells * p.n_terms * NQD, 301))
+            c += dg[t] * ct[(size_t)t * NQD];
       }
       cb[i] = c;
       if (q == 0) s_valid[o] = valid;
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(256) vanka_factor_kernel(const FactorParams p)
     for (int idx = tid; idx < NP * p.npp; idx += nthr) {
       const int row = idx / p.npp, col = idx - row * p.npp;
       const double v = col < NP ? aug[row * NP2 + NP + col] : 0.0;
+      if (!SG_IN(base + idx, units * NP * p.npp, 302)) continue;
       if (p.out_kind == 0) static_cast<double*>(p.out)[base + idx] = v;
       else if (p.out_kind == 1) static_cast<float*>(p.out)[base + idx] = (float)v;
       else static_cast<__nv_bfloat16*>(p.out)[base + idx] = __float2bfloat16_rn((float)v);
@@ -316,3 +320,5 @@ cudaError_t vanka_factor(const HostProblem& hp, const double* d_ctab, const std:
 }
 
 }  // namespace sg
+
+SG_BOUNDS_FETCH(bounds_fetch_factor)

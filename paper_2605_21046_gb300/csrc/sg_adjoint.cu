@@ -97,8 +97,9 @@ __global__ void __launch_bounds__(256) k_bilinear(const BilinParams p) {
       const int a = rest % NKD, cv = rest / NKD;
       const int v = cv % V, c = cv / V;
       const long long gc = c0 + c;
-      const int cx = (int)(gc % p.cells[0]), cy = (int)((gc / p.cells[0]) % p.cells[1]);
-      const int cz = (int)(gc / ((long long)p.cells[0] * p.cells[1]));
+      const unsigned int g32 = (unsigned int)gc;              // cells < 2^31: 32-bit divisions
+      const int cx = (int)(g32 % (unsigned int)p.cells[0]), cy = (int)((g32 / (unsigned int)p.cells[0]) % (unsigned int)p.cells[1]);
+      const int cz = (int)(g32 / ((unsigned int)p.cells[0] * (unsigned int)p.cells[1]));
       const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;

@@ -317,10 +317,10 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
     // extents would otherwise dominate the gather and scatter)
     for (int i = tid; i < nc * NKD; i += nthr) {
       const int c = i / NKD, a = i - c * NKD;
-      const long long gc = c0 + c;
-      const int cx = (int)(gc % p.cells[0]);
-      const int cy = (int)((gc / p.cells[0]) % p.cells[1]);
-      const int cz = (int)(gc / ((long long)p.cells[0] * p.cells[1]));
+      const unsigned int gc = (unsigned int)(c0 + c);       // cells < 2^31: 32-bit divisions
+      const int cx = (int)(gc % (unsigned int)p.cells[0]);
+      const int cy = (int)((gc / (unsigned int)p.cells[0]) % (unsigned int)p.cells[1]);
+      const int cz = (int)(gc / ((unsigned int)p.cells[0] * (unsigned int)p.cells[1]));
       const int gx = cx * K + a % N, gy = cy * K + (a / N) % N, gz = DIM == 3 ? cz * K + a / (N * N) : 0;
       bool interior = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
       if (DIM == 3) interior = interior && gz > 0 && gz < nnz_ - 1;

@@ -220,14 +220,19 @@ struct MGLevel {
   void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
   void* d_b = nullptr;
   void* d_r = nullptr;
-  // transfer from the next coarser level: per direction d, fine node index i ->
-  // coarse cell pc[i] and the (k+1) weights pw[i][.]; restriction lists per
-  // coarse node j: rptr[j]..rptr[j+1] entries (fine index, weight)
-  int* d_pc[3] = {nullptr, nullptr, nullptr};
-  void* d_pw[3] = {nullptr, nullptr, nullptr};      // weights in the MG precision
+  // transfer to and from the next coarser level, per direction d: the
+  // interpolation lists per fine node i (pptr[i]..pptr[i+1] entries (coarse
+  // index, weight)) and the restriction lists per coarse node j (rptr[j]..
+  // rptr[j+1] entries (fine index, weight)), weights in the MG precision;
+  // d_t1 / d_t2 hold the intermediate arrays of the separable passes
+  int* d_pptr[3] = {nullptr, nullptr, nullptr};
+  int* d_pidx[3] = {nullptr, nullptr, nullptr};
+  void* d_pwl[3] = {nullptr, nullptr, nullptr};
   int* d_rptr[3] = {nullptr, nullptr, nullptr};
   int* d_ridx[3] = {nullptr, nullptr, nullptr};
   void* d_rw[3] = {nullptr, nullptr, nullptr};
+  void* d_t1 = nullptr;
+  void* d_t2 = nullptr;
 };
 
 struct MG {

@@ -42,16 +42,20 @@ cudaError_t prepare_apply_kernel(int precision, int dim, int k, int n_t, size_t 
 namespace {
 
 // ------------------------------------------------------------------ kernels
+// Vector-wise kernels run on a 2D grid: blockIdx.y is the vector, the node
+// index within it stays 32-bit (no 64-bit division per element).
+inline dim3 vec_grid(long long n_x, int V) {
+  return dim3((unsigned)std::max<long long>(1, std::min<long long>((n_x + 255) / 256, 1024)), (unsigned)V);
+}
+
 template <typename T>
-__global__ void mg_init_x(const T* __restrict__ b, T* __restrict__ x, long long n_total, long long n_x,
-                          int nnx, int nny, int nnz, int dim) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long m = idx % n_x;
-    const int ix = (int)(m % nnx), iy = (int)((m / nnx) % nny), iz = (int)(m / ((long long)nnx * nny));
+__global__ void mg_init_x(const T* __restrict__ b, T* __restrict__ x, int n_x, int nnx, int nny, int nnz, int dim) {
+  const long long off = (long long)blockIdx.y * n_x;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
+    const int ix = m % nnx, rr = m / nnx, iy = rr % nny, iz = rr / nny;
     bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    x[idx] = bd ? b[idx] : T(0);
+    x[off + m] = bd ? b[off + m] : T(0);
   }
 }
 
@@ -67,28 +71,29 @@ __global__ void mg_convert(const S* __restrict__ a, D* __restrict__ b, long long
 //
 // Per (cell, diagonal class) the step is a dense product Z = inv * R with
 // inv the NP x NP patch inverse and R the patch values of the class's modes
-// (NP x modes).  A CTA takes a chunk of C cells that are consecutive in x:
-//   * it copies the chunk's inverses of the first class (contiguous in
-//     memory: cells consecutive in x) into shared memory with asynchronous
-//     16-byte copies, rows padded to an odd number of 16-byte pieces so that
-//     the rows of 8 consecutive threads fall in different banks, and while
-//     they are in flight gathers r on the chunk's node grid as
-//     [time node][node][slot], slots = the tile's modes grouped by class in
-//     blocks of kVankaVB (zero padded), coalesced along x on the global side;
-//   * every thread accumulates a register block of kVankaR patch rows x one
-//     block of kVankaVB slots: per patch column one broadcast 16-byte load
-//     of the patch values and kVankaR x kVankaVB FMAs, the inverse rows read
-//     16 bytes at a time (bf16 widened in registers);
-//   * the damped, multiplicity-weighted corrections of neighbouring cells are
-//     summed in shared memory and added into x once per node with reductions
-//     (no thread waits on a load of x).
-// The gather and the write-back walk their (slot, node) pairs with per-thread
-// increments instead of divisions; the gather keeps kVankaG loads in flight
-// per thread.  Inverses are stored
-// [class][cell][NP][npp] in W (double, float or bf16; npp = NP rounded up to 8).
+// (NP x modes).  Persistent CTAs walk units (a chunk of C cells consecutive
+// in x, a tile of mode blocks) in two pipeline stages: while one unit is
+// computed, the next unit's data land in the other stage by asynchronous
+// copies (cp.async):
+//   * the chunk's inverses of the unit's first class (contiguous in memory:
+//     cells consecutive in x), 16 bytes at a time, rows padded to an odd
+//     number of 16-byte pieces so that the rows of 8 consecutive threads fall
+//     in different banks;
+//   * r on the chunk's node grid as [time node][node][slot], one value per
+//     copy, slots = the tile's modes grouped by class in blocks of kVankaVB
+//     (padding and Dirichlet nodes stored as zero).
+// Every thread accumulates a register block of kVankaR patch rows x one block
+// of kVankaVB slots: per patch column one broadcast 16-byte load of the patch
+// values and kVankaR x kVankaVB FMAs, the inverse rows read 16 bytes at a time
+// (bf16 widened in registers).  The damped, multiplicity-weighted corrections
+// of neighbouring cells are summed in shared memory and added into x once per
+// node with reductions (no thread waits on a load of x).  The staging and the
+// write-back walk their (slot, node) pairs with per-thread increments instead
+// of divisions; further classes of a tile are staged synchronously.
+// Inverses are stored [class][cell][NP][npp] in W (double, float or bf16;
+// npp = NP rounded up to 8).
 constexpr int kVankaVB = 4;      // slots per mode block (modes of one class); slots per thread
 constexpr int kVankaR = 4;       // patch rows per thread
-constexpr int kVankaG = 8;       // gather loads in flight per thread
 
 template <typename T>
 struct VankaParams {
@@ -177,8 +182,26 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// A copy of sizeof(T) bytes (4 or 8) from global to shared memory, asynchronous.
+template <typename T>
+__device__ __forceinline__ void cp_async_val(T* smem, const T* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// One unit of work (a chunk of cells and a tile of mode blocks).
+struct VankaUnit {
+  int cx0, cy, cz, nc, b0, nb;
+  long long cell0;
+};
+
 template <typename T, typename W, int DIM, int K, int NT, bool TRANS>
-__global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
+__global__ void __launch_bounds__(256, 2) mg_vanka(const VankaParams<T> p) {
   constexpr int N = K + 1;
   constexpr int NKD = DIM == 2 ? N * N : N * N * N;
   constexpr int NP = NT * NKD;
@@ -196,88 +219,143 @@ __global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
   const int LN = LX * LYZ;
   const int SL = vanka_slots(p.tile_blocks);
   const int E = NT * LN;                                       // (time node, node) pairs per slot
-  T* Rl = reinterpret_cast<T*>(smem_raw);                      // [NT][LN][SL]
-  T* Zc = Rl + (size_t)E * SL;                                 // [NT][LN][SL]
-  W* Is = reinterpret_cast<W*>(Zc + (size_t)E * SL);           // [C][NP][RW] inverses of one class
-  int* Gn = reinterpret_cast<int*>(Is + (size_t)C * NP * RW);  // [LN] global node, -1 outside / boundary
-  int* Sm = Gn + LN;                                           // [SL] mode of every slot, -1 padding
+  // shared memory: the corrections, then two stages of (r, inverses, node and slot tables)
+  // stage b: r at Rl0 + b E SL, inverses at Is0 + b C NP RW, node table at
+  // Gn0 + b LN, slot table at Sm0 + b SL
+  T* Zc = reinterpret_cast<T*>(smem_raw);                      // [NT][LN][SL]
+  T* Rl0 = Zc + (size_t)E * SL;                                // 2 x [NT][LN][SL]
+  W* Is0 = reinterpret_cast<W*>(Zc + (size_t)3 * E * SL);      // 2 x [C][NP][RW] inverses of one class
+  int* Gn0 = reinterpret_cast<int*>(Is0 + (size_t)2 * C * NP * RW);   // 2 x [LN] global node, -1 outside / boundary
+  int* Sm0 = Gn0 + 2 * LN;                                     // 2 x [SL] mode of every slot, -1 padding
+  const size_t rl_stage = (size_t)E * SL, is_stage = (size_t)C * NP * RW;
   const W* inv = static_cast<const W*>(p.inv);
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
   const int cpr = (p.cells[0] + C - 1) / C;                    // chunks per row of cells
   const long long n_chunks = (long long)cpr * p.cells[1] * p.cells[2];
+  const long long n_units = n_chunks * p.n_tiles;
   // (slot, pair) walk of the gather and the write-back: start and increments
   const int w_sl0 = tid / E, w_e0 = tid - (tid / E) * E;
   const int w_dq = nthr / E, w_dr = nthr - (nthr / E) * E;
   const int LNSL = LN * SL, LXSL = LX * SL;
-  for (long long unit = blockIdx.x; unit < n_chunks * p.n_tiles; unit += gridDim.x) {
-    const long long ch = unit % n_chunks;
-    const int tile = (int)(unit / n_chunks);
-    const int b0 = tile * p.tile_blocks, nb = min(p.tile_blocks, p.n_blk - b0);
-    const int cx0 = (int)(ch % cpr) * C;
-    const long long row = ch / cpr;
-    const int cy = (int)(row % p.cells[1]), cz = (int)(row / p.cells[1]);
-    const int nc = min(C, p.cells[0] - cx0);
-    const int lxn = nc * K + 1;
-    const long long cell0 = ((long long)cz * p.cells[1] + cy) * p.cells[0] + cx0;
-    __syncthreads();
-    // the global index of every node of the chunk (-1 outside the mesh or on the boundary)
+
+  // 32-bit index arithmetic (units and cells stay below 2^31; 64-bit
+  // divisions would cost more than the rest of the bookkeeping)
+  auto decode = [&](long long unit, VankaUnit& U) {
+    const unsigned int uu = (unsigned int)unit, nch = (unsigned int)n_chunks;
+    const unsigned int ch = uu % nch;
+    const int tile = (int)(uu / nch);
+    U.b0 = tile * p.tile_blocks;
+    U.nb = min(p.tile_blocks, p.n_blk - U.b0);
+    U.cx0 = (int)(ch % (unsigned int)cpr) * C;
+    const unsigned int row = ch / (unsigned int)cpr;
+    U.cy = (int)(row % (unsigned int)p.cells[1]);
+    U.cz = (int)(row / (unsigned int)p.cells[1]);
+    U.nc = min(C, p.cells[0] - U.cx0);
+    U.cell0 = ((long long)U.cz * p.cells[1] + U.cy) * p.cells[0] + U.cx0;
+  };
+  // the global index of every node of the unit's chunk (-1 outside the mesh or
+  // on the boundary) and the mode of every slot
+  auto tables = [&](const VankaUnit& U, int* Gn, int* Sm) {
+    const int lxn = U.nc * K + 1;
     for (int ln = tid; ln < LN; ln += nthr) {
       const int lx = ln % LX, lyz = ln / LX;
       const int ly = lyz % N, lz = DIM == 3 ? lyz / N : 0;
       int node = -1;
       if (lx < lxn) {
-        const int gx = cx0 * K + lx, gy = cy * K + ly, gz = DIM == 3 ? cz * K + lz : 0;
+        const int gx = U.cx0 * K + lx, gy = U.cy * K + ly, gz = DIM == 3 ? U.cz * K + lz : 0;
         bool in = gx > 0 && gx < nnx - 1 && gy > 0 && gy < nny - 1;
         if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
         if (in) node = (int)(((long long)gz * nny + gy) * nnx + gx);
       }
       Gn[ln] = node;
     }
-    for (int sl = tid; sl < SL; sl += nthr) Sm[sl] = sl < nb * VB ? p.blk_alpha[b0 * VB + sl] : -1;
+    for (int sl = tid; sl < SL; sl += nthr) Sm[sl] = sl < U.nb * VB ? p.blk_alpha[U.b0 * VB + sl] : -1;
+  };
+  // asynchronous copies of the chunk's inverses of class `cls` (contiguous in
+  // memory: cells consecutive in x) in 16-byte pieces
+  auto stage_inverses = [&](const VankaUnit& U, int cls, W* Is, int stage_base) {
+    const long long ibeg = ((long long)cls * p.n_cells + U.cell0) * NP * p.npp;
+    for (int idx = tid; idx < U.nc * NP * RP; idx += nthr) {
+      const int rr = idx / RP, piece = idx - rr * RP;
+      if (piece * 16 >= p.npp * (int)sizeof(W)) continue;     // the padding piece of a row
+      const long long g = ibeg + (long long)rr * p.npp + piece * (16 / (int)sizeof(W));
+      if (!SG_IN(g + 16 / (int)sizeof(W) - 1, p.inv_count, 202)) continue;
+      if (!SG_IN((size_t)stage_base + ((size_t)rr * RW + piece * (16 / sizeof(W))) * sizeof(W), p.smem_values, 203))
+        continue;
+      cp_async16(Is + (size_t)rr * RW + piece * (16 / (int)sizeof(W)), inv + g);
+    }
+  };
+  // asynchronous gather of r on the chunk's node grid (slot-major, node
+  // fastest); padding slots and Dirichlet nodes are stored as zero
+  auto stage_r = [&](T* Rl, const int* Gn, const int* Sm) {
+    int sl = w_sl0, e = w_e0;
+    while (sl < SL) {
+      int i = 0;
+#pragma unroll
+      for (int j = 1; j < NT; ++j) i += e >= j * LN;
+      const int ln = e - i * LN;
+      const int mode = Sm[sl], node = Gn[ln];
+      const long long gi = ((long long)mode * NT + i) * p.n_x + node;
+      T* dst = Rl + (size_t)e * SL + sl;
+      if (mode >= 0 && node >= 0 && SG_IN(gi, p.n_vec_x, 201)) cp_async_val(dst, p.r + gi);
+      else *dst = T(0);
+      e += w_dr;
+      sl += w_dq;
+      if (e >= E) { e -= E; ++sl; }
+    }
+  };
+
+  for (int i = tid; i < E * SL; i += nthr) Zc[i] = T(0);
+  long long u = blockIdx.x;
+  int buf = 0;
+  VankaUnit cur, nxt;
+  if (u < n_units) {
+    decode(u, cur);
+    tables(cur, Gn0, Sm0);
+  }
+  __syncthreads();
+  if (u < n_units) {
+    stage_inverses(cur, p.blk_cls[cur.b0], Is0, (int)((size_t)3 * E * SL * sizeof(T)));
+    stage_r(Rl0, Gn0, Sm0);
+  }
+  cp_async_commit();
+  for (; u < n_units; u += gridDim.x, buf ^= 1) {
+    // the next unit's tables and copies go to the other stage while this one computes
+    const long long un = u + gridDim.x;
+    const bool has_next = un < n_units;
+    __syncthreads();                                           // the other stage is free
+    if (has_next) {
+      decode(un, nxt);
+      tables(nxt, Gn0 + (buf ^ 1) * LN, Sm0 + (buf ^ 1) * SL);
+    }
     __syncthreads();
+    if (has_next) {
+      stage_inverses(nxt, p.blk_cls[nxt.b0], Is0 + (buf ^ 1) * is_stage,
+                     (int)((size_t)3 * E * SL * sizeof(T) + (size_t)(buf ^ 1) * is_stage * sizeof(W)));
+      stage_r(Rl0 + (buf ^ 1) * rl_stage, Gn0 + (buf ^ 1) * LN, Sm0 + (buf ^ 1) * SL);
+    }
+    cp_async_commit();
+    cp_async_wait_prior1();                                    // this unit's copies have landed
+    __syncthreads();
+    const T* Rl = Rl0 + buf * rl_stage;
+    W* Is = Is0 + buf * is_stage;
+    const int* Gn = Gn0 + buf * LN;
+    const int* Sm = Sm0 + buf * SL;
     // runs of consecutive blocks of one class
-    for (int rb = 0; rb < nb;) {
-      const int cls = p.blk_cls[b0 + rb];
+    for (int rb = 0; rb < cur.nb;) {
+      const int cls = p.blk_cls[cur.b0 + rb];
       int re = rb + 1;
-      while (re < nb && p.blk_cls[b0 + re] == cls) ++re;
+      while (re < cur.nb && p.blk_cls[cur.b0 + re] == cls) ++re;
       const int nbr = re - rb;
       const int sa = rb * VB;
-      if (rb > 0) __syncthreads();                             // the previous run is done with Is
-      // the chunk's inverses of this class, 16-byte asynchronous copies
-      {
-        const long long ibeg = ((long long)cls * p.n_cells + cell0) * NP * p.npp;
-        for (int idx = tid; idx < nc * NP * RP; idx += nthr) {
-          const int rr = idx / RP, piece = idx - rr * RP;
-          if (piece * 16 >= p.npp * (int)sizeof(W)) continue;  // the padding piece of a row
-          const long long g = ibeg + (long long)rr * p.npp + piece * (16 / (int)sizeof(W));
-          if (!SG_IN(g + 16 / (int)sizeof(W) - 1, p.inv_count, 202)) continue;
-          if (!SG_IN((size_t)2 * E * SL * sizeof(T) + ((size_t)rr * RW + piece * (16 / sizeof(W))) * sizeof(W),
-                     p.smem_values, 203))
-            continue;
-          cp_async16(Is + (size_t)rr * RW + piece * (16 / (int)sizeof(W)), inv + g);
-        }
+      if (rb > 0) {
+        // a further class of this tile: its inverses, synchronously
+        __syncthreads();
+        stage_inverses(cur, cls, Is, (int)((size_t)3 * E * SL * sizeof(T) + (size_t)buf * is_stage * sizeof(W)));
+        cp_async_wait_all();
+        __syncthreads();
       }
-      if (rb == 0) {
-        // gather r on the chunk's node grid (slot-major, node fastest); clear the corrections
-        int sl = w_sl0, e = w_e0;
-        while (sl < SL) {
-          int i = 0;
-#pragma unroll
-          for (int j = 1; j < NT; ++j) i += e >= j * LN;
-          const int ln = e - i * LN;
-          const int mode = Sm[sl], node = Gn[ln];
-          const long long gi = ((long long)mode * NT + i) * p.n_x + node;
-          const size_t at = (size_t)e * SL + sl;
-          Rl[at] = mode >= 0 && node >= 0 && SG_IN(gi, p.n_vec_x, 201) ? p.r[gi] : T(0);
-          Zc[at] = T(0);
-          e += w_dr;
-          sl += w_dq;
-          if (e >= E) { e -= E; ++sl; }
-        }
-      }
-      cp_async_wait_all();
-      __syncthreads();
-      const int items = nc * NRG * nbr;
+      const int items = cur.nc * NRG * nbr;
       for (int it = tid; it < items; it += nthr) {
         const int rg = it % NRG, cb = it / NRG;
         const int bl = cb % nbr, c = cb / nbr;
@@ -289,7 +367,7 @@ __global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
 #pragma unroll
         for (int k = 0; k < R; ++k)
 #pragma unroll
-          for (int u = 0; u < VB; ++u) acc[k][u] = T(0);
+          for (int uu = 0; uu < VB; ++uu) acc[k][uu] = T(0);
         const T* pb = Rl + (size_t)(c * K) * SL + s0;
         const W* ib = Is + (size_t)c * NP * RW;
         if constexpr (!TRANS) {
@@ -312,7 +390,7 @@ __global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
 #pragma unroll
               for (int k = 0; k < R; ++k)
 #pragma unroll
-                for (int u = 0; u < VB; ++u) acc[k][u] = fma(w[k][j], v[u], acc[k][u]);
+                for (int uu = 0; uu < VB; ++uu) acc[k][uu] = fma(w[k][j], v[uu], acc[k][uu]);
             }
           }
         } else {
@@ -327,7 +405,7 @@ __global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
             for (int k = 0; k < R; ++k) {
               const T w = widen<T, W>(iqrow[min(rows[k], NP - 1)]);
 #pragma unroll
-              for (int u = 0; u < VB; ++u) acc[k][u] = fma(w, v[u], acc[k][u]);
+              for (int uu = 0; uu < VB; ++uu) acc[k][uu] = fma(w, v[uu], acc[k][uu]);
             }
           }
         }
@@ -344,17 +422,17 @@ __global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
           const T sc = p.omega / T(mult);
           const size_t zo = (size_t)(i * LN + lna) * SL + s0;
 #pragma unroll
-          for (int u = 0; u < VB; ++u)
-            if (SG_IN(zo + u, (size_t)E * SL, 204)) atomicAdd(Zc + zo + u, sc * acc[k][u]);
+          for (int uu = 0; uu < VB; ++uu)
+            if (SG_IN(zo + uu, (size_t)E * SL, 204)) atomicAdd(Zc + zo + uu, sc * acc[k][uu]);
         }
       }
       rb = re;
     }
     __syncthreads();
-    // add the corrections into x: reductions without a returned value, so
-    // that no thread waits on a load of x
+    // add the corrections into x (reductions: no thread waits on a load of x)
+    // and clear them for the next unit
     {
-      const int SLW = nb * VB;
+      const int SLW = cur.nb * VB;
       int sl = w_sl0, e = w_e0;
       while (sl < SLW) {
         int i = 0;
@@ -362,85 +440,56 @@ __global__ void __launch_bounds__(256, 3) mg_vanka(const VankaParams<T> p) {
         for (int j = 1; j < NT; ++j) i += e >= j * LN;
         const int ln = e - i * LN;
         const int mode = Sm[sl], node = Gn[ln];
+        T* z = Zc + (size_t)e * SL + sl;
         if (mode >= 0 && node >= 0) {
-          const T val = Zc[(size_t)e * SL + sl];
           const long long gi = ((long long)mode * NT + i) * p.n_x + node;
-          if (SG_IN(gi, p.n_vec_x, 205)) atomicAdd(p.x + gi, val);
+          if (SG_IN(gi, p.n_vec_x, 205)) atomicAdd(p.x + gi, *z);
         }
+        *z = T(0);
         e += w_dr;
         sl += w_dq;
         if (e >= E) { e -= E; ++sl; }
       }
     }
+    cur = nxt;
   }
+  cp_async_wait_all();
 }
 
-// x_fine += P e_coarse: gather over the (k+1)^d nodes of the coarse cell that
-// holds the fine node (tensor product of the 1D interpolation tables).
-template <typename T, int DIM, int K>
-__global__ void mg_prolong_add(const T* __restrict__ ec, T* __restrict__ xf, int V, int nfx, int nfy, int nfz,
-                               int ncx, int ncy, int ncz, const int* __restrict__ pcx, const T* __restrict__ pwx,
-                               const int* __restrict__ pcy, const T* __restrict__ pwy,
-                               const int* __restrict__ pcz, const T* __restrict__ pwz) {
-  constexpr int N = K + 1;
-  const long long nf = (long long)nfx * nfy * nfz, nc = (long long)ncx * ncy * ncz;
-  const long long total = nf * V;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(idx / nf);
-    const long long f = idx - (long long)v * nf;
-    const int ix = (int)(f % nfx), iy = (int)((f / nfx) % nfy), iz = (int)(f / ((long long)nfx * nfy));
-    const T* e = ec + (long long)v * nc;
-    T s = T(0);
-    for (int c = 0; c < (DIM == 3 ? N : 1); ++c) {
-      const T wz = DIM == 3 ? pwz[iz * N + c] : T(1);
-      if (wz == T(0)) continue;
-      const long long jz = DIM == 3 ? (long long)(pcz[iz] * K + c) : 0;
-      for (int b = 0; b < N; ++b) {
-        const T wy = pwy[iy * N + b];
-        if (wy == T(0)) continue;
-        const long long jy = pcy[iy] * K + b;
-        for (int a = 0; a < N; ++a) {
-          const T wx = pwx[ix * N + a];
-          if (wx == T(0)) continue;
-          const long long ci = (jz * ncy + jy) * ncx + pcx[ix] * K + a;
-          if (SG_IN(ci, nc, 501)) s += wz * wy * wx * e[ci];
-        }
+// One pass of a separable grid transfer: along one axis of a structured
+// array [VA][nin][B] -> [VA][nout][B],
+//     out[va][jo][b] (+)= sum_t w[t] in[va][idx[t]][b],  t in ptr[jo] .. ptr[jo+1],
+// with the 1D restriction lists (coarse node <- fine nodes) or the 1D
+// interpolation lists (fine node <- coarse nodes).  Restriction P^T and
+// prolongation P are d such passes (x, y, z resp. z, y, x), which read every
+// value a few times instead of (k+1)^d-fold per output.  blockIdx.y walks
+// the leading index, so the per-element index arithmetic stays 32-bit.
+template <typename T>
+__global__ void mg_axis_gather(const T* __restrict__ in, T* __restrict__ out, long long VA, int nin, int nout, int B,
+                               const int* __restrict__ ptr, const int* __restrict__ idx, const T* __restrict__ w,
+                               int accumulate) {
+  const int L = nout * B;
+  // short rows (L < blockDim): every block takes several rows, one element
+  // per thread; long rows: a row is strided over blockIdx.x
+  const bool shortrow = L < (int)blockDim.x;
+  const int rows = shortrow ? (int)blockDim.x / L : 1;
+  const int lr = shortrow ? (int)threadIdx.x / L : 0;
+  if (lr >= rows) return;
+  const int l_first = shortrow ? (int)threadIdx.x - lr * L : (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int l_step = shortrow ? L : (int)(gridDim.x * blockDim.x);
+  for (long long va = (long long)blockIdx.y * rows + lr; va < VA; va += (long long)gridDim.y * rows) {
+    const T* src = in + va * nin * (long long)B;
+    T* dst = out + va * L;
+    for (int l = l_first; l < L; l += l_step) {
+      const int jo = l / B, b = l - jo * B;
+      T s = T(0);
+      for (int t = ptr[jo]; t < ptr[jo + 1]; ++t) {
+        const int si = idx[t] * B + b;
+        if (SG_IN(si, (long long)nin * B, 501)) s += w[t] * src[si];
       }
+      if (accumulate) dst[l] += s;
+      else dst[l] = s;
     }
-    xf[idx] += s;
-  }
-}
-
-// b_coarse = P^T r_fine: gather over the fine nodes in the support of each
-// coarse node (tensor product of the 1D transposed tables).
-template <typename T, int DIM>
-__global__ void mg_restrict(const T* __restrict__ rf, T* __restrict__ bc, int V, int nfx, int nfy, int nfz,
-                            int ncx, int ncy, int ncz, const int* __restrict__ ptrx, const int* __restrict__ idxx,
-                            const T* __restrict__ wx, const int* __restrict__ ptry, const int* __restrict__ idxy,
-                            const T* __restrict__ wy, const int* __restrict__ ptrz, const int* __restrict__ idxz,
-                            const T* __restrict__ wz) {
-  const long long nf = (long long)nfx * nfy * nfz, nc = (long long)ncx * ncy * ncz;
-  const long long total = nc * V;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(idx / nc);
-    const long long j = idx - (long long)v * nc;
-    const int jx = (int)(j % ncx), jy = (int)((j / ncx) % ncy), jz = (int)(j / ((long long)ncx * ncy));
-    const T* r = rf + (long long)v * nf;
-    T s = T(0);
-    const int z0 = DIM == 3 ? ptrz[jz] : 0, z1 = DIM == 3 ? ptrz[jz + 1] : 1;
-    for (int tz = z0; tz < z1; ++tz) {
-      const T w3 = DIM == 3 ? wz[tz] : T(1);
-      const long long iz = DIM == 3 ? idxz[tz] : 0;
-      for (int ty = ptry[jy]; ty < ptry[jy + 1]; ++ty) {
-        const T w2 = w3 * wy[ty];
-        const long long row = (iz * nfy + idxy[ty]) * nfx;
-        for (int tx = ptrx[jx]; tx < ptrx[jx + 1]; ++tx)
-          if (SG_IN(row + idxx[tx], nf, 502)) s += w2 * wx[tx] * r[row + idxx[tx]];
-      }
-    }
-    bc[idx] = s;
   }
 }
 
@@ -641,8 +690,11 @@ bool coarse_inverse(const HostProblem& hp, const ElementData& e, const std::vect
 }
 
 // 1D interpolation table of one direction between a fine and a coarse level.
-void transfer_1d(const HostProblem& fine, const HostProblem& coarse, int d, std::vector<int>& pc,
-                 std::vector<double>& pw, std::vector<int>& rptr, std::vector<int>& ridx, std::vector<double>& rw) {
+void transfer_1d(const HostProblem& fine, const HostProblem& coarse, int d, std::vector<int>& pptr,
+                 std::vector<int>& pidx, std::vector<double>& pwl, std::vector<int>& rptr, std::vector<int>& ridx,
+                 std::vector<double>& rw) {
+  std::vector<int> pc;
+  std::vector<double> pw;
   const int K = fine.k, n = K + 1;
   const std::vector<double> gll = lobatto_nodes(K);
   const int nf = fine.nn[d], nc = coarse.nn[d];
@@ -674,6 +726,18 @@ void transfer_1d(const HostProblem& fine, const HostProblem& coarse, int d, std:
       rw.push_back(t.second);
     }
     rptr[j + 1] = (int)ridx.size();
+  }
+  // interpolation lists: fine node i <- coarse nodes pc[i] K + a with nonzero weight
+  pptr.assign(nf + 1, 0);
+  pidx.clear();
+  pwl.clear();
+  for (int i = 0; i < nf; ++i) {
+    for (int a = 0; a < n; ++a)
+      if (pw[(size_t)i * n + a] != 0.0) {
+        pidx.push_back(pc[i] * K + a);
+        pwl.push_back(pw[(size_t)i * n + a]);
+      }
+    pptr[i + 1] = (int)pidx.size();
   }
 }
 
@@ -786,17 +850,16 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
 // The initial iterate (x = b on Dirichlet dofs, 0 inside) and its residual
 // (r = b inside, 0 on Dirichlet dofs) in one pass, without an apply.
 template <typename T>
-__global__ void mg_start(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, long long n_total,
-                         long long n_x, int nnx, int nny, int nnz, int dim) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n_total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long m = idx % n_x;
-    const int ix = (int)(m % nnx), iy = (int)((m / nnx) % nny), iz = (int)(m / ((long long)nnx * nny));
+__global__ void mg_start(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, int n_x, int nnx, int nny,
+                         int nnz, int dim) {
+  const long long off = (long long)blockIdx.y * n_x;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
+    const int ix = m % nnx, rr = m / nnx, iy = rr % nny, iz = rr / nny;
     bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
     if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    const T v = b[idx];
-    x[idx] = bd ? v : T(0);
-    r[idx] = bd ? T(0) : v;
+    const T v = b[off + m];
+    x[off + m] = bd ? v : T(0);
+    r[off + m] = bd ? T(0) : v;
   }
 }
 
@@ -823,7 +886,9 @@ size_t vanka_smem(const MGLevel& L, int n_blk, int tile_slots, int chunk, size_t
   const int blocks = std::min(n_blk, std::max(1, tile_slots / kVankaVB));
   const size_t sl = (size_t)vanka_slots(blocks);
   const size_t row = (size_t)vanka_row_pieces(L.np, (int)inv_bytes) * 16;
-  return 2 * (size_t)L.hp.n_t * ln * sl * value_bytes + (size_t)chunk * L.np * row + (ln + sl) * sizeof(int);
+  // the corrections and two stages of r, inverses and tables
+  return 3 * (size_t)L.hp.n_t * ln * sl * value_bytes + 2 * (size_t)chunk * L.np * row +
+         2 * (ln + sl) * sizeof(int);
 }
 
 // Bytes of one stored patch-inverse value.
@@ -861,17 +926,24 @@ cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   const size_t smem = vanka_smem(L, mg.n_blk, tile, L.vanka_chunk, sizeof(T), sizeof(W));
   p.n_vec_x = (long long)L.hp.n_xi * L.hp.n_t * L.hp.n_x;
   p.inv_count = (long long)mg.n_classes * L.hp.n_cells * L.np * p.npp;
+  const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
   {
-    const int N = L.hp.k + 1, lyz = L.hp.dim == 2 ? N : N * N;
     const size_t ln = (size_t)(L.vanka_chunk * L.hp.k + 1) * lyz;
-    p.smem_values = 2 * (size_t)L.hp.n_t * ln * vanka_slots(p.tile_blocks) * sizeof(T) +
-                    (size_t)L.vanka_chunk * L.np * vanka_row_pieces(L.np, (int)sizeof(W)) * 16;
+    p.smem_values = 3 * (size_t)L.hp.n_t * ln * vanka_slots(p.tile_blocks) * sizeof(T) +
+                    2 * (size_t)L.vanka_chunk * L.np * vanka_row_pieces(L.np, (int)sizeof(W)) * 16;
   }
+  // threads: the row-group x slot-block items of a chunk (one class), whole warps
+  const int nrg = (L.np + kVankaR - 1) / kVankaR;
+  const int items = L.vanka_chunk * nrg * p.tile_blocks;
+  const int threads = std::max(64, std::min(256, (items + 31) / 32 * 32));
+  auto kern = trans ? &mg_vanka<T, W, DIM, K, NT, true> : &mg_vanka<T, W, DIM, K, NT, false>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
   const int cpr = (L.hp.cells[0] + L.vanka_chunk - 1) / L.vanka_chunk;
   const long long units = (long long)cpr * L.hp.cells[1] * L.hp.cells[2] * p.n_tiles;
-  const int grid = (int)std::min<long long>(units, sg::sm_count() * 8);
-  auto kern = trans ? &mg_vanka<T, W, DIM, K, NT, true> : &mg_vanka<T, W, DIM, K, NT, false>;
-  kern<<<grid, 256, smem, s>>>(p);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(units, sg::sm_count() * std::max(1, per_sm)));
+  kern<<<grid, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -930,49 +1002,55 @@ bool vk_launch(MG& mg, MGLevel& L, cudaStream_t s) {
 }
 
 template <typename T>
-bool prolong(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
-  const long long n = (long long)F.hp.n_x * V;
-  const int g = grid_for(n, 256);
-#define SG_P(D, KK)                                                                                             \
-  if (F.hp.dim == D && F.hp.k == KK) {                                                                        \
-    mg_prolong_add<T, D, KK><<<g, 256, 0, s>>>(static_cast<const T*>(C.d_x), static_cast<T*>(F.d_x), V, F.hp.nn[0], \
-                                               F.hp.nn[1], F.hp.nn[2], C.hp.nn[0], C.hp.nn[1], C.hp.nn[2],      \
-                                               F.d_pc[0], static_cast<const T*>(F.d_pw[0]), F.d_pc[1],          \
-                                               static_cast<const T*>(F.d_pw[1]), F.d_pc[2],                      \
-                                               static_cast<const T*>(F.d_pw[2]));                                \
-    return true;                                                                                              \
-  }
-  SG_P(2, 1) SG_P(2, 2) SG_P(2, 3) SG_P(3, 1) SG_P(3, 2)
-#undef SG_P
-  return false;
+void axis_pass(const void* in, void* out, long long VA, int nin, int nout, int B, const int* ptr, const int* idx,
+               const void* w, int accumulate, cudaStream_t s) {
+  const long long L = (long long)nout * B;
+  const long long rows = L < 256 ? 256 / L : 1;                // rows per block for short rows
+  const int gx = L < 256 ? 1 : (int)std::min<long long>((L + 255) / 256, 256);
+  const long long row_blocks = (VA + rows - 1) / rows;
+  const int gy = (int)std::max<long long>(1, std::min<long long>(row_blocks, std::max(1, 16384 / gx)));
+  mg_axis_gather<T><<<dim3(gx, gy), 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin, nout, B,
+                                                 ptr, idx, static_cast<const T*>(w), accumulate);
 }
 
+// x_fine += P e_coarse: interpolation along z (3D), y, then x
+template <typename T>
+bool prolong(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
+  const int nfx = F.hp.nn[0], nfy = F.hp.nn[1], nfz = F.hp.nn[2];
+  const int ncx = C.hp.nn[0], ncy = C.hp.nn[1], ncz = C.hp.nn[2];
+  if (F.hp.dim == 3) {
+    axis_pass<T>(C.d_x, F.d_t2, V, ncz, nfz, ncy * ncx, F.d_pptr[2], F.d_pidx[2], F.d_pwl[2], 0, s);
+    axis_pass<T>(F.d_t2, F.d_t1, (long long)V * nfz, ncy, nfy, ncx, F.d_pptr[1], F.d_pidx[1], F.d_pwl[1], 0, s);
+    axis_pass<T>(F.d_t1, F.d_x, (long long)V * nfz * nfy, ncx, nfx, 1, F.d_pptr[0], F.d_pidx[0], F.d_pwl[0], 1, s);
+  } else {
+    axis_pass<T>(C.d_x, F.d_t1, V, ncy, nfy, ncx, F.d_pptr[1], F.d_pidx[1], F.d_pwl[1], 0, s);
+    axis_pass<T>(F.d_t1, F.d_x, (long long)V * nfy, ncx, nfx, 1, F.d_pptr[0], F.d_pidx[0], F.d_pwl[0], 1, s);
+  }
+  return cudaGetLastError() == cudaSuccess;
+}
+
+// b_coarse = P^T r_fine: restriction along x, y, then z (3D)
 template <typename T>
 void restrict_to(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
-  const long long n = (long long)C.hp.n_x * V;
-  const int g = grid_for(n, 256);
-  if (F.hp.dim == 2)
-    mg_restrict<T, 2><<<g, 256, 0, s>>>(static_cast<const T*>(F.d_r), static_cast<T*>(C.d_b), V, F.hp.nn[0],
-                                        F.hp.nn[1], F.hp.nn[2], C.hp.nn[0], C.hp.nn[1], C.hp.nn[2], F.d_rptr[0],
-                                        F.d_ridx[0], static_cast<const T*>(F.d_rw[0]), F.d_rptr[1], F.d_ridx[1],
-                                        static_cast<const T*>(F.d_rw[1]), F.d_rptr[2], F.d_ridx[2],
-                                        static_cast<const T*>(F.d_rw[2]));
-  else
-    mg_restrict<T, 3><<<g, 256, 0, s>>>(static_cast<const T*>(F.d_r), static_cast<T*>(C.d_b), V, F.hp.nn[0],
-                                        F.hp.nn[1], F.hp.nn[2], C.hp.nn[0], C.hp.nn[1], C.hp.nn[2], F.d_rptr[0],
-                                        F.d_ridx[0], static_cast<const T*>(F.d_rw[0]), F.d_rptr[1], F.d_ridx[1],
-                                        static_cast<const T*>(F.d_rw[1]), F.d_rptr[2], F.d_ridx[2],
-                                        static_cast<const T*>(F.d_rw[2]));
+  const int nfx = F.hp.nn[0], nfy = F.hp.nn[1], nfz = F.hp.nn[2];
+  const int ncx = C.hp.nn[0], ncy = C.hp.nn[1], ncz = C.hp.nn[2];
+  if (F.hp.dim == 3) {
+    axis_pass<T>(F.d_r, F.d_t1, (long long)V * nfz * nfy, nfx, ncx, 1, F.d_rptr[0], F.d_ridx[0], F.d_rw[0], 0, s);
+    axis_pass<T>(F.d_t1, F.d_t2, (long long)V * nfz, nfy, ncy, ncx, F.d_rptr[1], F.d_ridx[1], F.d_rw[1], 0, s);
+    axis_pass<T>(F.d_t2, C.d_b, V, nfz, ncz, ncy * ncx, F.d_rptr[2], F.d_ridx[2], F.d_rw[2], 0, s);
+  } else {
+    axis_pass<T>(F.d_r, F.d_t1, (long long)V * nfy, nfx, ncx, 1, F.d_rptr[0], F.d_ridx[0], F.d_rw[0], 0, s);
+    axis_pass<T>(F.d_t1, C.d_b, V, nfy, ncy, ncx, F.d_rptr[1], F.d_ridx[1], F.d_rw[1], 0, s);
+  }
 }
 
 template <typename T>
 cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
   MGLevel& L = mg.lv[l];
   const int V = L.hp.n_xi * L.hp.n_t;
-  const long long n = (long long)V * L.hp.n_x;
   if (L.coarsest) {
-    mg_init_x<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x), n, L.hp.n_x,
-                                                  L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
+    mg_init_x<T><<<vec_grid(L.hp.n_x, V), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
+                                                      (int)L.hp.n_x, L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
     const size_t smem = (size_t)L.n_int * sizeof(T);
     mg_coarse<T><<<L.hp.n_xi, 256, smem, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
                                               static_cast<const T*>(L.d_inv), mg.d_cls,
@@ -981,9 +1059,9 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
     return cudaGetLastError();
   }
   cudaError_t e;
-  mg_start<T><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
-                                               static_cast<T*>(L.d_r), n, L.hp.n_x, L.hp.nn[0], L.hp.nn[1],
-                                               L.hp.nn[2], L.hp.dim);
+  mg_start<T><<<vec_grid(L.hp.n_x, V), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
+                                                    static_cast<T*>(L.d_r), (int)L.hp.n_x, L.hp.nn[0], L.hp.nn[1],
+                                                    L.hp.nn[2], L.hp.dim);
   for (int it = 0; it < mg.nu; ++it) {
     if (it > 0 && (e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
     if (!vanka<T>(mg, L, s, trans)) return cudaErrorInvalidValue;
@@ -1169,9 +1247,10 @@ void mg_free(MG& mg) {
   for (MGLevel& L : mg.lv) {
     cudaFree(L.d_ctab); cudaFree(L.d_grow); cudaFree(L.d_gcol); cudaFree(L.d_gterm); cudaFree(L.d_gval);
     cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner); cudaFree(L.d_amq); cudaFree(L.d_amqT);
-    cudaFree(L.d_x); cudaFree(L.d_b); cudaFree(L.d_r);
+    cudaFree(L.d_x); cudaFree(L.d_b); cudaFree(L.d_r); cudaFree(L.d_t1); cudaFree(L.d_t2);
     for (int d = 0; d < 3; ++d) {
-      cudaFree(L.d_pc[d]); cudaFree(L.d_pw[d]); cudaFree(L.d_rptr[d]); cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
+      cudaFree(L.d_pptr[d]); cudaFree(L.d_pidx[d]); cudaFree(L.d_pwl[d]);
+      cudaFree(L.d_rptr[d]); cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
     }
   }
   mg.lv.clear();
@@ -1362,24 +1441,25 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     if ((e = cudaMalloc(&L.d_r, bytes)) != cudaSuccess) break;
     if (l > 0) {
       MGLevel& F = mg.lv[l - 1];
-      for (int d = 0; d < 3; ++d) {
-        std::vector<int> pc, rptr, ridx;
-        std::vector<double> pw, rw;
-        if (d < F.hp.dim) {
-          transfer_1d(F.hp, L.hp, d, pc, pw, rptr, ridx, rw);
-        } else {
-          pc = {0};
-          pw.assign(F.hp.k + 1, 0.0);
-          pw[0] = 1.0;
-          rptr = {0, 1};
-          ridx = {0};
-          rw = {1.0};
-        }
-        if ((e = upload_vec(&F.d_pc[d], pc)) != cudaSuccess) break;
-        if ((e = upload_values(&F.d_pw[d], pw, precision)) != cudaSuccess) break;
+      for (int d = 0; d < F.hp.dim; ++d) {
+        std::vector<int> pptr, pidx, rptr, ridx;
+        std::vector<double> pwl, rw;
+        transfer_1d(F.hp, L.hp, d, pptr, pidx, pwl, rptr, ridx, rw);
+        if ((e = upload_vec(&F.d_pptr[d], pptr)) != cudaSuccess) break;
+        if ((e = upload_vec(&F.d_pidx[d], pidx)) != cudaSuccess) break;
+        if ((e = upload_values(&F.d_pwl[d], pwl, precision)) != cudaSuccess) break;
         if ((e = upload_vec(&F.d_rptr[d], rptr)) != cudaSuccess) break;
         if ((e = upload_vec(&F.d_ridx[d], ridx)) != cudaSuccess) break;
         if ((e = upload_values(&F.d_rw[d], rw, precision)) != cudaSuccess) break;
+      }
+      if (e != cudaSuccess) break;
+      // intermediate arrays of the separable transfers between F and this level
+      {
+        const long long V = (long long)F.hp.n_xi * F.hp.n_t;
+        const long long t1 = V * F.hp.nn[2] * F.hp.nn[1] * L.hp.nn[0];
+        const long long t2 = F.hp.dim == 3 ? V * F.hp.nn[2] * L.hp.nn[1] * L.hp.nn[0] : 1;
+        if ((e = cudaMalloc(&F.d_t1, t1 * vb)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&F.d_t2, t2 * vb)) != cudaSuccess) break;
       }
       if (e != cudaSuccess) break;
     }

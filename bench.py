@@ -352,6 +352,36 @@ def measure_solve(sg, torch, spec, dev, reps=3, autotune=True):
             "solver": f"FGMRES(30), block-Jacobi GMG V-cycle (Vanka, nu={MG_NU}, omega={MG_OMEGA})", "splits": out}
 
 
+def next_summary(rows):
+    """The NEXT rows' headline figures, compact (the line's last key, so that a
+    reader keeping only the end of the output still has them)."""
+    if not rows:
+        return None
+    out = {}
+    mp = rows.get("mixed_precision")
+    if mp:
+        sp = mp["splits"]
+        out["mixed_3d_q2_32^3_M3P3_20slabs"] = {
+            k: {"ms_per_slab": round(v["ms_per_slab"], 2), "setup_ms": round(v["mg_setup_ms"], 1),
+                "ratio_vs_fp64_with_setup": round(v["time_ratio_vs_fp64_with_setup"], 3),
+                "rel_diff_vs_fp64": float("%.2g" % v["max_rel_diff_vs_fp64"]),
+                "its": v["iterations_mean"]} for k, v in sp.items()}
+    mc = rows.get("mc_vs_sg")
+    if mc:
+        out["mc_vs_sg_4096_samples_50slabs"] = {
+            "mc_s": round(mc["mc"]["ms"] / 1e3, 2), "sg_s": round(mc["sg_ms_both_meshes"] / 1e3, 3),
+            "mc_err_mean_var": {k: [float("%.3g" % v["mc_error_mean_L2"]), float("%.3g" % v["mc_error_var_L2"])]
+                                for k, v in mc["meshes"].items()},
+            "sg_err_mean_var": {k: [float("%.3g" % v["sg_error_mean_L2"]), float("%.3g" % v["sg_error_var_L2"])]
+                                for k, v in mc["meshes"].items()}}
+    ad = rows.get("adjoint")
+    if ad:
+        out["adjoint_128^2_q2_M4P4_50slabs"] = {
+            "grad_s": round(ad["grad_ms"] / 1e3, 2), "grad_over_forward": round(ad["grad_over_forward"], 2),
+            "fd_rel_diff": {k: float("%.2g" % v["rel_diff"]) for k, v in ad["fd_checks"].items()}}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2605_21046_gb300 as sg
@@ -488,7 +518,8 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "variants": {"dw": dw, "l2_hot": hot},
             "solve": solve,
-            "next": next_rows,
+            "next_detail": next_rows,
+            "next": next_summary(next_rows),
         }
         if dw is not None:
             # the double-word apply runs on the FP32 pipe: 12 FP32 instructions per
@@ -802,7 +833,7 @@ def next_paper(sg, torch, inputs, steps=30, warmup=5):
             "paper_context": "Table 2 of the paper, its CPU cluster; context only", "degrees": out}
 
 
-def next_vcycle(sg, torch, inputs, profile_range=False):
+def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32"):
     """One V-cycle of the block-Jacobi multigrid (all modes at once) on the
     64x64 Q2 P=3 and 32^3 Q2 P=3 workloads, per precision: device ms per
     V-cycle (10 graph launches after 3 warm-up ones).  With profile_range one
@@ -830,7 +861,8 @@ def next_vcycle(sg, torch, inputs, profile_range=False):
                 torch.cuda.synchronize()
                 row[f"{pname}_nu{nu}"] = a.elapsed_time(b) / 10
         if profile_range and wname.startswith("3d"):
-            sg.sg_mg_setup(ctx, sg.SG_PREC_FP32, MG_NU, MG_OMEGA)
+            sg.sg_mg_setup(ctx, sg.SG_PREC_BF16 if profile_mg == "bf16" else sg.SG_PREC_FP32, MG_NU, MG_OMEGA)
+            row["profiled_levels"] = [sg.sg_mg_level_info(ctx, lev) for lev in range(sg.sg_mg_level_info(ctx, 0)["levels"])]
             sg.sg_vcycle(ctx, r, z)
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
@@ -861,7 +893,7 @@ def run_next(args, world, rank, local):
             elif row == "adjoint":
                 out = next_adjoint(sg, torch, inputs)
             elif row == "vcycle":
-                out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range)
+                out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range, profile_mg=args.profile_mg)
             elif row == "applies":
                 out = next_applies(sg, torch, inputs)
             elif row == "paper":
@@ -891,6 +923,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--profile-variant", choices=["fp64", "dw"], default="fp64",
                     help="which timed apply loop --profile-range brackets")
+    ap.add_argument("--profile-mg", choices=["fp32", "bf16"], default="fp32",
+                    help="multigrid precision of the V-cycle --profile-range brackets (--rows vcycle)")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the NEXT rows (mixed precision, Monte-Carlo vs SG, adjoint) of the default line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")

@@ -232,9 +232,9 @@ def sg_debug_bounds_probe(index, limit):
 
 def sg_mg_level_info(ctx, level):
     """The choices of the preconditioner on one level (sg_mg_level_info)."""
-    info = (C.c_int * 8)()
+    info = (C.c_int * 10)()
     _check(_abi.load().sg_mg_level_info(ctx.handle, int(level), info), "sg_mg_level_info")
-    keys = ("levels", "cells", "coarsest", "residual", "vanka_chunk", "vanka_tile", "np", "classes")
+    keys = ("levels", "cells", "coarsest", "residual", "vanka_chunk", "vanka_tile", "np", "classes", "vanka_kind")
     return dict(zip(keys, list(info)))
 
 
@@ -246,11 +246,11 @@ def sg_mg_setup_times(ctx):
     return {"total_ms": t.value, "factor_ms": f.value, "tune_ms": u.value}
 
 
-def sg_mg_set_level_variant(ctx, level=-1, residual_kind=-1, vanka_chunk=0, vanka_tile=-1):
-    """Force the residual kind / Vanka chunk / Vanka tile of one smoothed
-    level or of all of them (sg_mg_set_level_variant)."""
+def sg_mg_set_level_variant(ctx, level=-1, residual_kind=-1, vanka_chunk=0, vanka_tile=-1, vanka_kind=-1):
+    """Force the residual kind / Vanka chunk / Vanka tile / Vanka kernel of one
+    smoothed level or of all of them (sg_mg_set_level_variant)."""
     _check(_abi.load().sg_mg_set_level_variant(ctx.handle, int(level), int(residual_kind), int(vanka_chunk),
-                                               int(vanka_tile)), "sg_mg_set_level_variant")
+                                               int(vanka_tile), int(vanka_kind)), "sg_mg_set_level_variant")
 
 
 def sg_mg_patch_inverse(ctx, level, alpha, cell):

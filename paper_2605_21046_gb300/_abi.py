@@ -98,7 +98,7 @@ def load():
     lib.sg_mg_setup_times.restype = C.c_int
     lib.sg_mg_level_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     lib.sg_mg_level_info.restype = C.c_int
-    lib.sg_mg_set_level_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.sg_mg_set_level_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.sg_mg_set_level_variant.restype = C.c_int
     lib.sg_mg_patch_inverse.argtypes = [vp, C.c_int, C.c_int, C.c_longlong, C.POINTER(C.c_double)]
     lib.sg_mg_patch_inverse.restype = C.c_int

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_apply_f64.cu", "sg_apply_dw.cu", "sg_apply_f32.cu", "sg_mg.cu", "sg_vanka_factor.cu",
+SOURCES = ["sg_setup.cpp", "sg_apply.cu", "sg_apply_f64.cu", "sg_apply_dw.cu", "sg_apply_f32.cu", "sg_mg.cu", "sg_vanka_factor.cu", "sg_vanka_tc.cu",
            "sg_krylov.cu", "sg_noalloc.cu", "sg_manufactured.cu", "sg_mc.cu", "sg_mc_apply.cu", "sg_adjoint.cu", "sg_api.cu",
            "sg_debug.cu"]
 # the build with device bounds checks (-DSG_DEBUG_BOUNDS): libsg_debug.so
@@ -38,7 +38,7 @@ def _compile(src, verbose, debug_bounds=False):
         cmd[1:1] = ["-DSG_DEBUG_BOUNDS=1"]
     if src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
-    if src in ("sg_mg.cu", "sg_vanka_factor.cu", "sg_manufactured.cu", "sg_mc.cu"):
+    if src in ("sg_mg.cu", "sg_vanka_factor.cu", "sg_vanka_tc.cu", "sg_manufactured.cu", "sg_mc.cu"):
         cmd[1:1] = ["-Xcompiler", "-fopenmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -386,13 +386,15 @@ sg_status sg_mg_setup_times(sg_ctx* ctx, double* total_ms, double* factor_ms, do
   return SG_OK;
 }
 
-sg_status sg_mg_set_level_variant(sg_ctx* ctx, int level, int residual_kind, int vanka_chunk, int vanka_tile) {
+sg_status sg_mg_set_level_variant(sg_ctx* ctx, int level, int residual_kind, int vanka_chunk, int vanka_tile,
+                                  int vanka_kind) {
   if (!ctx) return fail(SG_ERR_ARG, "sg_mg_set_level_variant: ctx is NULL");
   if (!ctx->mg) return fail(SG_ERR_ARG, "sg_mg_set_level_variant: call sg_mg_setup first");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "sg_mg_set_level_variant: synchronize");
   std::string msg;
-  const sg_status st = sg::mg_force_variant(*ctx->mg, level, residual_kind, vanka_chunk, vanka_tile, msg);
+  const sg_status st =
+      sg::mg_force_variant(*ctx->mg, level, residual_kind, vanka_chunk, vanka_tile, vanka_kind, msg);
   ++ctx->gen;
   return st == SG_OK ? SG_OK : fail(st, "sg_mg_set_level_variant: " + msg);
 }

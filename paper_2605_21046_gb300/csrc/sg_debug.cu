@@ -15,6 +15,7 @@ cudaError_t bounds_fetch_mc_apply(BoundsRecord* out, bool clear);
 cudaError_t bounds_fetch_mg(BoundsRecord* out, bool clear);
 cudaError_t bounds_fetch_factor(BoundsRecord* out, bool clear);
 cudaError_t bounds_fetch_debug(BoundsRecord* out, bool clear);
+cudaError_t bounds_fetch_vanka_tc(BoundsRecord* out, bool clear);
 }  // namespace sg
 
 namespace {
@@ -49,7 +50,7 @@ sg_status sg_debug_bounds(int* enabled, unsigned int* count, int* site, long lon
   if (e != cudaSuccess) return fail(SG_ERR_CUDA, "sg_debug_bounds: synchronize failed");
   cudaError_t (*const fetch[])(sg::BoundsRecord*, bool) = {
       sg::bounds_fetch_apply_f64, sg::bounds_fetch_apply_dw, sg::bounds_fetch_apply_f32, sg::bounds_fetch_mc_apply,
-      sg::bounds_fetch_mg,        sg::bounds_fetch_factor,   sg::bounds_fetch_debug};
+      sg::bounds_fetch_mg,        sg::bounds_fetch_factor,   sg::bounds_fetch_debug, sg::bounds_fetch_vanka_tc};
   for (auto f : fetch) {
     sg::BoundsRecord r;
     if (f(&r, true) != cudaSuccess) return fail(SG_ERR_CUDA, "sg_debug_bounds: reading a record failed");

@@ -216,6 +216,7 @@ struct MGLevel {
                              //  bf16 when MG::bf16), or coarsest [class][n_int][n_int]
   int vanka_chunk = 0;       // cells per Vanka chunk
   int vanka_tile = 0;        // modes per Vanka tile on this level (0: the multigrid's tile)
+  int vanka_kind = 0;        // Vanka sweep: 0 FFMA kernel, 1 tensor-core kernel (bf16 factors)
   int* d_inner = nullptr;    // coarsest: dof offset (i * n_x + node) of every interior dof
   void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
   void* d_b = nullptr;
@@ -257,6 +258,7 @@ struct MG {
   cudaGraphExec_t exec_t[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
   double factor_ms = 0.0;         // Vanka patch factorisation (device, all levels)
+  int* d_status = nullptr;        // kernel status word (SG_ERR_TIMEOUT from a bounded wait)
   double tune_ms = 0.0;           // timing of the level residual and Vanka variants
 };
 
@@ -273,15 +275,25 @@ size_t krylov_bytes(long long N, int m);
 void mg_free(MG& mg);
 // Per-level choices of a built multigrid: info = {levels, cells, coarsest,
 // residual (0 SG cell kernel, 1 diagonal apply, -1 none), Vanka cells per
-// chunk, Vanka modes per tile, patch size, diagonal classes}.
-sg_status mg_level_info(const MG& mg, int level, int info[8], std::string& msg);
+// chunk, Vanka modes per tile, patch size, diagonal classes, Vanka kernel
+// (0 FFMA, 1 tensor cores), 0}.
+sg_status mg_level_info(const MG& mg, int level, int info[10], std::string& msg);
 // Forces the level residual kind (-1 keep, 0 cell kernel, 1 diagonal apply),
-// the Vanka cells per chunk (0 keep) and modes per tile (-1 keep, 0 all) on
-// one smoothed level (or every one with level = -1); drops the captured graphs.
-sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int tile, std::string& msg);
+// the Vanka cells per chunk (0 keep), modes per tile (-1 keep, 0 all) and
+// Vanka kernel (-1 keep, 0 FFMA, 1 tensor cores) on one smoothed level (or
+// every one with level = -1); drops the captured graphs.
+sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int tile, int kind, std::string& msg);
 // The stored inverse of the Vanka patch of (mode alpha's class, cell) on a
 // smoothed level, as np x np doubles (host).
 sg_status mg_patch_inverse(const MG& mg, int level, int alpha, long long cell, double* out, std::string& msg);
+// The tensor-core Vanka sweep (bf16 patch inverses, FP32 vectors, one diagonal
+// class): whether a level shape and tile can take it, its shared memory per
+// CTA, the kernel attributes, and one forward sweep.
+bool vanka_tc_eligible(int dim, int k, int nt, int tile_slots);
+size_t vanka_tc_smem(int dim, int k, int nt, int chunk, int tile_slots);
+cudaError_t prepare_vanka_tc(int dim, int k, int nt);
+cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, const void* inv, const int* blk_alpha,
+                            int n_blk, int chunk, int tile_slots, int* status, float omega, cudaStream_t s);
 // Vanka patch inverses of one multigrid level, assembled and inverted in FP64
 // on the device (Gauss-Jordan, partial pivoting) for every class and cell:
 // out[class][cell][np][npp] as double (out_kind 0), float (1) or bf16 (2).

@@ -979,9 +979,20 @@ cudaError_t prepare_vanka(int dim, int k, int nt, bool f32, bool bf16) {
 template <typename T, int DIM, int K, int NT>
 cudaError_t launch_vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   if constexpr (std::is_same<T, float>::value) {
+    if (mg.bf16 && L.vanka_kind == 1 && !trans) {
+      const int tile = L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile;
+      return launch_vanka_tc(L.hp, static_cast<const float*>(L.d_r), static_cast<float*>(L.d_x), L.d_inv,
+                             mg.d_blk_alpha, mg.n_blk, L.vanka_chunk, tile, mg.d_status, (float)mg.omega, s);
+    }
     if (mg.bf16) return launch_vanka_w<T, __nv_bfloat16, DIM, K, NT>(mg, L, s, trans);
   }
   return launch_vanka_w<T, T, DIM, K, NT>(mg, L, s, trans);
+}
+
+// The tensor-core sweep applies to this level: bf16 factors, one diagonal
+// class, a patch within the MMA's K extent, tiles of at most 40 slots.
+bool tc_level_ok(const MG& mg, const MGLevel& L, int tile) {
+  return mg.bf16 && mg.n_classes == 1 && !L.coarsest && vanka_tc_eligible(L.hp.dim, L.hp.k, L.hp.n_t, tile);
 }
 
 template <typename T>
@@ -1224,6 +1235,40 @@ static cudaError_t tune_vanka(MG& mg) {
     }
     L.vanka_chunk = best_c;
     L.vanka_tile = best_t;
+    L.vanka_kind = 0;
+    // the tensor-core sweep over its chunk sizes, where it applies; kept if faster
+    const int tile_all = mg.vanka_tile;
+    if (e == cudaSuccess && tc_level_ok(mg, L, tile_all)) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      int tc_c = 0;
+      float tc_ms = 1e30f;
+      for (int c : {1, 2, 4}) {
+        if (e != cudaSuccess || c > L.hp.cells[0]) break;
+        if (vanka_tc_smem(L.hp.dim, L.hp.k, L.hp.n_t, c, std::min(tile_all, mg.n_blk * kVankaVB)) >
+            (size_t)optin - 1024)
+          break;
+        L.vanka_chunk = c;
+        L.vanka_tile = 0;
+        L.vanka_kind = 1;
+        const float ms = time_candidate(
+            [&]() { return vk_launch(mg, L, mg.stream) ? cudaSuccess : cudaErrorInvalidValue; }, mg.stream, a, b, e);
+        if (e == cudaSuccess && ms < tc_ms) {
+          tc_ms = ms;
+          tc_c = c;
+        }
+      }
+      if (tc_c > 0 && tc_ms < best_ms) {
+        L.vanka_chunk = tc_c;
+        L.vanka_tile = 0;
+        L.vanka_kind = 1;
+      } else {
+        L.vanka_chunk = best_c;
+        L.vanka_tile = best_t;
+        L.vanka_kind = 0;
+      }
+    }
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
@@ -1242,7 +1287,9 @@ void mg_free(MG& mg) {
   cudaFree(mg.d_blk_cls);
   cudaFree(mg.d_blk_alpha);
   cudaFree(mg.d_wgt);
+  cudaFree(mg.d_status);
   mg.d_wgt = nullptr;
+  mg.d_status = nullptr;
   mg.d_blk_cls = mg.d_blk_alpha = nullptr;
   for (MGLevel& L : mg.lv) {
     cudaFree(L.d_ctab); cudaFree(L.d_grow); cudaFree(L.d_gcol); cudaFree(L.d_gterm); cudaFree(L.d_gval);
@@ -1428,6 +1475,7 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
         return SG_ERR_UNSUPPORTED;
       }
       if ((e = prepare_vanka(L.hp.dim, L.hp.k, L.hp.n_t, precision == kPrecF32, mg.bf16)) != cudaSuccess) break;
+      if (mg.bf16 && (e = prepare_vanka_tc(L.hp.dim, L.hp.k, L.hp.n_t)) != cudaSuccess) break;
     }
     if ((e = upload_vec(&L.d_grow, L.hp.g.row)) != cudaSuccess) break;
     if ((e = upload_vec(&L.d_gcol, L.hp.g.col)) != cudaSuccess) break;
@@ -1474,11 +1522,21 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
   if (e == cudaSuccess) e = upload_vec(&mg.d_cls, mg.cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_cls, blk_cls);
   if (e == cudaSuccess) e = upload_vec(&mg.d_blk_alpha, blk_alpha);
+  if (e == cudaSuccess) e = cudaMalloc(&mg.d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(mg.d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mg.stream, cudaStreamNonBlocking);
   const auto tt = std::chrono::steady_clock::now();
   if (e == cudaSuccess) e = tune_level_applies(mg);
   if (e == cudaSuccess) e = tune_vanka(mg);
   mg.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tt).count();
+  if (e == cudaSuccess) {
+    int status = 0;
+    e = cudaMemcpy(&status, mg.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && status != 0) {
+      msg = "multigrid set-up: a tensor-core Vanka sweep timed out waiting for its MMAs";
+      return SG_ERR_TIMEOUT;
+    }
+  }
   if (e != cudaSuccess) {
     msg = std::string("multigrid set-up: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
@@ -1506,7 +1564,7 @@ sg_status mg_build_mc(const HostProblem& fine, int precision, int nu, double ome
   return mg_build(fine, precision, nu, omega, mg, msg, true);
 }
 
-sg_status mg_level_info(const MG& mg, int level, int info[8], std::string& msg) {
+sg_status mg_level_info(const MG& mg, int level, int info[10], std::string& msg) {
   if (level < 0 || level >= (int)mg.lv.size()) {
     msg = "level out of range";
     return SG_ERR_ARG;
@@ -1520,15 +1578,17 @@ sg_status mg_level_info(const MG& mg, int level, int info[8], std::string& msg) 
   info[5] = L.coarsest ? 0 : (L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile);
   info[6] = L.np;
   info[7] = mg.n_classes;
+  info[8] = L.coarsest ? 0 : L.vanka_kind;
+  info[9] = 0;
   return SG_OK;
 }
 
-sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int tile, std::string& msg) {
+sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int tile, int kind, std::string& msg) {
   if (level < -1 || level >= (int)mg.lv.size()) {
     msg = "level out of range";
     return SG_ERR_ARG;
   }
-  if (residual_kind < -1 || residual_kind > 1 || chunk < 0 || chunk > 8 || tile < -1) {
+  if (residual_kind < -1 || residual_kind > 1 || chunk < 0 || chunk > 8 || tile < -1 || kind < -1 || kind > 1) {
     msg = "variant out of range";
     return SG_ERR_ARG;
   }
@@ -1558,7 +1618,18 @@ sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int 
         return SG_ERR_ARG;
       }
       const int c = chunk > 0 ? std::min(chunk, L.hp.cells[0]) : L.vanka_chunk;
-      if (vanka_smem(L, mg.n_blk, t, c, vb, inv_value_bytes(mg)) > (size_t)optin - 1024) {
+      const int kd = kind >= 0 ? kind : L.vanka_kind;
+      if (kd == 1) {
+        if (!tc_level_ok(mg, L, t)) {
+          msg = "the tensor-core Vanka sweep needs bf16 factors, one diagonal class, a patch of at most 64 and "
+                "at most 40 slots per tile";
+          return SG_ERR_UNSUPPORTED;
+        }
+        if (vanka_tc_smem(L.hp.dim, L.hp.k, L.hp.n_t, c, std::min(t, mg.n_blk * kVankaVB)) > (size_t)optin - 1024) {
+          msg = "Vanka chunk does not fit in shared memory";
+          return SG_ERR_UNSUPPORTED;
+        }
+      } else if (vanka_smem(L, mg.n_blk, t, c, vb, inv_value_bytes(mg)) > (size_t)optin - 1024) {
         msg = "Vanka chunk does not fit in shared memory";
         return SG_ERR_UNSUPPORTED;
       }
@@ -1566,6 +1637,7 @@ sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int 
         if (residual_kind >= 0) L.use_diag = residual_kind == 1;
         L.vanka_chunk = c;
         L.vanka_tile = t == mg.vanka_tile ? 0 : t;
+        L.vanka_kind = kd;
       }
     }
   }

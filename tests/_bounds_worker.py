@@ -59,8 +59,11 @@ def main():
         for res in (0, 1):
             for chunk in (1, 3, 8):
                 for tile in (0, 4):
-                    sg.sg_mg_set_level_variant(ctx, -1, res, chunk, tile)
+                    sg.sg_mg_set_level_variant(ctx, -1, res, chunk, tile, 0)
                     sg.sg_vcycle(ctx, r, z)
+                    if prec == sg.SG_PREC_BF16 and chunk <= 4:
+                        sg.sg_mg_set_level_variant(ctx, -1, res, chunk, tile, 1)     # tensor-core sweep
+                        sg.sg_vcycle(ctx, r, z)
         b = torch.rand(n, dtype=torch.float64, device="cuda")
         x = torch.zeros_like(b)
         sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-8)

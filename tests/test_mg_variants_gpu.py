@@ -12,6 +12,10 @@ Vanka patch factors, against the oracle (oracle/solver.py), through the C ABI.
   timing.  Every variant is forced in turn on meshes whose smoothed levels
   have >= 256 cells and the V-cycle must still equal the oracle's (1e-10 FP64,
   1e-4 FP32).
+* The tensor-core Vanka sweep (bf16 factors; tcgen05 MMAs with the patch
+  values split into three bf16 terms) gives the same V-cycle as the oracle's
+  with bf16-rounded factors (1e-4), for every chunk size, in 2D and 3D, Q2 and
+  Q3 / dG(3) (64-unknown patches).
 * A 3D 16^3 Q2 solve (M = 3, P = 3, 1.44 M unknowns) reaches 1e-8 in true
   residual, evaluated by the oracle's assembled operator."""
 import functools
@@ -177,6 +181,62 @@ def test_vcycle_variants_match_oracle(cuda, name, variant, prec):
     tol = 1e-10 if prec == "fp64" else 1e-4
     err = float(np.abs(got - want).max() / np.abs(want).max())
     assert err < tol, err
+
+
+TC_CASES = {
+    "2d-q2-32x32-M3P3": spec2((32, 32)),
+    "2d-q2-16x16-M4P3": spec2((16, 16), M=4, P=3),
+    "2d-q3-dg3-8x8-M2P2": spec2((8, 8), k=3, r=3, M=2, P=2),
+    "3d-q2-8x8x8-M3P2": spec3((8, 8, 8)),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_vcycle_bf16(name, seed=10):
+    spec = TC_CASES[name]
+    p = operator.SGProblem(spec)
+    r = np.random.default_rng(seed).uniform(-1, 1, p.shape)
+    return r, solver.Multigrid(p, factor_round=solver.round_bf16).apply(r).reshape(-1)
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["ffma", "tensor"])
+@pytest.mark.parametrize("chunk", [1, 2, 4])
+@pytest.mark.parametrize("name", list(TC_CASES))
+def test_vcycle_bf16_sweeps_match_oracle(cuda, name, chunk, kind):
+    torch = cuda
+    spec = TC_CASES[name]
+    r, want = _oracle_vcycle_bf16(name)
+    ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_setup(ctx, sg.SG_PREC_BF16)
+    sg.sg_mg_set_level_variant(ctx, -1, -1, chunk, 0, kind)
+    levels = sg.sg_mg_level_info(ctx, 0)["levels"]
+    for lev in range(levels - 1):
+        assert sg.sg_mg_level_info(ctx, lev)["vanka_kind"] == kind
+    rd = torch.from_numpy(r.reshape(-1).copy()).cuda()
+    zd = torch.full_like(rd, float("nan"))
+    sg.sg_vcycle(ctx, rd, zd)
+    z2 = torch.empty_like(rd)
+    sg.sg_vcycle(ctx, rd, z2)                      # graph replay: the same map
+    torch.cuda.synchronize()
+    got = zd.cpu().numpy()
+    ctx.destroy()
+    err = float(np.abs(got - want).max() / np.abs(want).max())
+    assert err < 1e-4, err
+    assert float(np.abs(z2.cpu().numpy() - got).max() / np.abs(got).max()) < 1e-6
+
+
+def test_tensor_core_sweep_refuses_unsupported_levels(cuda):
+    # FP32 factors, and bf16 factors of several diagonal classes, keep the FFMA sweep
+    ctx = sg.sg_setup_spec(spec2((8, 8)))
+    sg.sg_mg_setup(ctx, sg.SG_PREC_FP32)
+    with pytest.raises(sg.SGError):
+        sg.sg_mg_set_level_variant(ctx, -1, -1, 0, -1, 1)
+    ctx.destroy()
+    ctx = sg.sg_setup_spec(spec2((4, 4), M=4, P=2, lo=(-1.0, -1.0), coef=paper_coefficient()))
+    sg.sg_mg_setup(ctx, sg.SG_PREC_BF16)
+    with pytest.raises(sg.SGError):
+        sg.sg_mg_set_level_variant(ctx, -1, -1, 0, -1, 1)
+    ctx.destroy()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])

@@ -1113,9 +1113,11 @@ static float time_candidate(F&& launch, cudaStream_t s, cudaEvent_t a, cudaEvent
 }
 
 // Picks, for every smoothed level of at least 256 cells, the faster residual
-// apply on the level's own buffers: the diagonal apply over (rows per tile x
-// cells per chunk) or, where it applies, the SG cell kernel over (cells per
-// chunk x threads).  Smaller levels keep the SG cell kernel where it applies.
+// apply on the level's own buffers: the diagonal apply over (rows per tile in
+// {8, 32, all} x at most 8 or 2 cells per chunk) or, where it applies, the SG
+// cell kernel over (cells per chunk x 256 / 512 threads), then the staggered
+// first chunk of the best cell-kernel shape.  Smaller levels keep the SG cell
+// kernel where it applies.
 static cudaError_t tune_level_applies(MG& mg) {
   const size_t vb = mg.precision == kPrecF32 ? 4 : 8;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -1132,7 +1134,7 @@ static cudaError_t tune_level_applies(MG& mg) {
     if ((e = cudaMemsetAsync(L.d_x, 0, n * vb, mg.stream)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(L.d_b, 0, n * vb, mg.stream)) != cudaSuccess) break;
     std::vector<int> tss;
-    for (int t : {8, 16, 32, 64, L.hp.n_xi})
+    for (int t : {8, 32, L.hp.n_xi})
       if (t <= L.hp.n_xi && std::find(tss.begin(), tss.end(), t) == tss.end()) tss.push_back(t);
     int best_ts = L.mc_ts, best_c = 8;
     float best_ms = 1e30f;
@@ -1140,7 +1142,7 @@ static cudaError_t tune_level_applies(MG& mg) {
     LaunchShape best_ls = L.ls;
     L.use_diag = true;
     for (int ts : tss) {
-      for (int cmax : {8, 4, 2}) {
+      for (int cmax : {8, 2}) {
         if (e != cudaSuccess) break;
         if (level_diag_shape(L, ts, cmax, (int)vb) != SG_OK) continue;
         if (L.mc_chunk != cmax && cmax != 8) continue;           // the same shape as a larger cap
@@ -1163,22 +1165,32 @@ static cudaError_t tune_level_applies(MG& mg) {
       for (int c = max1; c >= 1; c = c > 1 ? (c + 1) / 2 - (c == 2) : 0) chunks.push_back(c);
       L.use_diag = false;
       const LaunchShape keep = L.ls;
+      // (cells per chunk x threads), then the staggered first chunk of the best
       for (int c : chunks)
-        for (int t : {128, 256, 384, 512})
-          for (int staggered = 0; staggered < (c > 1 ? 2 : 1); ++staggered) {
-            if (e != cudaSuccess) break;
-            LaunchShape ls;
-            std::string msg;
-            if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
-            ls.stagger = staggered ? (c + 1) / 2 : 0;
-            L.ls = ls;
-            const float ms = time_candidate(res, mg.stream, a, b, e);
-            if (e == cudaSuccess && ms < best_ms) {
-              best_ms = ms;
-              best_diag = false;
-              best_ls = ls;
-            }
+        for (int t : {256, 512}) {
+          if (e != cudaSuccess) break;
+          LaunchShape ls;
+          std::string msg;
+          if (plan_apply_shape(L.hp, c, t, ls, msg) != SG_OK) continue;
+          ls.stagger = 0;
+          L.ls = ls;
+          const float ms = time_candidate(res, mg.stream, a, b, e);
+          if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best_diag = false;
+            best_ls = ls;
           }
+        }
+      if (!best_diag && best_ls.chunk > 1 && e == cudaSuccess) {
+        LaunchShape ls = best_ls;
+        ls.stagger = (ls.chunk + 1) / 2;
+        L.ls = ls;
+        const float ms = time_candidate(res, mg.stream, a, b, e);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best_ls = ls;
+        }
+      }
       L.ls = best_diag ? keep : best_ls;
     }
     L.use_diag = best_diag;

@@ -862,9 +862,10 @@ def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32"):
                 row[f"{pname}_nu{nu}"] = a.elapsed_time(b) / 10
                 if prec == sg.SG_PREC_BF16 and nu == MG_NU:
                     # the same V-cycle with each Vanka sweep forced on every level
-                    for kname, kind in (("ffma", 0), ("tensor", 1)):
+                    # (the tensor-core sweep with one and with two staging buffers)
+                    for kname, kind, chunk in (("ffma", 0, 0), ("tensor_1buf", 1, 1), ("tensor_2buf", 1, 2)):
                         try:
-                            sg.sg_mg_set_level_variant(ctx, -1, -1, 0, -1, kind)
+                            sg.sg_mg_set_level_variant(ctx, -1, -1, chunk, -1, kind)
                         except sg.SGError:
                             continue
                         for _ in range(3):
@@ -877,10 +878,10 @@ def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32"):
                         torch.cuda.synchronize()
                         row[f"{pname}_nu{nu}_vanka_{kname}"] = a.elapsed_time(b) / 10
         if profile_range and wname.startswith("3d"):
-            sg.sg_mg_setup(ctx, sg.SG_PREC_BF16 if profile_mg in ("bf16", "bf16-tensor") else sg.SG_PREC_FP32,
+            sg.sg_mg_setup(ctx, sg.SG_PREC_BF16 if profile_mg.startswith("bf16") else sg.SG_PREC_FP32,
                            MG_NU, MG_OMEGA)
-            if profile_mg == "bf16-tensor":
-                sg.sg_mg_set_level_variant(ctx, -1, -1, 0, -1, 1)
+            if profile_mg in ("bf16-tensor", "bf16-tensor-1buf"):
+                sg.sg_mg_set_level_variant(ctx, -1, -1, 1 if profile_mg.endswith("1buf") else 2, -1, 1)
             row["profiled_levels"] = [sg.sg_mg_level_info(ctx, lev) for lev in range(sg.sg_mg_level_info(ctx, 0)["levels"])]
             sg.sg_vcycle(ctx, r, z)
             torch.cuda.synchronize()
@@ -942,7 +943,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--profile-variant", choices=["fp64", "dw"], default="fp64",
                     help="which timed apply loop --profile-range brackets")
-    ap.add_argument("--profile-mg", choices=["fp32", "bf16", "bf16-tensor"], default="fp32",
+    ap.add_argument("--profile-mg", choices=["fp32", "bf16", "bf16-tensor", "bf16-tensor-1buf"], default="fp32",
                     help="multigrid precision of the V-cycle --profile-range brackets (--rows vcycle)")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the NEXT rows (mixed precision, Monte-Carlo vs SG, adjoint) of the default line")

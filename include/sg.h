@@ -243,7 +243,8 @@ sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega);
  * (0 = finest).  info: HOST int[10] out = {number of levels, cells, 1 if the
  * coarsest (dense) level, level residual (0 the SG cell kernel with the
  * diagonal coupling table, 1 the diagonal apply, -1 none on the coarsest),
- * Vanka cells per shared-memory chunk, Vanka chaos modes per tile, patch size
+ * Vanka cells per shared-memory chunk (tensor-core sweep: staging buffers),
+ * Vanka chaos modes per tile, patch size
  * N_t (k+1)^d, diagonal classes, Vanka kernel (0 FFMA, 1 tensor cores),
  * reserved 0}.  SG_ERR_ARG without sg_mg_setup or for a level out of range. */
 sg_status sg_mg_level_info(sg_ctx* ctx, int level, int* info);
@@ -257,10 +258,12 @@ sg_status sg_mg_setup_times(sg_ctx* ctx, double* total_ms, double* factor_ms, do
 /* sg_mg_set_level_variant - replace set-up's timed choices on one smoothed
  * level (level >= 0) or on all of them (level = -1): residual_kind -1 keeps,
  * 0 forces the SG cell kernel, 1 the diagonal apply; vanka_chunk 0 keeps, else
- * 1..8 cells per chunk; vanka_tile -1 keeps, 0 all modes, else a multiple of 4
- * modes; vanka_kind -1 keeps, 0 the FFMA sweep, 1 the tensor-core sweep
- * (SG_PREC_BF16 factors, one diagonal class, patches of at most 64 unknowns,
- * at most 40 modes per tile; the transposed V-cycle keeps the FFMA sweep).
+ * 1..8 cells per chunk (the tensor-core sweep works on pairs of cells and
+ * reads it as 1 or 2 staging buffers, larger values as 2); vanka_tile -1
+ * keeps, 0 all modes, else a multiple of 4 modes; vanka_kind -1 keeps, 0 the
+ * FFMA sweep, 1 the tensor-core sweep (SG_PREC_BF16 factors, one diagonal
+ * class, patches of at most 64 unknowns, at most 80 modes per tile; the
+ * transposed V-cycle keeps the FFMA sweep).
  * The results stay the same up to rounding (the variants compute the same
  * V-cycle).  The next sg_vcycle records a new graph.  SG_ERR_ARG /
  * SG_ERR_UNSUPPORTED (nothing changed) when a level cannot take the variant.

@@ -86,7 +86,7 @@ size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int coef_rows, int nn
                         int value_bytes, bool premul) {
   const size_t nqd = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
   const size_t V = (size_t)n_xi * n_t;
-  size_t vals = (size_t)chunk * V * (1 + dim) * nqd      // Qs
+  size_t vals = (size_t)chunk * V * (((1 + dim) * nqd) | 1)   // Qs (odd slot pitch)
                 + (size_t)chunk * coef_rows * nqd        // Cs
                 + nqd * n_t * n_t                        // Amq
                 + n_t + 3                                // Tb, Rt

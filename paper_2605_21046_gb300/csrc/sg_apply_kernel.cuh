@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
   using T = typename A::T;
   using Sh = Shape<DIM, K>;
   constexpr int NQD = Sh::NQD, NKD = Sh::NKD, NC = Sh::NC, N = Sh::N;
-  constexpr int SLOT = NC * NQD;                 // values per (cell, vector)
+  constexpr int SLOT = (NC * NQD) | 1;           // values per (cell, vector), odd pitch: no bank conflicts
+                                                 // between the vectors of phases 1 and 3
   using IO = typename A::IO;
   const IO* __restrict__ xin = reinterpret_cast<const IO*>(p.x);
   IO* __restrict__ yout = reinterpret_cast<IO*>(p.y);

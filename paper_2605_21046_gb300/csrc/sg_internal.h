@@ -217,6 +217,7 @@ struct MGLevel {
   int vanka_chunk = 0;       // cells per Vanka chunk
   int vanka_tile = 0;        // modes per Vanka tile on this level (0: the multigrid's tile)
   int vanka_kind = 0;        // Vanka sweep: 0 FFMA kernel, 1 tensor-core kernel (bf16 factors)
+  int ffma_chunk = 0, ffma_tile = 0;   // the FFMA sweep's timed choice (kept while the other sweep runs)
   int* d_inner = nullptr;    // coarsest: dof offset (i * n_x + node) of every interior dof
   void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
   void* d_b = nullptr;
@@ -232,6 +233,10 @@ struct MGLevel {
   int* d_rptr[3] = {nullptr, nullptr, nullptr};
   int* d_ridx[3] = {nullptr, nullptr, nullptr};
   void* d_rw[3] = {nullptr, nullptr, nullptr};
+  int pnnz[3] = {0, 0, 0};    // entries of the interpolation / restriction lists
+  int rnnz[3] = {0, 0, 0};
+  int pmax[3] = {0, 0, 0};    // the longest list of each
+  int rmax[3] = {0, 0, 0};
   void* d_t1 = nullptr;
   void* d_t2 = nullptr;
 };
@@ -290,10 +295,10 @@ sg_status mg_patch_inverse(const MG& mg, int level, int alpha, long long cell, d
 // class): whether a level shape and tile can take it, its shared memory per
 // CTA, the kernel attributes, and one forward sweep.
 bool vanka_tc_eligible(int dim, int k, int nt, int tile_slots);
-size_t vanka_tc_smem(int dim, int k, int nt, int chunk, int tile_slots);
+size_t vanka_tc_smem(int dim, int k, int nt, int stages, int tile_slots);
 cudaError_t prepare_vanka_tc(int dim, int k, int nt);
 cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, const void* inv, const int* blk_alpha,
-                            int n_blk, int chunk, int tile_slots, int* status, float omega, cudaStream_t s);
+                            int n_blk, int stages, int tile_slots, int* status, float omega, cudaStream_t s);
 // Vanka patch inverses of one multigrid level, assembled and inverted in FP64
 // on the device (Gauss-Jordan, partial pivoting) for every class and cell:
 // out[class][cell][np][npp] as double (out_kind 0), float (1) or bf16 (2).

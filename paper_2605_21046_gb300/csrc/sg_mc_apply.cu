@@ -18,29 +18,11 @@
 #include <vector>
 
 #include "sg_apply_kernel.cuh"
+#include "sg_vec.cuh"
 
 namespace sg {
 
 namespace {
-
-template <typename IO>
-__global__ void mc_init_y(const IO* __restrict__ x, IO* y, const IO* b, int mode, int n_x, int nnx, int nny,
-                          int nnz, int dim) {
-  const long long off = (long long)blockIdx.y * n_x;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
-    const long long idx = off + m;
-    if (mode == kApplyAccumulate) {
-      y[idx] = b[idx];
-      continue;
-    }
-    const int ix = m % nnx, r = m / nnx;
-    const int iy = r % nny, iz = r / nny;
-    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
-    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    const IO v = bd ? x[idx] : IO(0);
-    y[idx] = mode == kApplyResidual ? b[idx] - v : v;
-  }
-}
 
 template <class A, int DIM, int K, int NT>
 __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
@@ -48,7 +30,7 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
   using IO = typename A::IO;
   using Sh = Shape<DIM, K>;
   constexpr int NQD = Sh::NQD, NKD = Sh::NKD, NC = Sh::NC, N = Sh::N;
-  constexpr int SLOT = NC * NQD;
+  constexpr int SLOT = (NC * NQD) | 1;   // values of one (cell, vector), odd pitch: no bank conflicts between them
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int C = p.chunk, nterm = p.n_terms;
@@ -58,7 +40,9 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
   T* Cs = Qs + (size_t)C * ts_max * NT * SLOT;                  // [C][term][NQD]
   T* Wt = Cs + (size_t)C * nterm * NQD;                         // [ts][term]
   T* Amq = Wt + (size_t)ts_max * nterm;                         // [NQD][NT][NT]
-  int* Nd = reinterpret_cast<int*>(Amq + NQD * NT * NT);        // [C][NKD] node, -1 on the boundary
+  T* Tbs = Amq + NQD * NT * NT;                                 // [NT] tau Bhat_ii, converted once
+  int* Nd = reinterpret_cast<int*>(Tbs + NT);                   // [C][NKD] node, -1 on the boundary
+  if (tid < NT) Tbs[tid] = A::in(p.tb[tid]);
   const long long u_begin = (long long)blockIdx.x * p.units / gridDim.x;
   const long long u_end = (long long)(blockIdx.x + 1) * p.units / gridDim.x;
   int cur_prob = -1, cur_tile = -1;
@@ -120,11 +104,12 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
       forward_cell<A, DIM, K>(uv, q);
     }
     __syncthreads();
-    // phase 2: per (cell, point, sample): mass coupling and a(x_q, xi_s) grad u
+    // phase 2: per (cell, point, sample): mass coupling and a(x_q, xi_s) grad u;
+    // (point, sample, cell) of the item index advance with the stride (no
+    // divisions in the loop)
+    const int dq = nthr % NQD, dr = nthr / NQD;
+    int q = tid % NQD, sl = (tid / NQD) % ns, c = (tid / NQD) / ns;
     for (int it = tid; it < nc * NQD * ns; it += nthr) {
-      const int q = it % NQD;
-      const int rest = it / NQD;
-      const int sl = rest % ns, c = rest / ns;
       T* base = Qs + ((size_t)c * VT + (size_t)sl * NT) * SLOT + q;
       T uv[NT], out[NT][NC];
 #pragma unroll
@@ -159,6 +144,21 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
       for (int i = 0; i < NT; ++i)
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) base[(size_t)i * SLOT + cc * NQD] = out[i][cc];
+      q += dq;
+      sl += dr;
+      if (q >= NQD) {
+        q -= NQD;
+        ++sl;
+      }
+      if (sl >= ns) {
+        if (sl < 2 * ns) {
+          sl -= ns;
+          ++c;
+        } else {
+          c += sl / ns;
+          sl %= ns;
+        }
+      }
     }
     __syncthreads();
     // phase 3: back to the nodes
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
         const int v = j / NKD, a = j - v * NKD;
         const int node = nd[a];
         if (node >= 0 && SG_IN((long long)(s0 * NT + v) * P.n_x + node, (long long)P.S * NT * P.n_x, 403)) {
-          T val = A::mul(A::in(p.tb[v % NT]), qc[(size_t)v * SLOT + a]);
+          T val = A::mul(Tbs[v % NT], qc[(size_t)v * SLOT + a]);
           if (p.mode == kApplyResidual) val = A::neg(val);
           A::add_out(yout + (long long)(s0 * NT + v) * P.n_x + node, val);
         }
@@ -199,8 +199,9 @@ void* select_mc(int precision, int dim, int k, int n_t) {
 
 size_t mc_smem_bytes(int dim, int k, int n_t, int ts, int n_terms, int chunk, int value_bytes) {
   const size_t nqd = dim == 2 ? (k + 1) * (k + 1) : (k + 1) * (k + 1) * (k + 1);
-  const size_t vals = (size_t)chunk * ts * n_t * (1 + dim) * nqd + (size_t)chunk * n_terms * nqd +
-                      (size_t)ts * n_terms + nqd * n_t * n_t;
+  const size_t slot = ((1 + dim) * nqd) | 1;
+  const size_t vals = (size_t)chunk * ts * n_t * slot + (size_t)chunk * n_terms * nqd +
+                      (size_t)ts * n_terms + nqd * n_t * n_t + n_t;
   // values, then the chunk's node indices at a 4-byte boundary
   return ((vals * value_bytes + 3) / 4) * 4 + (size_t)chunk * nqd * sizeof(int);
 }
@@ -234,18 +235,18 @@ cudaError_t launch_mc_apply(int precision, int dim, int k, int n_t, const McPara
                             size_t smem, cudaStream_t s) {
   void* f = select_mc(precision, dim, k, n_t);
   if (!f) return cudaErrorInvalidValue;
+  // y's start: b (accumulate), b - x on the boundary and b inside (residual),
+  // x on the boundary and 0 inside (overwrite)
   for (int q = 0; q < p.n_prob; ++q) {
     const McProblem& P = p.pr[q];
-    const dim3 ig((unsigned)std::max<long long>(1, std::min<long long>((P.n_x + 255) / 256, 64)),
-                  (unsigned)(P.S * n_t));
+    const int V = P.S * n_t;
+    const int op = p.mode == kApplyResidual ? 1 : (p.mode == kApplyAccumulate ? 3 : 2);
     if (precision == kPrecF32)
-      mc_init_y<float><<<ig, 256, 0, s>>>(static_cast<const float*>(P.x), static_cast<float*>(P.y),
-                                          static_cast<const float*>(P.b), p.mode, (int)P.n_x, P.nn[0], P.nn[1],
-                                          P.nn[2], dim);
+      launch_vec_start<float>(static_cast<const float*>(P.b), static_cast<const float*>(P.x), static_cast<float*>(P.y),
+                              nullptr, op, V, P.n_x, P.nn, dim, s);
     else
-      mc_init_y<double><<<ig, 256, 0, s>>>(static_cast<const double*>(P.x), static_cast<double*>(P.y),
-                                           static_cast<const double*>(P.b), p.mode, (int)P.n_x, P.nn[0], P.nn[1],
-                                           P.nn[2], dim);
+      launch_vec_start<double>(static_cast<const double*>(P.b), static_cast<const double*>(P.x),
+                               static_cast<double*>(P.y), nullptr, op, V, P.n_x, P.nn, dim, s);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

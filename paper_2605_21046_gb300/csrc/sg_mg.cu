@@ -31,6 +31,7 @@
 
 #include "sg_bounds.h"
 #include "sg_internal.h"
+#include "sg_vec.cuh"
 
 namespace sg {
 
@@ -462,33 +463,73 @@ __global__ void __launch_bounds__(256, 2) mg_vanka(const VankaParams<T> p) {
 // with the 1D restriction lists (coarse node <- fine nodes) or the 1D
 // interpolation lists (fine node <- coarse nodes).  Restriction P^T and
 // prolongation P are d such passes (x, y, z resp. z, y, x), which read every
-// value a few times instead of (k+1)^d-fold per output.  blockIdx.y walks
-// the leading index, so the per-element index arithmetic stays 32-bit.
-template <typename T>
-__global__ void mg_axis_gather(const T* __restrict__ in, T* __restrict__ out, long long VA, int nin, int nout, int B,
-                               const int* __restrict__ ptr, const int* __restrict__ idx, const T* __restrict__ w,
-                               int accumulate) {
-  const int L = nout * B;
-  // short rows (L < blockDim): every block takes several rows, one element
-  // per thread; long rows: a row is strided over blockIdx.x
-  const bool shortrow = L < (int)blockDim.x;
-  const int rows = shortrow ? (int)blockDim.x / L : 1;
-  const int lr = shortrow ? (int)threadIdx.x / L : 0;
-  if (lr >= rows) return;
-  const int l_first = shortrow ? (int)threadIdx.x - lr * L : (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int l_step = shortrow ? L : (int)(gridDim.x * blockDim.x);
-  for (long long va = (long long)blockIdx.y * rows + lr; va < VA; va += (long long)gridDim.y * rows) {
-    const T* src = in + va * nin * (long long)B;
-    T* dst = out + va * L;
-    for (int l = l_first; l < L; l += l_step) {
-      const int jo = l / B, b = l - jo * B;
-      T s = T(0);
-      for (int t = ptr[jo]; t < ptr[jo + 1]; ++t) {
-        const int si = idx[t] * B + b;
-        if (SG_IN(si, (long long)nin * B, 501)) s += w[t] * src[si];
+// value a few times instead of (k+1)^d-fold per output.  The lists are staged
+// in shared memory (TAB_SMEM) or read where they are; each thread walks the
+// flat output index with a fixed stride, carrying (va, jo, b) along instead
+// of dividing for every element.
+constexpr int kAxisMax = 16;  // entries of one output of a 1D transfer list, at most (4k + 1 for k <= 3)
+
+template <typename T, bool TAB_SMEM, int MAXE>
+__global__ void __launch_bounds__(256) mg_axis_gather(const T* __restrict__ in, T* __restrict__ out, long long VA,
+                                                      int nin, int nout, int B, const int* __restrict__ ptr,
+                                                      const int* __restrict__ idx, const T* __restrict__ w, int nnz,
+                                                      int accumulate) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const T* tw = w;
+  const int* tidx = idx;
+  const int* tptr = ptr;
+  if constexpr (TAB_SMEM) {
+    T* sw = reinterpret_cast<T*>(sm_raw);
+    int* sidx = reinterpret_cast<int*>(sw + nnz);
+    int* sptr = sidx + nnz;
+    for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
+      sw[i] = w[i];
+      sidx[i] = idx[i];
+    }
+    for (int i = threadIdx.x; i <= nout; i += blockDim.x) sptr[i] = ptr[i];
+    __syncthreads();
+    tw = sw;
+    tidx = sidx;
+    tptr = sptr;
+  }
+  const long long total = VA * nout * B;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int b = (int)(e % B);
+  long long r = e / B;
+  int jo = (int)(r % nout);
+  long long va = r / nout;
+  const int db = (int)(stride % B);
+  const long long rs = stride / B;
+  const int djo = (int)(rs % nout);
+  const long long dva = rs / nout;
+  const long long row_in = (long long)nin * B;
+  for (; e < total; e += stride) {
+    const T* src = in + va * row_in + b;
+    T acc = T(0);
+    const int t0 = tptr[jo], cnt = tptr[jo + 1] - t0;
+    // at most MAXE entries: unrolled, so the loads of one output are in
+    // flight together
+#pragma unroll
+    for (int k = 0; k < MAXE; ++k) {
+      if (k < cnt) {
+        const int si = tidx[t0 + k];
+        if (SG_IN(si, nin, 501)) acc += tw[t0 + k] * src[(long long)si * B];
       }
-      if (accumulate) dst[l] += s;
-      else dst[l] = s;
+    }
+    if (accumulate) out[e] += acc;
+    else out[e] = acc;
+    b += db;
+    jo += djo;
+    va += dva;
+    if (b >= B) {
+      b -= B;
+      ++jo;
+    }
+    if (jo >= nout) {
+      jo -= nout;
+      ++va;
     }
   }
 }
@@ -849,20 +890,6 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
 
 // The initial iterate (x = b on Dirichlet dofs, 0 inside) and its residual
 // (r = b inside, 0 on Dirichlet dofs) in one pass, without an apply.
-template <typename T>
-__global__ void mg_start(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, int n_x, int nnx, int nny,
-                         int nnz, int dim) {
-  const long long off = (long long)blockIdx.y * n_x;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
-    const int ix = m % nnx, rr = m / nnx, iy = rr % nny, iz = rr / nny;
-    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
-    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    const T v = b[off + m];
-    x[off + m] = bd ? v : T(0);
-    r[off + m] = bd ? T(0) : v;
-  }
-}
-
 // Tile (rows) and chunk (cells) of a level's diagonal apply: the largest
 // chunk <= max_chunk within 100 KB of shared memory; the grid covers the units.
 sg_status level_diag_shape(MGLevel& L, int ts, int max_chunk, int vb) {
@@ -990,7 +1017,7 @@ cudaError_t launch_vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
 }
 
 // The tensor-core sweep applies to this level: bf16 factors, one diagonal
-// class, a patch within the MMA's K extent, tiles of at most 40 slots.
+// class, a patch of at most 64 unknowns, tiles of at most 80 slots.
 bool tc_level_ok(const MG& mg, const MGLevel& L, int tile) {
   return mg.bf16 && mg.n_classes == 1 && !L.coarsest && vanka_tc_eligible(L.hp.dim, L.hp.k, L.hp.n_t, tile);
 }
@@ -1012,16 +1039,27 @@ bool vk_launch(MG& mg, MGLevel& L, cudaStream_t s) {
   return mg.precision == kPrecF32 ? vanka<float>(mg, L, s, 0) : vanka<double>(mg, L, s, 0);
 }
 
+template <typename T, int MAXE>
+void axis_pass_m(const void* in, void* out, long long VA, int nin, int nout, int B, const int* ptr, const int* idx,
+                 const void* w, int nnz, int accumulate, cudaStream_t s) {
+  const long long total = VA * nout * B;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, sg::sm_count() * 8));
+  const size_t tab = (size_t)nnz * (sizeof(T) + sizeof(int)) + (size_t)(nout + 1) * sizeof(int);
+  if (tab <= 32 * 1024)
+    mg_axis_gather<T, true, MAXE><<<grid, 256, tab, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin,
+                                                         nout, B, ptr, idx, static_cast<const T*>(w), nnz, accumulate);
+  else
+    mg_axis_gather<T, false, MAXE><<<grid, 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin,
+                                                        nout, B, ptr, idx, static_cast<const T*>(w), nnz, accumulate);
+}
+
+// one pass; maxe = the longest list of the pass (at most kAxisMax)
 template <typename T>
 void axis_pass(const void* in, void* out, long long VA, int nin, int nout, int B, const int* ptr, const int* idx,
-               const void* w, int accumulate, cudaStream_t s) {
-  const long long L = (long long)nout * B;
-  const long long rows = L < 256 ? 256 / L : 1;                // rows per block for short rows
-  const int gx = L < 256 ? 1 : (int)std::min<long long>((L + 255) / 256, 256);
-  const long long row_blocks = (VA + rows - 1) / rows;
-  const int gy = (int)std::max<long long>(1, std::min<long long>(row_blocks, std::max(1, 16384 / gx)));
-  mg_axis_gather<T><<<dim3(gx, gy), 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin, nout, B,
-                                                 ptr, idx, static_cast<const T*>(w), accumulate);
+               const void* w, int nnz, int maxe, int accumulate, cudaStream_t s) {
+  if (maxe <= 4) axis_pass_m<T, 4>(in, out, VA, nin, nout, B, ptr, idx, w, nnz, accumulate, s);
+  else if (maxe <= 8) axis_pass_m<T, 8>(in, out, VA, nin, nout, B, ptr, idx, w, nnz, accumulate, s);
+  else axis_pass_m<T, kAxisMax>(in, out, VA, nin, nout, B, ptr, idx, w, nnz, accumulate, s);
 }
 
 // x_fine += P e_coarse: interpolation along z (3D), y, then x
@@ -1029,13 +1067,16 @@ template <typename T>
 bool prolong(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
   const int nfx = F.hp.nn[0], nfy = F.hp.nn[1], nfz = F.hp.nn[2];
   const int ncx = C.hp.nn[0], ncy = C.hp.nn[1], ncz = C.hp.nn[2];
+  auto pass = [&](const void* in, void* out, long long VA, int nin, int nout, int B, int d, int acc) {
+    axis_pass<T>(in, out, VA, nin, nout, B, F.d_pptr[d], F.d_pidx[d], F.d_pwl[d], F.pnnz[d], F.pmax[d], acc, s);
+  };
   if (F.hp.dim == 3) {
-    axis_pass<T>(C.d_x, F.d_t2, V, ncz, nfz, ncy * ncx, F.d_pptr[2], F.d_pidx[2], F.d_pwl[2], 0, s);
-    axis_pass<T>(F.d_t2, F.d_t1, (long long)V * nfz, ncy, nfy, ncx, F.d_pptr[1], F.d_pidx[1], F.d_pwl[1], 0, s);
-    axis_pass<T>(F.d_t1, F.d_x, (long long)V * nfz * nfy, ncx, nfx, 1, F.d_pptr[0], F.d_pidx[0], F.d_pwl[0], 1, s);
+    pass(C.d_x, F.d_t2, V, ncz, nfz, ncy * ncx, 2, 0);
+    pass(F.d_t2, F.d_t1, (long long)V * nfz, ncy, nfy, ncx, 1, 0);
+    pass(F.d_t1, F.d_x, (long long)V * nfz * nfy, ncx, nfx, 1, 0, 1);
   } else {
-    axis_pass<T>(C.d_x, F.d_t1, V, ncy, nfy, ncx, F.d_pptr[1], F.d_pidx[1], F.d_pwl[1], 0, s);
-    axis_pass<T>(F.d_t1, F.d_x, (long long)V * nfy, ncx, nfx, 1, F.d_pptr[0], F.d_pidx[0], F.d_pwl[0], 1, s);
+    pass(C.d_x, F.d_t1, V, ncy, nfy, ncx, 1, 0);
+    pass(F.d_t1, F.d_x, (long long)V * nfy, ncx, nfx, 1, 0, 1);
   }
   return cudaGetLastError() == cudaSuccess;
 }
@@ -1045,13 +1086,16 @@ template <typename T>
 void restrict_to(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
   const int nfx = F.hp.nn[0], nfy = F.hp.nn[1], nfz = F.hp.nn[2];
   const int ncx = C.hp.nn[0], ncy = C.hp.nn[1], ncz = C.hp.nn[2];
+  auto pass = [&](const void* in, void* out, long long VA, int nin, int nout, int B, int d) {
+    axis_pass<T>(in, out, VA, nin, nout, B, F.d_rptr[d], F.d_ridx[d], F.d_rw[d], F.rnnz[d], F.rmax[d], 0, s);
+  };
   if (F.hp.dim == 3) {
-    axis_pass<T>(F.d_r, F.d_t1, (long long)V * nfz * nfy, nfx, ncx, 1, F.d_rptr[0], F.d_ridx[0], F.d_rw[0], 0, s);
-    axis_pass<T>(F.d_t1, F.d_t2, (long long)V * nfz, nfy, ncy, ncx, F.d_rptr[1], F.d_ridx[1], F.d_rw[1], 0, s);
-    axis_pass<T>(F.d_t2, C.d_b, V, nfz, ncz, ncy * ncx, F.d_rptr[2], F.d_ridx[2], F.d_rw[2], 0, s);
+    pass(F.d_r, F.d_t1, (long long)V * nfz * nfy, nfx, ncx, 1, 0);
+    pass(F.d_t1, F.d_t2, (long long)V * nfz, nfy, ncy, ncx, 1);
+    pass(F.d_t2, C.d_b, V, nfz, ncz, ncy * ncx, 2);
   } else {
-    axis_pass<T>(F.d_r, F.d_t1, (long long)V * nfy, nfx, ncx, 1, F.d_rptr[0], F.d_ridx[0], F.d_rw[0], 0, s);
-    axis_pass<T>(F.d_t1, C.d_b, V, nfy, ncy, ncx, F.d_rptr[1], F.d_ridx[1], F.d_rw[1], 0, s);
+    pass(F.d_r, F.d_t1, (long long)V * nfy, nfx, ncx, 1, 0);
+    pass(F.d_t1, C.d_b, V, nfy, ncy, ncx, 1);
   }
 }
 
@@ -1070,9 +1114,9 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
     return cudaGetLastError();
   }
   cudaError_t e;
-  mg_start<T><<<vec_grid(L.hp.n_x, V), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
-                                                    static_cast<T*>(L.d_r), (int)L.hp.n_x, L.hp.nn[0], L.hp.nn[1],
-                                                    L.hp.nn[2], L.hp.dim);
+  // the start: x = the boundary values of b, r = b on the interior (0 on the boundary)
+  launch_vec_start<T>(static_cast<const T*>(L.d_b), nullptr, static_cast<T*>(L.d_x), static_cast<T*>(L.d_r), 0, V,
+                      L.hp.n_x, L.hp.nn, L.hp.dim, s);
   for (int it = 0; it < mg.nu; ++it) {
     if (it > 0 && (e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
     if (!vanka<T>(mg, L, s, trans)) return cudaErrorInvalidValue;
@@ -1245,8 +1289,8 @@ static cudaError_t tune_vanka(MG& mg) {
         }
       }
     }
-    L.vanka_chunk = best_c;
-    L.vanka_tile = best_t;
+    L.vanka_chunk = L.ffma_chunk = best_c;
+    L.vanka_tile = L.ffma_tile = best_t;
     L.vanka_kind = 0;
     // the tensor-core sweep over its chunk sizes, where it applies; kept if faster
     const int tile_all = mg.vanka_tile;
@@ -1256,8 +1300,8 @@ static cudaError_t tune_vanka(MG& mg) {
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       int tc_c = 0;
       float tc_ms = 1e30f;
-      for (int c : {1, 2, 4}) {
-        if (e != cudaSuccess || c > L.hp.cells[0]) break;
+      for (int c : {1, 2}) {                     // one or two staging buffers
+        if (e != cudaSuccess) break;
         if (vanka_tc_smem(L.hp.dim, L.hp.k, L.hp.n_t, c, std::min(tile_all, mg.n_blk * kVankaVB)) >
             (size_t)optin - 1024)
           break;
@@ -1486,6 +1530,7 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
         msg = "Vanka smoother: one cell with all rows does not fit in shared memory (fewer samples per batch)";
         return SG_ERR_UNSUPPORTED;
       }
+      L.ffma_chunk = L.vanka_chunk;
       if ((e = prepare_vanka(L.hp.dim, L.hp.k, L.hp.n_t, precision == kPrecF32, mg.bf16)) != cudaSuccess) break;
       if (mg.bf16 && (e = prepare_vanka_tc(L.hp.dim, L.hp.k, L.hp.n_t)) != cudaSuccess) break;
     }
@@ -1505,6 +1550,15 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
         std::vector<int> pptr, pidx, rptr, ridx;
         std::vector<double> pwl, rw;
         transfer_1d(F.hp, L.hp, d, pptr, pidx, pwl, rptr, ridx, rw);
+        F.pnnz[d] = (int)pidx.size();
+        F.rnnz[d] = (int)ridx.size();
+        F.pmax[d] = F.rmax[d] = 0;
+        for (size_t i = 0; i + 1 < pptr.size(); ++i) F.pmax[d] = std::max(F.pmax[d], pptr[i + 1] - pptr[i]);
+        for (size_t j = 0; j + 1 < rptr.size(); ++j) F.rmax[d] = std::max(F.rmax[d], rptr[j + 1] - rptr[j]);
+        if (F.pmax[d] > kAxisMax || F.rmax[d] > kAxisMax) {
+          e = cudaErrorInvalidValue;
+          break;
+        }
         if ((e = upload_vec(&F.d_pptr[d], pptr)) != cudaSuccess) break;
         if ((e = upload_vec(&F.d_pidx[d], pidx)) != cudaSuccess) break;
         if ((e = upload_values(&F.d_pwl[d], pwl, precision)) != cudaSuccess) break;
@@ -1624,17 +1678,23 @@ sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int 
         msg = "the SG cell kernel has no launch shape on this level";
         return SG_ERR_UNSUPPORTED;
       }
-      const int t = tile < 0 ? (L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile) : (tile == 0 ? mg.vanka_tile : tile);
+      const int kd = kind >= 0 ? kind : L.vanka_kind;
+      // "keep" of a sweep that is not running: the FFMA sweep's last chunk and
+      // tile, two staging buffers and all modes for the tensor-core sweep
+      const int keep = kd == L.vanka_kind ? L.vanka_chunk : (kd == 0 ? L.ffma_chunk : 2);
+      const int keep_tile = kd == L.vanka_kind ? L.vanka_tile : (kd == 0 ? L.ffma_tile : 0);
+      const int t = tile < 0 ? (keep_tile > 0 ? keep_tile : mg.vanka_tile) : (tile == 0 ? mg.vanka_tile : tile);
       if (t != mg.vanka_tile && (t % kVankaVB != 0 || t > mg.vanka_tile)) {
         msg = "mode tiles are multiples of 4 slots, at most all of them";
         return SG_ERR_ARG;
       }
-      const int c = chunk > 0 ? std::min(chunk, L.hp.cells[0]) : L.vanka_chunk;
-      const int kd = kind >= 0 ? kind : L.vanka_kind;
+      int c = chunk > 0 ? std::min(chunk, L.hp.cells[0]) : keep;
+      if (kd == 1) c = std::max(1, std::min(chunk > 0 ? chunk : c, 2));   // staging buffers of the tensor-core sweep
+      if (c <= 0) c = 1;
       if (kd == 1) {
         if (!tc_level_ok(mg, L, t)) {
           msg = "the tensor-core Vanka sweep needs bf16 factors, one diagonal class, a patch of at most 64 and "
-                "at most 40 slots per tile";
+                "at most 80 slots per tile";
           return SG_ERR_UNSUPPORTED;
         }
         if (vanka_tc_smem(L.hp.dim, L.hp.k, L.hp.n_t, c, std::min(t, mg.n_blk * kVankaVB)) > (size_t)optin - 1024) {
@@ -1650,6 +1710,10 @@ sg_status mg_force_variant(MG& mg, int level, int residual_kind, int chunk, int 
         L.vanka_chunk = c;
         L.vanka_tile = t == mg.vanka_tile ? 0 : t;
         L.vanka_kind = kd;
+        if (kd == 0) {
+          L.ffma_chunk = c;
+          L.ffma_tile = L.vanka_tile;
+        }
       }
     }
   }

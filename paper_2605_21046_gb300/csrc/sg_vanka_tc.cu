@@ -4,26 +4,40 @@
 // local space-time patch problems) is, per cell, a dense product
 //     Z = inv * R,   inv: NP x NP patch inverse (bf16),  R: NP x modes,
 // followed by the damped, multiplicity-weighted sum of the cells' corrections.
-// Here every cell's product is one chain of tcgen05.mma (kind::f16, FP32
-// accumulation in tensor memory), issued by one thread:
-//   * A = inv, M = 128 rows (NP <= 64 used, the rest zero), K = 64 (NP padded
-//     with zeros), staged by asynchronous 16-byte copies straight from the
-//     stored rows into the canonical no-swizzle K-major layout (8-row x 16-byte
-//     core matrices);
-//   * B = R split into three bf16 terms R = R1 + R2 + R3 (each the bf16
-//     rounding of what the previous ones leave), side by side along N: the
-//     bf16 x bf16 products are exact and accumulate in FP32, so the product
-//     carries about the FP32 accuracy of the patch values;
-//   * D (128 lanes x N columns of FP32 in tensor memory) is read back with
-//     tcgen05.ld by the two warps whose lanes hold the patch rows, the three
-//     split columns summed, and the corrections added into a shared-memory
-//     accumulator.
-// Two D / B buffers let cell c's MMAs run while cell c-1 is read back.  Units
-// (a chunk of cells and a tile of modes) are double buffered as in the FFMA
-// sweep: the next unit's inverses and r are copied in while one is computed.
-// Waits on the MMA completion barrier are bounded; if one runs out the kernel
-// records SG_ERR_TIMEOUT, stops issuing work, frees its tensor memory and
-// returns.
+// The unit of work is a pair of neighbouring cells (along x) and a tile of
+// chaos modes; the pair's two products are one chain of tcgen05.mma (kind::f16,
+// FP32 accumulation in tensor memory) issued by one thread, as one
+// block-diagonal product
+//     [Z0]   [inv0   0 ] [R0]
+//     [Z1] = [ 0   inv1] [R1]      M = 128 (64 rows per cell), K = 128,
+// so the 128 lanes of the accumulator hold both cells' rows and all four
+// warps read results back:
+//   * A: each 8-value K chunk holds cell 0's NPR rows (NP rounded up to 8),
+//     64 rows of zeros and cell 1's NPR rows; the K steps of cell 0 read 128
+//     rows from the first, those of cell 1 from 64 rows before the second, so
+//     the zero rows fill the off-diagonal blocks (rows of D past a cell's NP
+//     are never read and may hold anything finite).  The stored inverse rows
+//     (pitch npp, zero padded) are copied in by asynchronous 16-byte copies
+//     into the canonical no-swizzle K-major layout (8-row x 16-byte core
+//     matrices); K past npp stays zero.
+//   * B: R split into three bf16 terms R = R1 + R2 + R3 (each the bf16
+//     rounding of what the previous ones leave): the bf16 x bf16 products are
+//     exact and accumulate in FP32, so the product carries about the FP32
+//     accuracy of the patch values.  Term t of slot s is MMA column
+//     t SLP + s (SLP = the slots rounded up to 16), so one thread writes eight
+//     K values of one column as a 16-byte store and consecutive slots fall in
+//     consecutive core-matrix rows.  Cell 1's K chunks follow cell 0's
+//     directly: where a K step of cell 0 reaches into them, A's columns are
+//     zero.
+//   * D (128 lanes x 3 SLP columns of FP32 in tensor memory) is read back with
+//     tcgen05.ld (three loads of 16 columns give 16 slots' three terms, summed
+//     in registers), damped, divided by the node's multiplicity and added into
+//     x with one reduction per (patch row, slot).
+// The next unit's r values and inverses are copied in while the current one
+// computes: into a second buffer (two stages), or, with one buffer, r once B
+// is built and the inverses once the MMAs are done.  Waits on the MMA
+// completion barrier are bounded; if one runs out the kernel records
+// SG_ERR_TIMEOUT, stops issuing work, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -37,12 +51,18 @@ namespace sg {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr int kTcM = 128;                  // MMA rows (patch rows; NP <= 64 are used)
-constexpr int kTcK = 64;                   // patch columns, zero padded
-constexpr int kTcACell = kTcM * kTcK * 2;  // bytes of one cell's A tile
-constexpr int kTcLboA = (kTcM / 8) * 128;  // A: bytes between the 8-value K chunks
-constexpr int kTcVB = 4;                   // slots per mode block
-constexpr unsigned int kTcSpin = 1u << 22; // bound of a completion wait (polls)
+constexpr int kTcKC = 8;                       // 8-value K chunks per cell (K = 64 per cell)
+// A: bytes between K chunks (cell 0's groups of 8 rows, 8 zero groups, cell
+// 1's groups) and bytes of one buffer (8 chunks and the groups that the last
+// K step of cell 1 reads past them)
+__host__ __device__ constexpr int tc_lbo_a(int kc) { return (2 * kc + 8) * 128; }
+__host__ __device__ constexpr int tc_a_stage(int kc) { return kTcKC * tc_lbo_a(kc) + (8 - kc) * 128; }
+// B: K chunks of the pair (cell 1's follow cell 0's; one more when the last K
+// step of cell 1 reads past them)
+__host__ __device__ constexpr int tc_b_chunks(int kc) { return 2 * kc + (kc & 1); }
+constexpr int kTcVB = 4;                       // slots per mode block
+constexpr int kTcMaxSlots = 80;                // 3 x 80 columns <= the MMA's N limit of 256
+constexpr unsigned int kTcSpin = 1u << 22;     // bound of a completion wait (polls)
 
 struct TcParams {
   const float* r;
@@ -50,7 +70,7 @@ struct TcParams {
   const __nv_bfloat16* inv;
   const int* blk_alpha;     // [n_blk][kTcVB] modes, -1 padded
   int* status;              // SG_ERR_TIMEOUT is recorded here
-  int n_blk, chunk, npp, tile_blocks, n_tiles, ncols, tmem_cols;
+  int n_blk, npp, tile_blocks, n_tiles, slp, ncols, tmem_cols, stages;
   long long n_x, n_cells, n_vec_x, inv_count;
   int cells[3], nn[3];
   float omega;
@@ -65,7 +85,6 @@ __device__ __forceinline__ void cp_async4_tc(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_commit_tc() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1_tc() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0_tc() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
@@ -128,38 +147,43 @@ struct TcUnit {
 };
 
 template <int DIM, int K, int NT>
-__global__ void __launch_bounds__(kTcThreads, 2) mg_vanka_tc(const TcParams p) {
+__global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
   constexpr int N = K + 1;
   constexpr int NKD = DIM == 2 ? N * N : N * N * N;
   constexpr int NP = NT * NKD;
-  static_assert(NP <= kTcK, "patch larger than the MMA K extent");
-  constexpr int LYZ = DIM == 2 ? N : N * N;
+  static_assert(NP <= 8 * kTcKC, "patch larger than 64 unknowns");
+  constexpr int KC = (NP + 7) / 8;               // K chunks of a cell that hold values = row groups of a cell
+  constexpr int LBO_A = tc_lbo_a(KC), A_STAGE = tc_a_stage(KC), B_CHUNKS = tc_b_chunks(KC);
   constexpr int RPC = (NP * 2 + 15) / 16;        // 16-byte pieces of a stored row that hold values
-  __shared__ __align__(8) uint64_t s_bar[2];
+  constexpr int LX = 2 * K + 1;                  // nodes of the pair along x
+  constexpr int LYZ = DIM == 2 ? N : N * N;
+  constexpr int LN = LX * LYZ;                   // nodes of the pair
+  constexpr int E = NT * LN;                     // (time node, node) entries of the pair
+  constexpr int EP = E | 1;                      // odd pitch: slots of one entry fall in distinct banks
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
+  __shared__ int s_qoff[8 * kTcKC];              // patch column -> entry of cell 0
+  __shared__ int s_ge[2][E];                     // offset of each entry in a mode's block of r (-1: none)
+  __shared__ long long s_so[2][kTcMaxSlots];     // offset of each slot's mode block (-1: none)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int C = p.chunk, LX = C * K + 1, LN = LX * LYZ, E = NT * LN;
   const int SL = p.tile_blocks * kTcVB;           // slots of a tile
-  const int NCOL = p.ncols;                       // MMA N: 3 SL rounded up to 16
-  const int BBYTES = NCOL * kTcK * 2;             // one B buffer
+  const int SLP = p.slp;                          // column pitch of a split term
+  const int NCOL = p.ncols;                       // MMA N = 3 SLP
+  const bool two = p.stages == 2;
   const uint32_t LBO_B = (uint32_t)(NCOL / 8) * 128u;
-  // shared memory: two stages of A tiles, two B buffers, corrections, two
-  // stages of r, two stages of node / slot tables
-  unsigned char* A0 = smem_raw;                                    // 2 x C x kTcACell
-  unsigned char* Bb = A0 + (size_t)2 * C * kTcACell;               // 2 x BBYTES
-  float* Zc = reinterpret_cast<float*>(Bb + (size_t)2 * BBYTES);   // [NT][LN][SL]
-  float* Rl0 = Zc + (size_t)E * SL;                                // 2 x [NT][LN][SL]
-  int* Gn0 = reinterpret_cast<int*>(Rl0 + (size_t)2 * E * SL);     // 2 x [LN]
-  int* Sm0 = Gn0 + 2 * LN;                                         // 2 x [SL]
+  // shared memory: A buffers, B, r buffers
+  unsigned char* A0 = smem_raw;                                         // stages x A_STAGE
+  unsigned char* B = A0 + (size_t)p.stages * A_STAGE;                   // B_CHUNKS x LBO_B
+  float* Rl0 = reinterpret_cast<float*>(B + (size_t)B_CHUNKS * LBO_B);  // stages x [SL][EP]
   const int nnx = p.nn[0], nny = p.nn[1], nnz_ = p.nn[2];
-  const int cpr = (p.cells[0] + C - 1) / C;
-  const unsigned int n_chunks = (unsigned int)(cpr * p.cells[1] * p.cells[2]);
-  const unsigned int n_units = n_chunks * (unsigned int)p.n_tiles;
-  const uint32_t idesc = idesc_bf16(kTcM, NCOL);
+  const unsigned int ppr = (unsigned int)(p.cells[0] + 1) / 2u;
+  const unsigned int n_pairs = ppr * (unsigned int)(p.cells[1] * p.cells[2]);
+  const unsigned int n_units = n_pairs * (unsigned int)p.n_tiles;
+  const uint32_t idesc = idesc_bf16(128, NCOL);
 
-  // tensor memory (one warp), completion barriers, zeroed operands
+  // tensor memory (one warp), completion barrier, zeroed operands, column table
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
                  "r"(p.tmem_cols)
@@ -167,36 +191,38 @@ __global__ void __launch_bounds__(kTcThreads, 2) mg_vanka_tc(const TcParams p) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
+    mbar_init(&s_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     s_fail = 0;
   }
   {
     uint4* z = reinterpret_cast<uint4*>(smem_raw);
-    const size_t n16 = ((size_t)2 * C * kTcACell + (size_t)2 * BBYTES) / 16;
-    for (size_t i = tid; i < n16; i += kTcThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = tid; i < E * SL; i += kTcThreads) Zc[i] = 0.0f;
+    const int n16 = (p.stages * A_STAGE + B_CHUNKS * (int)LBO_B) / 16;
+    for (int i = tid; i < n16; i += kTcThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = tid; q < 8 * kTcKC; q += kTcThreads) {
+      int off = 0;
+      if (q < NP) {
+        const int iq = q / NKD, a = q - iq * NKD;
+        const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
+        off = iq * LN + ax + LX * (ay + N * az);
+      }
+      s_qoff[q] = off;
+    }
   }
-  tc_before_sync();
-  __syncthreads();
-  tc_after_sync();
-  const uint32_t tmem = s_tmem;
-  uint32_t phase_bits = 0u;                       // parity of the next completion, per barrier
 
   auto decode = [&](unsigned int unit, TcUnit& U) {
-    const unsigned int ch = unit % n_chunks;
-    const int tile = (int)(unit / n_chunks);
+    const unsigned int pr = unit % n_pairs;
+    const int tile = (int)(unit / n_pairs);
     U.b0 = tile * p.tile_blocks;
     U.nb = min(p.tile_blocks, p.n_blk - U.b0);
-    U.cx0 = (int)(ch % (unsigned int)cpr) * C;
-    const unsigned int row = ch / (unsigned int)cpr;
+    U.cx0 = (int)(pr % ppr) * 2;
+    const unsigned int row = pr / ppr;
     U.cy = (int)(row % (unsigned int)p.cells[1]);
     U.cz = (int)(row / (unsigned int)p.cells[1]);
-    U.nc = min(C, p.cells[0] - U.cx0);
+    U.nc = min(2, p.cells[0] - U.cx0);
     U.cell0 = ((long long)U.cz * p.cells[1] + U.cy) * p.cells[0] + U.cx0;
   };
-  auto tables = [&](const TcUnit& U, int* Gn, int* Sm) {
+  auto tables = [&](const TcUnit& U, int tb) {
     const int lxn = U.nc * K + 1;
     for (int ln = tid; ln < LN; ln += kTcThreads) {
       const int lx = ln % LX, lyz = ln / LX;
@@ -208,182 +234,195 @@ __global__ void __launch_bounds__(kTcThreads, 2) mg_vanka_tc(const TcParams p) {
         if (DIM == 3) in = in && gz > 0 && gz < nnz_ - 1;
         if (in) node = (int)(((long long)gz * nny + gy) * nnx + gx);
       }
-      Gn[ln] = node;
-    }
-    for (int sl = tid; sl < SL; sl += kTcThreads) Sm[sl] = sl < U.nb * kTcVB ? p.blk_alpha[U.b0 * kTcVB + sl] : -1;
-  };
-  // the unit's inverses into the canonical A layout, r onto the node grid
-  auto stage = [&](const TcUnit& U, unsigned char* A, float* Rl, const int* Gn, const int* Sm) {
-    const long long ibeg = U.cell0 * NP * p.npp;
-    for (int idx = tid; idx < U.nc * NP * RPC; idx += kTcThreads) {
-      const int rr = idx / RPC, kc = idx - rr * RPC;
-      const int c = rr / NP, row = rr - c * NP;
-      const long long g = ibeg + (long long)rr * p.npp + kc * 8;
-      if (!SG_IN(g + 7, p.inv_count, 601)) continue;
-      cp_async16_tc(A + (size_t)c * kTcACell + (size_t)kc * kTcLboA + (row >> 3) * 128 + (row & 7) * 16, p.inv + g);
-    }
-    for (int idx = tid; idx < SL * E; idx += kTcThreads) {
-      const int sl = idx / E, e = idx - sl * E;
-      int i = 0;
 #pragma unroll
-      for (int j = 1; j < NT; ++j) i += e >= j * LN;
-      const int ln = e - i * LN;
-      const int mode = Sm[sl], node = Gn[ln];
-      const long long gi = ((long long)mode * NT + i) * p.n_x + node;
-      float* dst = Rl + (size_t)e * SL + sl;
-      if (mode >= 0 && node >= 0 && SG_IN(gi, p.n_vec_x, 602)) cp_async4_tc(dst, p.r + gi);
-      else *dst = 0.0f;
+      for (int i = 0; i < NT; ++i) s_ge[tb][i * LN + ln] = node >= 0 ? (int)(i * p.n_x + node) : -1;
+    }
+    for (int sl = tid; sl < SL; sl += kTcThreads) {
+      const int mode = sl < U.nb * kTcVB ? p.blk_alpha[U.b0 * kTcVB + sl] : -1;
+      s_so[tb][sl] = mode >= 0 ? (long long)mode * NT * p.n_x : -1;
     }
   };
-  // B of one cell: the three bf16 terms of its patch values, slot s of term
-  // t in MMA column t SL + s, patch column q in K
-  auto build_b = [&](const float* Rl, int c, unsigned char* B) {
-    const int half = (NP + 1) / 2;
-    for (int it = tid; it < half * SL; it += kTcThreads) {
-      const int kp = it % half, s = it / half;
-      const int q0 = 2 * kp;
-      float v[2];
+  // the unit's r values: slot-major, entries (time node, pair node)
+  // contiguous; warp w takes slots w, w + 4, ..., its lanes the entries
+  constexpr int EW = (E + 31) / 32;               // entries a lane takes
+  auto stage_r = [&](int tb, float* Rl) {
+    int ge[EW];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int q = q0 + h;
-        v[h] = 0.0f;
-        if (q < NP) {
-          const int iq = q / NKD, aq = q - iq * NKD;
-          const int ax = aq % N, ayz = aq / N;
-          v[h] = Rl[(size_t)(iq * LN + c * K + ax + LX * ayz) * SL + s];
+    for (int j = 0; j < EW; ++j) ge[j] = lane + 32 * j < E ? s_ge[tb][lane + 32 * j] : -1;
+    for (int sl = warp; sl < SL; sl += kTcThreads / 32) {
+      const long long so = s_so[tb][sl];
+      float* row = Rl + sl * EP;
+#pragma unroll
+      for (int j = 0; j < EW; ++j) {
+        const int e = lane + 32 * j;
+        if (e < E) {
+          if (so >= 0 && ge[j] >= 0 && SG_IN(so + ge[j], p.n_vec_x, 602)) cp_async4_tc(row + e, p.r + so + ge[j]);
+          else row[e] = 0.0f;
         }
       }
-      const int kc = q0 >> 3, kw = q0 & 7;
+    }
+  };
+  // the unit's inverses into A: row rho of cell c, K chunk kc; a thread's
+  // (c, kc, rho) items are the same in every unit
+  constexpr int A_ITEMS = 2 * RPC * NP, A_PER = (A_ITEMS + kTcThreads - 1) / kTcThreads;
+  int a_src[A_PER], a_dst[A_PER];
+#pragma unroll
+  for (int j = 0; j < A_PER; ++j) {
+    const int idx = tid + j * kTcThreads;
+    const int rho = idx % NP, rest = idx / NP;
+    const int kc = rest % RPC, c = rest / RPC;
+    a_src[j] = idx < A_ITEMS ? (c * NP + rho) * p.npp + kc * 8 : -1;
+    a_dst[j] = kc * LBO_A + (c * (KC + 8) + (rho >> 3)) * 128 + (rho & 7) * 16;
+  }
+  auto stage_a = [&](const TcUnit& U, unsigned char* A) {
+    const long long base = U.cell0 * NP * (long long)p.npp;
+    const int lim = U.nc * NP * p.npp;             // values of the unit's cells
+#pragma unroll
+    for (int j = 0; j < A_PER; ++j) {
+      if (a_src[j] >= 0 && a_src[j] < lim && SG_IN(base + a_src[j] + 7, p.inv_count, 601))
+        cp_async16_tc(A + a_dst[j], p.inv + base + a_src[j]);
+    }
+  };
+  // B: eight K values (patch columns 8 kc ..) of slot s of cell c, three terms
+  auto build_b = [&](const float* Rl) {
+    for (int idx = tid; idx < 2 * KC * SL; idx += kTcThreads) {
+      const int s = idx % SL, ck = idx / SL;
+      const int c = ck / KC, kc = ck - c * KC;
+      const float* src = Rl + s * EP + c * K;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = kc * 8 + j;
+        v[j] = q < NP ? src[s_qoff[q]] : 0.0f;
+      }
+      unsigned char* dst = B + (size_t)(KC * c + kc) * LBO_B;
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
-        __nv_bfloat16 b[2];
+        uint32_t w[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          b[h] = __float2bfloat16_rn(v[h]);
-          v[h] -= __bfloat162float(b[h]);
+        for (int h = 0; h < 4; ++h) {
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+          w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+          const float2 back = __bfloat1622float2(b2);
+          v[2 * h] -= back.x;
+          v[2 * h + 1] -= back.y;
         }
-        const int n = t * SL + s;
-        __nv_bfloat162 pr;
-        pr.x = b[0];
-        pr.y = b[1];
-        *reinterpret_cast<__nv_bfloat162*>(B + (size_t)kc * LBO_B + (n >> 3) * 128 + (n & 7) * 16 + kw * 2) = pr;
+        const int n = t * SLP + s;
+        *reinterpret_cast<uint4*>(dst + (n >> 3) * 128 + (n & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
   };
-  // wait (bounded) for the MMAs committed to barrier b
-  auto wait_mma = [&](int b) {
-    if (s_fail) return;
-    unsigned int polls = 0;
-    while (!mbar_test(&s_bar[b], (phase_bits >> b) & 1u)) {
-      if (++polls > kTcSpin) {
-        atomicExch(&s_fail, 1);
-        atomicExch(p.status, (int)SG_ERR_TIMEOUT);
-        break;
+  // wait (bounded) for the MMAs committed to the barrier
+  uint32_t phase = 0u;
+  auto wait_mma = [&]() {
+    if (!s_fail) {
+      unsigned int polls = 0;
+      while (!mbar_test(&s_bar, phase)) {
+        if (++polls > kTcSpin) {
+          atomicExch(&s_fail, 1);
+          atomicExch(p.status, (int)SG_ERR_TIMEOUT);
+          break;
+        }
       }
     }
-    phase_bits ^= 1u << b;
+    phase ^= 1u;
   };
-  // D of one cell (buffer b) into the corrections
-  auto read_back = [&](const TcUnit& U, const int* Gn, int c, int b) {
-    wait_mma(b);
-    tc_after_sync();
-    // warp-uniform: tcgen05.ld is executed by all 32 lanes of a warp or none
-    const int failed = __shfl_sync(0xffffffffu, s_fail, 0);
-    if (warp < 2 && !failed) {
-      const int rho = warp * 32 + lane;
-      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * NCOL);
-      float d[16];
-      const int i = rho / NKD, a = rho - i * NKD;
-      const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
-      const int lna = c * K + ax + LX * (ay + (DIM == 3 ? N * az : 0));
-      const bool live = rho < NP && Gn[lna] >= 0 && c < U.nc;
-      const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
-      const float sc = p.omega / (float)mult;
-      float* z = Zc + (size_t)(i * LN + lna) * SL;
-      for (int c0 = 0; c0 < NCOL; c0 += 16) {
-        tmem_ld16(base + (uint32_t)c0, d);
-        tmem_ld_wait();
+  // D into x: lane row = 64 c + patch row
+  auto read_back = [&](const TcUnit& U, int tb, uint32_t tmem) {
+    const int failed = __shfl_sync(0xffffffffu, s_fail, 0);   // warp-uniform: tcgen05.ld is .sync.aligned
+    if (failed) return;
+    const int row = warp * 32 + lane, c = row >> 6, rho = row & 63;
+    const int i = rho / NKD, a = rho - i * NKD;
+    const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
+    const int lna = c * K + ax + LX * (ay + N * az);
+    const int ge = rho < NP ? s_ge[tb][i * LN + lna] : -1;
+    const bool live = rho < NP && c < U.nc && ge >= 0;
+    const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
+    const float sc = p.omega / (float)mult;
+    const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int s0 = 0; s0 < SL; s0 += 16) {
+      float d0[16], d1[16], d2[16];
+      tmem_ld16(base + (uint32_t)s0, d0);
+      tmem_ld16(base + (uint32_t)(SLP + s0), d1);
+      tmem_ld16(base + (uint32_t)(2 * SLP + s0), d2);
+      tmem_ld_wait();
+      if (live) {
+        float* xrow = p.x + ge;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int col = c0 + j;
-          if (live && col < 3 * SL) {
-            const int s = col % SL;
-            if (SG_IN((size_t)(i * LN + lna) * SL + s, (size_t)E * SL, 603)) atomicAdd(z + s, sc * d[j]);
-          }
+          if (s0 + j >= SL) break;
+          const long long so = s_so[tb][s0 + j];
+          if (so >= 0 && SG_IN(so + ge, p.n_vec_x, 604)) atomicAdd(xrow + so, sc * ((d0[j] + d1[j]) + d2[j]));
         }
       }
     }
-    tc_before_sync();
   };
 
   unsigned int u = blockIdx.x;
-  int buf = 0;
+  int tb = 0, ab = 0;
   TcUnit cur, nxt;
   if (u < n_units) {
     decode(u, cur);
-    tables(cur, Gn0, Sm0);
+    tables(cur, 0);
   }
+  tc_before_sync();
   __syncthreads();
-  if (u < n_units) stage(cur, A0, Rl0, Gn0, Sm0);
+  tc_after_sync();
+  const uint32_t tmem = s_tmem;
+  if (u < n_units) {
+    stage_r(0, Rl0);
+    stage_a(cur, A0);
+  }
   cp_commit_tc();
-  for (; u < n_units; u += gridDim.x, buf ^= 1) {
+  for (; u < n_units; u += gridDim.x) {
     const unsigned int un = u + gridDim.x;
     const bool has_next = un < n_units;
-    __syncthreads();
     if (has_next) {
       decode(un, nxt);
-      tables(nxt, Gn0 + (buf ^ 1) * LN, Sm0 + (buf ^ 1) * SL);
+      tables(nxt, tb ^ 1);
     }
-    __syncthreads();
-    if (has_next)
-      stage(nxt, A0 + (size_t)(buf ^ 1) * C * kTcACell, Rl0 + (size_t)(buf ^ 1) * E * SL, Gn0 + (buf ^ 1) * LN,
-            Sm0 + (buf ^ 1) * SL);
-    cp_commit_tc();
-    cp_wait1_tc();
+    cp_wait0_tc();
     fence_async_smem();
     __syncthreads();
-    const float* Rl = Rl0 + (size_t)buf * E * SL;
-    const int* Gn = Gn0 + buf * LN;
-    const unsigned char* A = A0 + (size_t)buf * C * kTcACell;
-    for (int c = 0; c < cur.nc; ++c) {
-      const int b = c & 1;
-      unsigned char* B = Bb + (size_t)b * BBYTES;
-      build_b(Rl, c, B);
-      fence_async_smem();
-      tc_before_sync();
-      __syncthreads();
-      tc_after_sync();
-      if (tid == 0 && !s_fail) {
-        const uint32_t a_addr = smem_u32(A + (size_t)c * kTcACell), b_addr = smem_u32(B);
-#pragma unroll
-        for (int ks = 0; ks < kTcK / 16; ++ks) {
-          const uint64_t ad = smem_desc(a_addr + (uint32_t)(ks * 2 * kTcLboA), (uint32_t)kTcLboA, 128u);
-          const uint64_t bd = smem_desc(b_addr + (uint32_t)ks * 2u * LBO_B, LBO_B, 128u);
-          mma_bf16(tmem + (uint32_t)(b * NCOL), ad, bd, idesc, ks > 0 ? 1u : 0u);
-        }
-        mma_commit(&s_bar[b]);
-      }
-      if (c > 0) read_back(cur, Gn, c - 1, b ^ 1);
-      __syncthreads();
+    const int nb = two ? ab ^ 1 : ab;               // buffers of the next unit
+    float* Rl = Rl0 + (size_t)ab * SL * EP;
+    if (two && has_next) {
+      stage_r(tb ^ 1, Rl0 + (size_t)nb * SL * EP);
+      stage_a(nxt, A0 + (size_t)nb * A_STAGE);
+      cp_commit_tc();
     }
-    if (cur.nc > 0) read_back(cur, Gn, cur.nc - 1, (cur.nc - 1) & 1);
+    build_b(Rl);
+    fence_async_smem();
+    tc_before_sync();
     __syncthreads();
-    // add the corrections into x and clear them
-    for (int idx = tid; idx < cur.nb * kTcVB * E; idx += kTcThreads) {
-      const int sl = idx / E, e = idx - sl * E;
-      int i = 0;
+    tc_after_sync();
+    if (tid == 0 && !s_fail) {
+      const uint32_t a_addr = smem_u32(A0 + (size_t)ab * A_STAGE), b_addr = smem_u32(B);
+      bool first = true;
 #pragma unroll
-      for (int j = 1; j < NT; ++j) i += e >= j * LN;
-      const int ln = e - i * LN;
-      const int mode = Sm0[buf * SL + sl], node = Gn[ln];
-      float* z = Zc + (size_t)e * SL + sl;
-      if (mode >= 0 && node >= 0) {
-        const long long gi = ((long long)mode * NT + i) * p.n_x + node;
-        if (SG_IN(gi, p.n_vec_x, 604)) atomicAdd(p.x + gi, *z);
+      for (int ks = 0; ks < 8; ++ks) {
+        const int kl = ks & 3;                      // K step within the cell
+        if (2 * kl >= KC) continue;                 // only zeros there
+        const uint32_t a_start = a_addr + (uint32_t)(2 * kl * LBO_A) + (ks >= 4 ? (uint32_t)KC * 128u : 0u);
+        const uint64_t ad = smem_desc(a_start, (uint32_t)LBO_A, 128u);
+        const uint32_t b_chunk = (uint32_t)((ks >= 4 ? KC : 0) + 2 * kl);
+        const uint64_t bd = smem_desc(b_addr + b_chunk * LBO_B, LBO_B, 128u);
+        mma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
+        first = false;
       }
-      *z = 0.0f;
+      mma_commit(&s_bar);
     }
+    if (!two && has_next) stage_r(tb ^ 1, Rl);      // B is built: r's buffer is free
+    wait_mma();
+    tc_after_sync();
+    if (!two && has_next) stage_a(nxt, A0);         // the MMAs are done: A's buffer is free
+    if (!two) cp_commit_tc();
+    read_back(cur, tb, tmem);
+    tc_before_sync();
+    __syncthreads();
     cur = nxt;
+    tb ^= 1;
+    if (two) ab ^= 1;
   }
   cp_wait0_tc();
   tc_before_sync();
@@ -395,22 +434,51 @@ __global__ void __launch_bounds__(kTcThreads, 2) mg_vanka_tc(const TcParams p) {
 
 }  // namespace
 
-size_t vanka_tc_smem(int dim, int k, int nt, int chunk, int tile_slots) {
+// slots of a tile rounded up to 16: the column pitch of one split term
+static int tc_slot_pitch(int tile_slots) { return (tile_slots + 15) / 16 * 16; }
+
+size_t vanka_tc_smem(int dim, int k, int nt, int stages, int tile_slots) {
   const int n = k + 1, lyz = dim == 2 ? n : n * n;
-  const size_t ln = (size_t)(chunk * k + 1) * lyz, e = (size_t)nt * ln;
-  const int ncol = (3 * tile_slots + 15) / 16 * 16;
-  return (size_t)2 * chunk * kTcACell + (size_t)2 * ncol * kTcK * 2 + 3 * e * tile_slots * sizeof(float) +
-         2 * (ln + (size_t)tile_slots) * sizeof(int);
+  const int e = nt * (2 * k + 1) * lyz, ep = e | 1;
+  const int kc = (nt * (dim == 2 ? n * n : n * n * n) + 7) / 8;
+  const int ncol = 3 * tc_slot_pitch(tile_slots);
+  return (size_t)stages * tc_a_stage(kc) + (size_t)tc_b_chunks(kc) * (ncol / 8) * 128 +
+         (size_t)stages * tile_slots * ep * sizeof(float);
 }
 
 bool vanka_tc_eligible(int dim, int k, int nt, int tile_slots) {
   const int n = k + 1, np = nt * (dim == 2 ? n * n : n * n * n);
-  return np <= kTcK && tile_slots >= kTcVB && 3 * tile_slots <= 128;
+  return np <= 8 * kTcKC && tile_slots >= kTcVB && tile_slots % kTcVB == 0 && tile_slots <= kTcMaxSlots;
+}
+
+// static shared memory and registers of each instantiation (prepare_vanka_tc)
+struct TcAttr {
+  int static_smem = 0, regs = 0;
+};
+static TcAttr g_tc_attr[4][4][5];      // [dim][k][n_t]
+
+// CTAs of one instantiation resident on an SM at once: shared memory (with the
+// per-CTA reservation), registers, and tensor memory (512 columns an SM), so
+// that no CTA of the persistent grid waits in its allocation.
+static int tc_ctas_per_sm(const TcAttr& a, size_t smem, int tmem_cols) {
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  const long long per_cta_smem = (long long)smem + a.static_smem + reserved;
+  const int regs = (a.regs + 7) / 8 * 8;                      // allocated in steps of 8 a thread
+  int n = 512 / tmem_cols;
+  if (per_cta_smem > 0) n = std::min<long long>(n, smem_sm / per_cta_smem);
+  if (regs > 0) n = std::min(n, regs_sm / (regs * kTcThreads));
+  return std::max(1, n);
 }
 
 template <int DIM, int K, int NT>
-static cudaError_t launch_tc(const TcParams& p, size_t smem, cudaStream_t s, int grid) {
+static cudaError_t launch_tc(const TcParams& p, size_t smem, cudaStream_t s, long long units) {
   auto kern = &mg_vanka_tc<DIM, K, NT>;
+  const int per_sm = tc_ctas_per_sm(g_tc_attr[DIM][K][NT], smem, p.tmem_cols);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(units, sm_count() * per_sm));
   kern<<<grid, kTcThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -425,8 +493,12 @@ cudaError_t prepare_vanka_tc(int dim, int k, int nt) {
     cudaFuncAttributes fa;                                                                               \
     cudaError_t e = cudaFuncGetAttributes(&fa, &mg_vanka_tc<D, KK, TT>);                                 \
     if (e != cudaSuccess) return e;                                                                      \
-    return cudaFuncSetAttribute(&mg_vanka_tc<D, KK, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                optin - (int)fa.sharedSizeBytes);                                        \
+    g_tc_attr[D][KK][TT] = TcAttr{(int)fa.sharedSizeBytes, fa.numRegs};                                  \
+    e = cudaFuncSetAttribute(&mg_vanka_tc<D, KK, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                             optin - (int)fa.sharedSizeBytes);                                           \
+    if (e != cudaSuccess) return e;                                                                      \
+    return cudaFuncSetAttribute(&mg_vanka_tc<D, KK, TT>, cudaFuncAttributePreferredSharedMemoryCarveout, \
+                                100);                                                                    \
   }
   SG_TP(2, 1, 1) SG_TP(2, 1, 2) SG_TP(2, 1, 3) SG_TP(2, 1, 4)
   SG_TP(2, 2, 1) SG_TP(2, 2, 2) SG_TP(2, 2, 3) SG_TP(2, 2, 4)
@@ -437,7 +509,7 @@ cudaError_t prepare_vanka_tc(int dim, int k, int nt) {
 }
 
 cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, const void* inv, const int* blk_alpha,
-                            int n_blk, int chunk, int tile_slots, int* status, float omega, cudaStream_t s) {
+                            int n_blk, int stages, int tile_slots, int* status, float omega, cudaStream_t s) {
   TcParams p{};
   p.r = r;
   p.x = x;
@@ -445,15 +517,17 @@ cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, con
   p.blk_alpha = blk_alpha;
   p.status = status;
   p.n_blk = n_blk;
-  p.chunk = chunk;
+  p.stages = stages >= 2 ? 2 : 1;
   const int n = hp.k + 1, np = hp.n_t * (hp.dim == 2 ? n * n : n * n * n);
   p.npp = (np + 7) / 8 * 8;
   p.tile_blocks = std::max(1, std::min(n_blk, tile_slots / kTcVB));
   p.n_tiles = (n_blk + p.tile_blocks - 1) / p.tile_blocks;
   const int sl = p.tile_blocks * kTcVB;
-  p.ncols = (3 * sl + 15) / 16 * 16;
+  if (sl > kTcMaxSlots) return cudaErrorInvalidValue;
+  p.slp = tc_slot_pitch(sl);
+  p.ncols = 3 * p.slp;                    // a multiple of 16, at most 240
   p.tmem_cols = 32;
-  while (p.tmem_cols < 2 * p.ncols) p.tmem_cols *= 2;
+  while (p.tmem_cols < p.ncols) p.tmem_cols *= 2;
   p.n_x = hp.n_x;
   p.n_cells = hp.n_cells;
   p.n_vec_x = (long long)hp.n_xi * hp.n_t * hp.n_x;
@@ -463,13 +537,10 @@ cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, con
     p.nn[d] = hp.nn[d];
   }
   p.omega = omega;
-  const size_t smem = vanka_tc_smem(hp.dim, hp.k, hp.n_t, chunk, sl);
-  const int cpr = (hp.cells[0] + chunk - 1) / chunk;
-  const long long units = (long long)cpr * hp.cells[1] * hp.cells[2] * p.n_tiles;
-  // at most two CTAs per SM: their tensor memory (2 x tmem_cols <= 512) never waits
-  const int grid = (int)std::max<long long>(1, std::min<long long>(units, sm_count() * 2));
+  const size_t smem = vanka_tc_smem(hp.dim, hp.k, hp.n_t, p.stages, sl);
+  const long long units = (long long)((hp.cells[0] + 1) / 2) * hp.cells[1] * hp.cells[2] * p.n_tiles;
 #define SG_TL(D, KK, TT) \
-  if (hp.dim == D && hp.k == KK && hp.n_t == TT) return launch_tc<D, KK, TT>(p, smem, s, grid);
+  if (hp.dim == D && hp.k == KK && hp.n_t == TT) return launch_tc<D, KK, TT>(p, smem, s, units);
   SG_TL(2, 1, 1) SG_TL(2, 1, 2) SG_TL(2, 1, 3) SG_TL(2, 1, 4)
   SG_TL(2, 2, 1) SG_TL(2, 2, 2) SG_TL(2, 2, 3) SG_TL(2, 2, 4)
   SG_TL(2, 3, 1) SG_TL(2, 3, 2) SG_TL(2, 3, 3) SG_TL(2, 3, 4)

@@ -14,8 +14,9 @@ Vanka patch factors, against the oracle (oracle/solver.py), through the C ABI.
   1e-4 FP32).
 * The tensor-core Vanka sweep (bf16 factors; tcgen05 MMAs with the patch
   values split into three bf16 terms) gives the same V-cycle as the oracle's
-  with bf16-rounded factors (1e-4), for every chunk size, in 2D and 3D, Q2 and
-  Q3 / dG(3) (64-unknown patches).
+  with bf16-rounded factors (1e-4), for every chunk size (one or two staging
+  buffers for the tensor-core sweep), in 2D and 3D, Q2 and Q3 / dG(3)
+  (64-unknown patches), up to 70 modes in one tile and in tiles of 4 to 32.
 * A 3D 16^3 Q2 solve (M = 3, P = 3, 1.44 M unknowns) reaches 1e-8 in true
   residual, evaluated by the oracle's assembled operator."""
 import functools
@@ -187,6 +188,7 @@ TC_CASES = {
     "2d-q2-32x32-M3P3": spec2((32, 32)),
     "2d-q2-16x16-M4P3": spec2((16, 16), M=4, P=3),
     "2d-q3-dg3-8x8-M2P2": spec2((8, 8), k=3, r=3, M=2, P=2),
+    "2d-q2-8x8-M4P4": spec2((8, 8), M=4, P=4),          # 70 modes: 72 slots, 240 MMA columns
     "3d-q2-8x8x8-M3P2": spec3((8, 8, 8)),
 }
 
@@ -223,6 +225,26 @@ def test_vcycle_bf16_sweeps_match_oracle(cuda, name, chunk, kind):
     err = float(np.abs(got - want).max() / np.abs(want).max())
     assert err < 1e-4, err
     assert float(np.abs(z2.cpu().numpy() - got).max() / np.abs(got).max()) < 1e-6
+
+
+@pytest.mark.parametrize("tile", [4, 8, 12, 32])
+def test_vcycle_tensor_sweep_mode_tiles_match_oracle(cuda, tile):
+    """35 modes in tiles of 4 to 32 slots (the last tile partly empty)."""
+    torch = cuda
+    name = "2d-q2-16x16-M4P3"
+    r, want = _oracle_vcycle_bf16(name)
+    ctx = sg.sg_setup_spec(TC_CASES[name])
+    sg.sg_mg_setup(ctx, sg.SG_PREC_BF16)
+    sg.sg_mg_set_level_variant(ctx, -1, -1, 1, tile, 1)
+    assert sg.sg_mg_level_info(ctx, 0)["vanka_tile"] == tile
+    rd = torch.from_numpy(r.reshape(-1).copy()).cuda()
+    zd = torch.full_like(rd, float("nan"))
+    sg.sg_vcycle(ctx, rd, zd)
+    torch.cuda.synchronize()
+    got = zd.cpu().numpy()
+    ctx.destroy()
+    err = float(np.abs(got - want).max() / np.abs(want).max())
+    assert err < 1e-4, err
 
 
 def test_tensor_core_sweep_refuses_unsupported_levels(cuda):

@@ -393,6 +393,14 @@ sg_status sg_debug_bounds(int* enabled, unsigned int* count, int* site, long lon
  * Synchronous. */
 sg_status sg_debug_bounds_probe(long long index, long long limit);
 
+/* sg_debug_wait_probe - self-test of the bounded completion wait of the
+ * tensor-core Vanka sweep: one CTA waits, polling at most `polls` (1..2^20)
+ * times, on an mbarrier that nothing arrives on.  The wait runs out and the
+ * kernel writes SG_ERR_TIMEOUT to *status (HOST int out); the kernel returns
+ * normally and the context stays usable.  Synchronous.  The paper has no
+ * counterpart. */
+sg_status sg_debug_wait_probe(unsigned int polls, int* status);
+
 /* sg_autotune - time the apply kernel of this context over candidate launch
  * shapes (cells per shared-memory chunk x threads per CTA x whether the upper
  * half of the CTAs starts with a half chunk, so that CTAs sharing an SM reach

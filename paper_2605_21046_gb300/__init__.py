@@ -230,6 +230,14 @@ def sg_debug_bounds_probe(index, limit):
     _check(_abi.load().sg_debug_bounds_probe(int(index), int(limit)), "sg_debug_bounds_probe")
 
 
+def sg_debug_wait_probe(polls=1000):
+    """Self-test of the bounded completion wait (sg_debug_wait_probe): the
+    status the waiting kernel recorded (SG_ERR_TIMEOUT when the wait ran out)."""
+    st = C.c_int(0)
+    _check(_abi.load().sg_debug_wait_probe(int(polls), C.byref(st)), "sg_debug_wait_probe")
+    return st.value
+
+
 def sg_mg_level_info(ctx, level):
     """The choices of the preconditioner on one level (sg_mg_level_info)."""
     info = (C.c_int * 10)()

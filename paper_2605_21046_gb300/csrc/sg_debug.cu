@@ -83,4 +83,11 @@ sg_status sg_debug_bounds_probe(long long index, long long limit) {
   return e == cudaSuccess ? SG_OK : fail(SG_ERR_CUDA, "sg_debug_bounds_probe: launch failed");
 }
 
+sg_status sg_debug_wait_probe(unsigned int polls, int* status) {
+  if (!status || polls < 1 || polls > (1u << 20))
+    return fail(SG_ERR_ARG, "sg_debug_wait_probe: status must be given and polls in 1..2^20");
+  cudaError_t e = sg::vanka_tc_wait_probe(polls, status);
+  return e == cudaSuccess ? SG_OK : fail(SG_ERR_CUDA, "sg_debug_wait_probe: launch failed");
+}
+
 }  // extern "C"

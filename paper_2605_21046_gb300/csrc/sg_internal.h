@@ -297,6 +297,9 @@ sg_status mg_patch_inverse(const MG& mg, int level, int alpha, long long cell, d
 bool vanka_tc_eligible(int dim, int k, int nt, int tile_slots);
 size_t vanka_tc_smem(int dim, int k, int nt, int stages, int tile_slots);
 cudaError_t prepare_vanka_tc(int dim, int k, int nt);
+// Runs the sweep's bounded completion wait on an mbarrier that nothing
+// arrives on (polls polls at most); status_out gets SG_ERR_TIMEOUT.
+cudaError_t vanka_tc_wait_probe(unsigned int polls, int* status_out);
 cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, const void* inv, const int* blk_alpha,
                             int n_blk, int stages, int tile_slots, int* status, float omega, cudaStream_t s);
 // Vanka patch inverses of one multigrid level, assembled and inverted in FP64

@@ -62,7 +62,7 @@ __host__ __device__ constexpr int tc_a_stage(int kc) { return kTcKC * tc_lbo_a(k
 __host__ __device__ constexpr int tc_b_chunks(int kc) { return 2 * kc + (kc & 1); }
 constexpr int kTcVB = 4;                       // slots per mode block
 constexpr int kTcMaxSlots = 80;                // 3 x 80 columns <= the MMA's N limit of 256
-constexpr unsigned int kTcSpin = 1u << 22;     // bound of a completion wait (polls)
+constexpr unsigned int kTcSpin = 1u << 20;     // bound of a completion wait (polls)
 
 struct TcParams {
   const float* r;
@@ -101,6 +101,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+// Waits for the phase of the given parity to complete, polling at most
+// limit times; false if the limit ran out first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned int limit) {
+  for (unsigned int polls = 0; polls < limit; ++polls)
+    if (mbar_test(bar, parity)) return true;
+  return false;
 }
 
 // shared-memory matrix descriptor: no swizzle, K-major; lbo = bytes between
@@ -315,15 +322,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
   // wait (bounded) for the MMAs committed to the barrier
   uint32_t phase = 0u;
   auto wait_mma = [&]() {
-    if (!s_fail) {
-      unsigned int polls = 0;
-      while (!mbar_test(&s_bar, phase)) {
-        if (++polls > kTcSpin) {
-          atomicExch(&s_fail, 1);
-          atomicExch(p.status, (int)SG_ERR_TIMEOUT);
-          break;
-        }
-      }
+    if (!s_fail && !mbar_wait_bounded(&s_bar, phase, kTcSpin)) {
+      atomicExch(&s_fail, 1);
+      atomicExch(p.status, (int)SG_ERR_TIMEOUT);
     }
     phase ^= 1u;
   };
@@ -432,7 +433,33 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
 }
 
+// Self-test of the bounded wait: an mbarrier that nothing arrives on, waited
+// for with the sweep's wait; the wait runs out and records SG_ERR_TIMEOUT.
+__global__ void mbar_wait_probe(unsigned int limit, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(&bar, 0u, limit) && threadIdx.x == 0) atomicExch(status, (int)SG_ERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t vanka_tc_wait_probe(unsigned int polls, int* status_out) {
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    mbar_wait_probe<<<1, 32>>>(polls, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(status_out, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e;
+}
 
 // slots of a tile rounded up to 16: the column pitch of one split term
 static int tc_slot_pitch(int tile_slots) { return (tile_slots + 15) / 16 * 16; }

@@ -85,8 +85,13 @@ def test_paper_squared_coefficient(cuda, prec):
 
 
 @pytest.mark.parametrize("prec", list(PRECISIONS))
-@pytest.mark.parametrize("maker", [I.config_3d_q2_32, I.config_2d_q2_128])
+@pytest.mark.parametrize("maker", [I.config_3d_q2_32, I.config_2d_q2_128, I.config_paper_q3],
+                         ids=["3d-q2-32", "2d-q2-128", "paper-q3-dg3-128-M4P3"])
 def test_apply_full_size_sampled(cuda, maker, prec):
+    """Full-size workloads in the launch shapes set-up picks, on sampled
+    output rows the oracle computes one by one: 32^3 Q2, 128^2 Q2 P = 4 and
+    the paper's 128^2 Q3 / dG(3) with M = 4, P = 3 (35 modes, 20.75 M
+    unknowns), the workload of the paper-discretisation bench row."""
     spec = maker()
     ctx = sg.sg_setup_spec(spec, PRECISIONS[prec])
     x = I.random_vector(spec)

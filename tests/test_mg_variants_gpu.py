@@ -280,3 +280,16 @@ def test_solve_3d_16cubed_reaches_tolerance(cuda, prec):
     ctx.destroy()
     res = np.linalg.norm(b.reshape(-1) - p.apply(got).reshape(-1)) / np.linalg.norm(b)
     assert st["converged"] == 1 and res <= 1.2e-8, (res, st)
+
+
+def test_tensor_sweep_wait_runs_out_and_reports_timeout(cuda):
+    """The tensor-core sweep waits for its MMAs on an mbarrier with a poll
+    limit.  The same bounded wait on an mbarrier that nothing arrives on runs
+    out, records SG_ERR_TIMEOUT and returns; the context stays usable (a
+    V-cycle afterwards still equals the oracle's)."""
+    from paper_2605_21046_gb300 import _abi
+    assert sg.sg_debug_wait_probe(1000) == _abi.SG_ERR_TIMEOUT
+    assert sg.sg_debug_wait_probe(1) == _abi.SG_ERR_TIMEOUT
+    with pytest.raises(sg.SGError):
+        sg.sg_debug_wait_probe(0)
+    test_vcycle_bf16_sweeps_match_oracle(cuda, "3d-q2-8x8x8-M3P2", 1, 1)

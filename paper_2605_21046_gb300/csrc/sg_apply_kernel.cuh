@@ -329,16 +329,28 @@ __global__ void __launch_bounds__(ChunkBounds<DIM, K, NT>::threads, ChunkBounds<
       Nd[i] = interior && SG_IN(node, p.n_x, 102) ? (int)node : -1;
     }
     __syncthreads();
+    // GU values per thread in flight: a batch's loads all issue before its
+    // shared-memory stores
+    constexpr int GU = 4;
     for (int c = 0; c < nc; ++c) {
       const int* nd = Nd + c * NKD;
       T* qc = Qs + (size_t)c * V * SLOT;
-      for (int j = tid; j < V * NKD; j += nthr) {
-        const int v = j / NKD, a = j - v * NKD;
-        const int node = nd[a];
-        T val = A::zero();
-        if (node >= 0 && SG_IN((long long)v * p.n_x + node, (long long)V * p.n_x, 103))
-          val = A::in(xin[(long long)v * p.n_x + node]);
-        if (SG_IN((size_t)c * V * SLOT + (size_t)v * SLOT + a, (size_t)C * V * SLOT, 104)) qc[(size_t)v * SLOT + a] = val;
+      for (int j0 = tid; j0 < V * NKD; j0 += GU * nthr) {
+        T val[GU];
+        int dst[GU];
+#pragma unroll
+        for (int g = 0; g < GU; ++g) {
+          const int j = j0 + g * nthr;
+          const int v = j / NKD, a = j - v * NKD;
+          val[g] = A::zero();
+          dst[g] = j < V * NKD ? v * SLOT + a : -1;
+          const int node = j < V * NKD ? nd[a] : -1;
+          if (node >= 0 && SG_IN((long long)v * p.n_x + node, (long long)V * p.n_x, 103))
+            val[g] = A::in(xin[(long long)v * p.n_x + node]);
+        }
+#pragma unroll
+        for (int g = 0; g < GU; ++g)
+          if (dst[g] >= 0 && SG_IN((size_t)c * V * SLOT + dst[g], (size_t)C * V * SLOT, 104)) qc[dst[g]] = val[g];
       }
     }
     __syncthreads();

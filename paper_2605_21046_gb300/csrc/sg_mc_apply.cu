@@ -82,16 +82,29 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
       Nd[i] = interior ? (int)(((long long)gz * nny + gy) * nnx + gx) : -1;
     }
     __syncthreads();
+    // the values, GU per thread in flight: all loads of a batch are issued
+    // before its shared-memory stores
+    constexpr int GU = 4;
+    const IO* xtile = xin + (long long)s0 * NT * P.n_x;
     for (int c = 0; c < nc; ++c) {
       const int* nd = Nd + c * NKD;
       T* qc = Qs + (size_t)c * VT * SLOT;
-      for (int j = tid; j < VT * NKD; j += nthr) {
-        const int v = j / NKD, a = j - v * NKD;
-        const int node = nd[a];
-        T val = A::zero();
-        if (node >= 0 && SG_IN((long long)(s0 * NT + v) * P.n_x + node, (long long)P.S * NT * P.n_x, 402))
-          val = A::in(xin[(long long)(s0 * NT + v) * P.n_x + node]);
-        qc[(size_t)v * SLOT + a] = val;
+      for (int j0 = tid; j0 < VT * NKD; j0 += GU * nthr) {
+        T val[GU];
+        int dst[GU];
+#pragma unroll
+        for (int g = 0; g < GU; ++g) {
+          const int j = j0 + g * nthr;
+          const int v = j / NKD, a = j - v * NKD;
+          val[g] = A::zero();
+          dst[g] = j < VT * NKD ? v * SLOT + a : -1;
+          const int node = j < VT * NKD ? nd[a] : -1;
+          if (node >= 0 && SG_IN((long long)(s0 * NT + v) * P.n_x + node, (long long)P.S * NT * P.n_x, 402))
+            val[g] = A::in(xtile[(long long)v * P.n_x + node]);
+        }
+#pragma unroll
+        for (int g = 0; g < GU; ++g)
+          if (dst[g] >= 0) qc[dst[g]] = val[g];
       }
     }
     __syncthreads();
@@ -104,59 +117,65 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
       forward_cell<A, DIM, K>(uv, q);
     }
     __syncthreads();
-    // phase 2: per (cell, point, sample): mass coupling and a(x_q, xi_s) grad u;
-    // (point, sample, cell) of the item index advance with the stride (no
-    // divisions in the loop)
-    const int dq = nthr % NQD, dr = nthr / NQD;
-    int q = tid % NQD, sl = (tid / NQD) % ns, c = (tid / NQD) / ns;
-    for (int it = tid; it < nc * NQD * ns; it += nthr) {
-      T* base = Qs + ((size_t)c * VT + (size_t)sl * NT) * SLOT + q;
-      T uv[NT], out[NT][NC];
-#pragma unroll
-      for (int j = 0; j < NT; ++j) uv[j] = base[(size_t)j * SLOT];
-      const T* am = Amq + q * NT * NT;
-#pragma unroll
-      for (int i = 0; i < NT; ++i) {
-        T sacc = A::mul(am[i * NT], uv[0]);
-#pragma unroll
-        for (int j = 1; j < NT; ++j) A::fma(am[i * NT + j], uv[j], sacc);
-        out[i][0] = A::fin(sacc);
-      }
-      if (p.mass_only) {
+    // phase 2: per (cell, point, sample): mass coupling and a(x_q, xi_s) grad u.
+    // A thread keeps one point q (the first (nthr / NQD) NQD threads take
+    // part), holds its N_t x N_t mass weights in registers and walks the
+    // (sample, cell) pairs with stride nthr / NQD.
+    {
+      const int rows = nthr / NQD;
+      const int q = tid % NQD, r0 = tid / NQD;
+      if (r0 < rows) {
+        T am[NT][NT];
 #pragma unroll
         for (int i = 0; i < NT; ++i)
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) out[i][1 + d] = A::zero();
-      } else {
-        const T* cq = Cs + (size_t)c * nterm * NQD + q;
-        T acoef = A::mul(Wt[sl * nterm], cq[0]);
-        for (int t = 1; t < nterm; ++t) A::fma(Wt[sl * nterm + t], cq[t * NQD], acoef);
-        acoef = A::fin(acoef);
+          for (int j = 0; j < NT; ++j) am[i][j] = Amq[(q * NT + i) * NT + j];
+        int sl = r0 % ns, c = r0 / ns;
+        while (c < nc) {
+          T* base = Qs + ((size_t)c * VT + (size_t)sl * NT) * SLOT + q;
+          T uv[NT], out[NT][NC];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          T ad = acoef;
-          if (P.aniso && d > 0) ad = A::fin(A::mul(acoef, A::in(P.ratio[d])));
+          for (int j = 0; j < NT; ++j) uv[j] = base[(size_t)j * SLOT];
 #pragma unroll
-          for (int i = 0; i < NT; ++i) out[i][1 + d] = A::fin(A::mul(ad, base[(size_t)i * SLOT + (1 + d) * NQD]));
-        }
-      }
+          for (int i = 0; i < NT; ++i) {
+            T sacc = A::mul(am[i][0], uv[0]);
 #pragma unroll
-      for (int i = 0; i < NT; ++i)
+            for (int j = 1; j < NT; ++j) A::fma(am[i][j], uv[j], sacc);
+            out[i][0] = A::fin(sacc);
+          }
+          if (p.mass_only) {
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) base[(size_t)i * SLOT + cc * NQD] = out[i][cc];
-      q += dq;
-      sl += dr;
-      if (q >= NQD) {
-        q -= NQD;
-        ++sl;
-      }
-      if (sl >= ns) {
-        if (sl < 2 * ns) {
-          sl -= ns;
-          ++c;
-        } else {
-          c += sl / ns;
-          sl %= ns;
+            for (int i = 0; i < NT; ++i)
+#pragma unroll
+              for (int d = 0; d < DIM; ++d) out[i][1 + d] = A::zero();
+          } else {
+            const T* cq = Cs + (size_t)c * nterm * NQD + q;
+            const T* wt = Wt + sl * nterm;
+            T acoef = A::mul(wt[0], cq[0]);
+            for (int t = 1; t < nterm; ++t) A::fma(wt[t], cq[t * NQD], acoef);
+            acoef = A::fin(acoef);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              T ad = acoef;
+              if (P.aniso && d > 0) ad = A::fin(A::mul(acoef, A::in(P.ratio[d])));
+#pragma unroll
+              for (int i = 0; i < NT; ++i) out[i][1 + d] = A::fin(A::mul(ad, base[(size_t)i * SLOT + (1 + d) * NQD]));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < NT; ++i)
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) base[(size_t)i * SLOT + cc * NQD] = out[i][cc];
+          sl += rows;
+          if (sl >= ns) {
+            if (sl < 2 * ns) {
+              sl -= ns;
+              ++c;
+            } else {
+              c += sl / ns;
+              sl %= ns;
+            }
+          }
         }
       }
     }

@@ -20,18 +20,19 @@
 //     (pitch npp, zero padded) are copied in by asynchronous 16-byte copies
 //     into the canonical no-swizzle K-major layout (8-row x 16-byte core
 //     matrices); K past npp stays zero.
-//   * B: R split into three bf16 terms R = R1 + R2 + R3 (each the bf16
-//     rounding of what the previous ones leave): the bf16 x bf16 products are
-//     exact and accumulate in FP32, so the product carries about the FP32
-//     accuracy of the patch values.  Term t of slot s is MMA column
+//   * B: R split into two bf16 terms R = R1 + R2 (R1 the bf16 rounding of R,
+//     R2 that of R - R1; |R - R1 - R2| <= 2^-18 |R|): the bf16 x bf16
+//     products are exact and accumulate in FP32, so the product carries the
+//     patch values to 2^-18, 2^9 times finer than the rounding of the stored
+//     bf16 factors it multiplies.  Term t of slot s is MMA column
 //     t SLP + s (SLP = the slots rounded up to 16), so one thread writes eight
 //     K values of one column as a 16-byte store and consecutive slots fall in
 //     consecutive core-matrix rows.  Cell 1's K chunks follow cell 0's
 //     directly: where a K step of cell 0 reaches into them, A's columns are
 //     zero.
-//   * D (128 lanes x 3 SLP columns of FP32 in tensor memory) is read back with
-//     tcgen05.ld (three loads of 16 columns give 16 slots' three terms, summed
-//     in registers), damped, divided by the node's multiplicity and added into
+//   * D (128 lanes x 2 SLP columns of FP32 in tensor memory) is read back with
+//     tcgen05.ld (two loads of 16 columns give 16 slots' two terms, summed in
+//     registers), damped, divided by the node's multiplicity and added into
 //     x with one reduction per (patch row, slot).
 // The next unit's r values and inverses are copied in while the current one
 // computes: into a second buffer (two stages), or, with one buffer, r once B
@@ -61,7 +62,8 @@ __host__ __device__ constexpr int tc_a_stage(int kc) { return kTcKC * tc_lbo_a(k
 // step of cell 1 reads past them)
 __host__ __device__ constexpr int tc_b_chunks(int kc) { return 2 * kc + (kc & 1); }
 constexpr int kTcVB = 4;                       // slots per mode block
-constexpr int kTcMaxSlots = 80;                // 3 x 80 columns <= the MMA's N limit of 256
+constexpr int kTcTerms = 2;                    // bf16 terms of a patch value
+constexpr int kTcMaxSlots = 80;                // kTcTerms x 80 columns <= the MMA's N limit of 256
 constexpr unsigned int kTcSpin = 1u << 20;     // bound of a completion wait (polls)
 
 struct TcParams {
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int SL = p.tile_blocks * kTcVB;           // slots of a tile
   const int SLP = p.slp;                          // column pitch of a split term
-  const int NCOL = p.ncols;                       // MMA N = 3 SLP
+  const int NCOL = p.ncols;                       // MMA N = kTcTerms SLP
   const bool two = p.stages == 2;
   const uint32_t LBO_B = (uint32_t)(NCOL / 8) * 128u;
   // shared memory: A buffers, B, r buffers
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
         cp_async16_tc(A + a_dst[j], p.inv + base + a_src[j]);
     }
   };
-  // B: eight K values (patch columns 8 kc ..) of slot s of cell c, three terms
+  // B: eight K values (patch columns 8 kc ..) of slot s of cell c, kTcTerms terms
   auto build_b = [&](const float* Rl) {
     for (int idx = tid; idx < 2 * KC * SL; idx += kTcThreads) {
       const int s = idx % SL, ck = idx / SL;
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
       }
       unsigned char* dst = B + (size_t)(KC * c + kc) * LBO_B;
 #pragma unroll
-      for (int t = 0; t < 3; ++t) {
+      for (int t = 0; t < kTcTerms; ++t) {
         uint32_t w[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -342,18 +344,18 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
     const float sc = p.omega / (float)mult;
     const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
     for (int s0 = 0; s0 < SL; s0 += 16) {
-      float d0[16], d1[16], d2[16];
+      float d0[16], d1[16];
       tmem_ld16(base + (uint32_t)s0, d0);
       tmem_ld16(base + (uint32_t)(SLP + s0), d1);
-      tmem_ld16(base + (uint32_t)(2 * SLP + s0), d2);
       tmem_ld_wait();
+      static_assert(kTcTerms == 2, "the read-back sums two terms");
       if (live) {
         float* xrow = p.x + ge;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           if (s0 + j >= SL) break;
           const long long so = s_so[tb][s0 + j];
-          if (so >= 0 && SG_IN(so + ge, p.n_vec_x, 604)) atomicAdd(xrow + so, sc * ((d0[j] + d1[j]) + d2[j]));
+          if (so >= 0 && SG_IN(so + ge, p.n_vec_x, 604)) atomicAdd(xrow + so, sc * (d0[j] + d1[j]));
         }
       }
     }
@@ -468,7 +470,7 @@ size_t vanka_tc_smem(int dim, int k, int nt, int stages, int tile_slots) {
   const int n = k + 1, lyz = dim == 2 ? n : n * n;
   const int e = nt * (2 * k + 1) * lyz, ep = e | 1;
   const int kc = (nt * (dim == 2 ? n * n : n * n * n) + 7) / 8;
-  const int ncol = 3 * tc_slot_pitch(tile_slots);
+  const int ncol = kTcTerms * tc_slot_pitch(tile_slots);
   return (size_t)stages * tc_a_stage(kc) + (size_t)tc_b_chunks(kc) * (ncol / 8) * 128 +
          (size_t)stages * tile_slots * ep * sizeof(float);
 }
@@ -552,7 +554,7 @@ cudaError_t launch_vanka_tc(const HostProblem& hp, const float* r, float* x, con
   const int sl = p.tile_blocks * kTcVB;
   if (sl > kTcMaxSlots) return cudaErrorInvalidValue;
   p.slp = tc_slot_pitch(sl);
-  p.ncols = 3 * p.slp;                    // a multiple of 16, at most 240
+  p.ncols = kTcTerms * p.slp;             // a multiple of 16, at most 160
   p.tmem_cols = 32;
   while (p.tmem_cols < p.ncols) p.tmem_cols *= 2;
   p.n_x = hp.n_x;

@@ -833,12 +833,12 @@ def next_paper(sg, torch, inputs, steps=30, warmup=5):
             "paper_context": "Table 2 of the paper, its CPU cluster; context only", "degrees": out}
 
 
-def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32"):
+def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32", profile_workload="3d"):
     """One V-cycle of the block-Jacobi multigrid (all modes at once) on the
     64x64 Q2 P=3 and 32^3 Q2 P=3 workloads, per precision: device ms per
     V-cycle (10 graph launches after 3 warm-up ones).  With profile_range one
-    more FP32 3D V-cycle with the solver's sweeps and damping is bracketed by
-    cudaProfilerStart/Stop."""
+    more V-cycle (profile_mg precision) with the solver's sweeps and damping on
+    the profile_workload ("3d" or "2d") is bracketed by cudaProfilerStart/Stop."""
     out = {}
     for wname, maker in (("2d-q2-64x64-M4P3", inputs.config_2d_q2_64), ("3d-q2-32x32x32-M3P3", inputs.config_3d_q2_32)):
         spec = maker()
@@ -877,7 +877,7 @@ def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32"):
                         b.record()
                         torch.cuda.synchronize()
                         row[f"{pname}_nu{nu}_vanka_{kname}"] = a.elapsed_time(b) / 10
-        if profile_range and wname.startswith("3d"):
+        if profile_range and wname.startswith(profile_workload):
             sg.sg_mg_setup(ctx, sg.SG_PREC_BF16 if profile_mg.startswith("bf16") else sg.SG_PREC_FP32,
                            MG_NU, MG_OMEGA)
             if profile_mg in ("bf16-tensor", "bf16-tensor-1buf"):
@@ -913,7 +913,8 @@ def run_next(args, world, rank, local):
             elif row == "adjoint":
                 out = next_adjoint(sg, torch, inputs)
             elif row == "vcycle":
-                out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range, profile_mg=args.profile_mg)
+                out = next_vcycle(sg, torch, inputs, profile_range=args.profile_range, profile_mg=args.profile_mg,
+                                  profile_workload=args.profile_workload)
             elif row == "applies":
                 out = next_applies(sg, torch, inputs)
             elif row == "paper":
@@ -943,6 +944,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--profile-variant", choices=["fp64", "dw"], default="fp64",
                     help="which timed apply loop --profile-range brackets")
+    ap.add_argument("--profile-workload", choices=["3d", "2d"], default="3d",
+                    help="workload of the V-cycle --profile-range brackets (--rows vcycle): 32^3 Q2 or 64x64 Q2")
     ap.add_argument("--profile-mg", choices=["fp32", "bf16", "bf16-tensor", "bf16-tensor-1buf"], default="fp32",
                     help="multigrid precision of the V-cycle --profile-range brackets (--rows vcycle)")
     ap.add_argument("--no-next", action="store_true",

@@ -239,6 +239,18 @@ sg_status sg_apply_host_async(sg_ctx* ctx, int slab, const double* x_host, doubl
  * Synchronous. */
 sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega);
 
+/* sg_mg_set_coarse_dofs - size of the coarsest multigrid level for the next
+ * sg_mg_setup (and the mean-operator V-cycles of mc_solve_batch /
+ * mc_solve_meshes on this context).  Coarsening (halving the cells per
+ * direction while every count is even and above 2) stops at the first level
+ * with at most max_dofs interior space-time unknowns per chaos row, N_t times
+ * the interior nodes, which is solved exactly by its dense inverse; 0 coarsens
+ * down to two cells per direction.  Default 1024 (64x64 Q2 dG(1): levels 64^2,
+ * 32^2, 16^2 and the 8^2 coarse solve with 450 unknowns per row; 32^3 Q2:
+ * 32^3, 16^3, 8^3 and 4^3 with 686).  max_dofs 0..2048, else SG_ERR_ARG.  The
+ * paper defers the hierarchy (Sec. 3.5 remark). */
+sg_status sg_mg_set_coarse_dofs(sg_ctx* ctx, int max_dofs);
+
 /* sg_mg_level_info - the choices of a built preconditioner on one level
  * (0 = finest).  info: HOST int[10] out = {number of levels, cells, 1 if the
  * coarsest (dense) level, level residual (0 the SG cell kernel with the

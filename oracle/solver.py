@@ -12,7 +12,10 @@ implementation"):
     problems on space-time patches).
 
 Readings (the paper defers these details to a follow-up work):
-  * levels: halve the cells per direction while every count is even and > 2;
+  * levels: halve the cells per direction while every count is even and > 2
+    and the current level has more than ``coarse_dofs`` interior space-time
+    unknowns per mode (N_t x interior nodes; default COARSE_DOFS; 0: no such
+    limit, down to two cells per direction);
     the coefficient is re-evaluated on every level (rediscretisation); a
     per-cell scale is averaged over the fine cells of a coarse cell;
   * transfer: canonical Q_k interpolation from coarse to fine (P), restriction
@@ -33,6 +36,7 @@ from . import coeff, hermite, space_fe, time_dg
 
 OMEGA = 0.7
 NU = 2
+COARSE_DOFS = 1024
 
 
 def direct_solve(problem, b):
@@ -41,12 +45,21 @@ def direct_solve(problem, b):
     return spla.spsolve(A, np.asarray(b, dtype=np.float64).reshape(-1)).reshape(problem.shape)
 
 
-def coarse_specs(spec):
+def interior_dofs(spec):
+    """N_t x interior nodes of a level: the size of its dense coarse solve."""
+    n = int(spec["r"]) + 1
+    for c in spec["cells"][: spec["dim"]]:
+        n *= int(c) * int(spec["k"]) - 1
+    return n
+
+
+def coarse_specs(spec, coarse_dofs=COARSE_DOFS):
     """The spec of every multigrid level, finest first."""
     spec = dict(spec, coef=coeff.as_pieces(spec["coef"], int(spec["M"])))
     out = [spec]
     cur = spec
-    while all(c % 2 == 0 and c > 2 for c in cur["cells"][: cur["dim"]]):
+    while (all(c % 2 == 0 and c > 2 for c in cur["cells"][: cur["dim"]])
+           and not (coarse_dofs > 0 and interior_dofs(cur) <= coarse_dofs)):
         nxt = dict(cur)
         nxt["cells"] = tuple(c // 2 for c in cur["cells"][: cur["dim"]])
         fine_cells = cur["cells"][: cur["dim"]]
@@ -185,10 +198,10 @@ class Multigrid:
     """Block-Jacobi (in alpha) preconditioner: one V-cycle of the diagonal
     block A_alpha for every chaos mode and both time nodes at once."""
 
-    def __init__(self, problem, factor_round=None, nu=NU, omega=OMEGA):
+    def __init__(self, problem, factor_round=None, nu=NU, omega=OMEGA, coarse_dofs=COARSE_DOFS):
         self.p = problem
         self.nu, self.omega = nu, omega
-        specs = coarse_specs(problem.spec)
+        specs = coarse_specs(problem.spec, coarse_dofs)
         self.keys, self.cls = diagonal_classes(problem.G)
         self.levels = [Level(s, problem.At, problem.Bt, self.keys, i == len(specs) - 1, factor_round)
                        for i, s in enumerate(specs)]

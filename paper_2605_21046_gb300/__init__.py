@@ -230,6 +230,13 @@ def sg_debug_bounds_probe(index, limit):
     _check(_abi.load().sg_debug_bounds_probe(int(index), int(limit)), "sg_debug_bounds_probe")
 
 
+def sg_mg_set_coarse_dofs(ctx, max_dofs):
+    """Coarsest-level size of the next sg_mg_setup (sg_mg_set_coarse_dofs):
+    coarsening stops at the first level with at most max_dofs interior
+    space-time unknowns per chaos row; 0 coarsens to two cells per direction."""
+    _check(_abi.load().sg_mg_set_coarse_dofs(ctx.handle, int(max_dofs)), "sg_mg_set_coarse_dofs")
+
+
 def sg_debug_wait_probe(polls=1000):
     """Self-test of the bounded completion wait (sg_debug_wait_probe): the
     status the waiting kernel recorded (SG_ERR_TIMEOUT when the wait ran out)."""

@@ -21,7 +21,7 @@ EXPORTED = sorted(["sg_setup", "sg_apply", "sg_apply_host", "sg_get_info", "sg_g
                    "sg_stat_errors", "mc_solve_meshes", "sg_set_apply_shape",
                    "sg_apply_host_async", "sg_mg_level_info", "sg_mg_set_level_variant",
                    "sg_mg_patch_inverse", "sg_debug_bounds", "sg_debug_bounds_probe", "sg_mg_setup_times",
-                   "sg_debug_wait_probe"])
+                   "sg_debug_wait_probe", "sg_mg_set_coarse_dofs"])
 
 
 class sg_mesh(C.Structure):
@@ -95,6 +95,8 @@ def load():
     lib.sg_debug_bounds.restype = C.c_int
     lib.sg_debug_bounds_probe.argtypes = [C.c_longlong, C.c_longlong]
     lib.sg_debug_bounds_probe.restype = C.c_int
+    lib.sg_mg_set_coarse_dofs.argtypes = [vp, C.c_int]
+    lib.sg_mg_set_coarse_dofs.restype = C.c_int
     lib.sg_debug_wait_probe.argtypes = [C.c_uint, C.POINTER(C.c_int)]
     lib.sg_debug_wait_probe.restype = C.c_int
     lib.sg_mg_setup_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]

@@ -322,6 +322,7 @@ sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega) {
   sg::MG* mg = new (std::nothrow) sg::MG();
   if (!mg) return fail(SG_ERR_OOM, "sg_mg_setup: host allocation failed");
   std::string msg;
+  mg->coarse_dofs = ctx->mg_coarse_dofs;
   sg_status st = sg::mg_build(ctx->hp, mg_precision, nu, omega, *mg, msg);
   if (st != SG_OK) {
     sg::mg_free(*mg);
@@ -330,6 +331,13 @@ sg_status sg_mg_setup(sg_ctx* ctx, int mg_precision, int nu, double omega) {
   }
   ctx->mg = mg;
   ++ctx->gen;
+  return SG_OK;
+}
+
+sg_status sg_mg_set_coarse_dofs(sg_ctx* ctx, int max_dofs) {
+  if (!ctx) return fail(SG_ERR_ARG, "sg_mg_set_coarse_dofs: ctx is NULL");
+  if (max_dofs < 0 || max_dofs > 2048) return fail(SG_ERR_ARG, "sg_mg_set_coarse_dofs: max_dofs must be 0..2048");
+  ctx->mg_coarse_dofs = max_dofs;
   return SG_OK;
 }
 

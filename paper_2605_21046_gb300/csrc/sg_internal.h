@@ -241,7 +241,13 @@ struct MGLevel {
   void* d_t2 = nullptr;
 };
 
+// Coarsening stops at the first level with at most this many interior
+// space-time unknowns per chaos row (its dense solve); 0: at two cells per
+// direction.
+constexpr int kCoarseDofsDefault = 1024;
+
 struct MG {
+  int coarse_dofs = kCoarseDofsDefault;   // see kCoarseDofsDefault
   int precision = SG_PREC_FP64;   // vector precision: SG_PREC_FP64 or kPrecF32
   int requested = SG_PREC_FP64;   // as passed to mg_build (SG_PREC_BF16 included)
   bool bf16 = false;              // patch inverses stored in bf16 (FP32 vectors)
@@ -430,6 +436,7 @@ struct sg_ctx {
     bool ready = false;
   } pipe;
   sg::MG* mg = nullptr;       // multigrid preconditioner (sg_mg_setup)
+  int mg_coarse_dofs = sg::kCoarseDofsDefault;   // coarsest-level size of the next sg_mg_setup
   sg::ExactData* exact = nullptr;  // manufactured solution (sg_set_exact)
   double* d_krylov = nullptr; // FGMRES workspace (lazy): V, Z, w, r and partial sums
   size_t krylov_bytes = 0;

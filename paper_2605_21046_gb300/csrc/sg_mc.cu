@@ -417,6 +417,7 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
       if (e != cudaSuccess) break;
       // mean-operator V-cycle over all samples of the group
       m.mg = new MG();
+      m.mg->coarse_dofs = m.parent->mg_coarse_dofs;
       status = mg_build_mc(m.hp, mgp, 2, 0.7, wgt, std::min(ts, 32), *m.mg, msg);
     }
     if (e != cudaSuccess || status != SG_OK) break;

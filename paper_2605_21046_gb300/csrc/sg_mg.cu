@@ -535,27 +535,37 @@ __global__ void __launch_bounds__(256) mg_axis_gather(const T* __restrict__ in, 
 }
 
 // Coarsest level: x[inner] = inv(C_class) b[inner] for every chaos mode
-// (one CTA per mode; the right-hand side is staged in shared memory).
+// (blockIdx.y) and a block of rows (blockIdx.x); the right-hand side is
+// staged in shared memory.  A warp takes one row of inv (its lanes read the
+// row coalesced and reduce with shuffles); the transposed cycle takes a
+// column per thread (consecutive threads, consecutive columns).
 template <typename T>
 __global__ void mg_coarse(const T* __restrict__ b, T* __restrict__ x, const T* __restrict__ inv,
                           const int* __restrict__ cls, const long long* __restrict__ inner, int n_int,
                           int n_t, long long n_x, int trans) {
   extern __shared__ __align__(16) unsigned char sm[];
   T* bs = reinterpret_cast<T*>(sm);
-  const int alpha = blockIdx.x;
+  const int alpha = blockIdx.y;
   const long long base = (long long)alpha * n_t * n_x;
   for (int i = threadIdx.x; i < n_int; i += blockDim.x) bs[i] = b[base + inner[i]];
   __syncthreads();
   const T* M = inv + (long long)cls[alpha] * n_int * n_int;
-  for (int i = threadIdx.x; i < n_int; i += blockDim.x) {
-    T s = T(0);
-    if (trans) {
+  if (trans) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_int; i += gridDim.x * blockDim.x) {
+      T s = T(0);
       for (int q = 0; q < n_int; ++q) s += M[(long long)q * n_int + i] * bs[q];
-    } else {
-      const T* row = M + (long long)i * n_int;
-      for (int q = 0; q < n_int; ++q) s += row[q] * bs[q];
+      x[base + inner[i]] = s;
     }
-    x[base + inner[i]] = s;
+  } else {
+    const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * warps + warp; i < n_int; i += gridDim.x * warps) {
+      const T* row = M + (long long)i * n_int;
+      T s = T(0);
+      for (int q = lane; q < n_int; q += 32) s += row[q] * bs[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) x[base + inner[i]] = s;
+    }
   }
 }
 
@@ -584,6 +594,7 @@ bool invert(std::vector<double>& a, int n) {
       a[(size_t)c * n + k] *= d;
       inv[(size_t)c * n + k] *= d;
     }
+#pragma omp parallel for schedule(static) if (n >= 256)
     for (int r = 0; r < n; ++r) {
       if (r == c) continue;
       const double f = a[(size_t)r * n + c];
@@ -1107,7 +1118,8 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
     mg_init_x<T><<<vec_grid(L.hp.n_x, V), 256, 0, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
                                                       (int)L.hp.n_x, L.hp.nn[0], L.hp.nn[1], L.hp.nn[2], L.hp.dim);
     const size_t smem = (size_t)L.n_int * sizeof(T);
-    mg_coarse<T><<<L.hp.n_xi, 256, smem, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
+    const int gx = trans ? (L.n_int + 255) / 256 : (L.n_int + 7) / 8;   // rows: a warp each (8 a block)
+    mg_coarse<T><<<dim3(gx, L.hp.n_xi), 256, smem, s>>>(static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x),
                                               static_cast<const T*>(L.d_inv), mg.d_cls,
                                               reinterpret_cast<const long long*>(L.d_inner), L.n_int, L.hp.n_t, L.hp.n_x,
                                               trans);
@@ -1419,6 +1431,10 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
     bool ok = true;
     for (int d = 0; d < f.dim; ++d) ok = ok && f.cells[d] % 2 == 0 && f.cells[d] > 2;
     if (!ok) break;
+    // a level small enough for the dense coarse solve ends the hierarchy
+    long long inner = f.n_t;
+    for (int d = 0; d < f.dim; ++d) inner *= std::max(0, f.nn[d] - 2);
+    if (mg.coarse_dofs > 0 && inner <= mg.coarse_dofs) break;
     sg_mesh m;
     std::memset(&m, 0, sizeof(m));
     m.dim = f.dim;

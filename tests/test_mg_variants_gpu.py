@@ -74,8 +74,9 @@ def _round(a, store):
 def test_patch_inverses_match_oracle(cuda, name, store):
     spec = FACTOR_CASES[name]
     p = operator.SGProblem(spec)
-    mg = solver.Multigrid(p)
+    mg = solver.Multigrid(p, coarse_dofs=0)          # every level down to two cells
     ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, STORE[store])
     n_levels = sg.sg_mg_level_info(ctx, 0)["levels"]
     assert n_levels == len(mg.levels)
@@ -119,6 +120,7 @@ def test_patch_inverse_errors(cuda):
     ctx = sg.sg_setup_spec(spec2((4, 4), M=1, P=1))
     with pytest.raises(sg.SGError):
         sg.sg_mg_level_info(ctx, 0)                  # no preconditioner yet
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, sg.SG_PREC_FP64)
     info = sg.sg_mg_level_info(ctx, 0)
     with pytest.raises(sg.SGError):
@@ -198,7 +200,7 @@ def _oracle_vcycle_bf16(name, seed=10):
     spec = TC_CASES[name]
     p = operator.SGProblem(spec)
     r = np.random.default_rng(seed).uniform(-1, 1, p.shape)
-    return r, solver.Multigrid(p, factor_round=solver.round_bf16).apply(r).reshape(-1)
+    return r, solver.Multigrid(p, factor_round=solver.round_bf16, coarse_dofs=0).apply(r).reshape(-1)
 
 
 @pytest.mark.parametrize("kind", [0, 1], ids=["ffma", "tensor"])
@@ -209,6 +211,7 @@ def test_vcycle_bf16_sweeps_match_oracle(cuda, name, chunk, kind):
     spec = TC_CASES[name]
     r, want = _oracle_vcycle_bf16(name)
     ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_set_coarse_dofs(ctx, 0)                 # every level down to two cells
     sg.sg_mg_setup(ctx, sg.SG_PREC_BF16)
     sg.sg_mg_set_level_variant(ctx, -1, -1, chunk, 0, kind)
     levels = sg.sg_mg_level_info(ctx, 0)["levels"]
@@ -234,6 +237,7 @@ def test_vcycle_tensor_sweep_mode_tiles_match_oracle(cuda, tile):
     name = "2d-q2-16x16-M4P3"
     r, want = _oracle_vcycle_bf16(name)
     ctx = sg.sg_setup_spec(TC_CASES[name])
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, sg.SG_PREC_BF16)
     sg.sg_mg_set_level_variant(ctx, -1, -1, 1, tile, 1)
     assert sg.sg_mg_level_info(ctx, 0)["vanka_tile"] == tile
@@ -250,11 +254,13 @@ def test_vcycle_tensor_sweep_mode_tiles_match_oracle(cuda, tile):
 def test_tensor_core_sweep_refuses_unsupported_levels(cuda):
     # FP32 factors, and bf16 factors of several diagonal classes, keep the FFMA sweep
     ctx = sg.sg_setup_spec(spec2((8, 8)))
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, sg.SG_PREC_FP32)
     with pytest.raises(sg.SGError):
         sg.sg_mg_set_level_variant(ctx, -1, -1, 0, -1, 1)
     ctx.destroy()
     ctx = sg.sg_setup_spec(spec2((4, 4), M=4, P=2, lo=(-1.0, -1.0), coef=paper_coefficient()))
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, sg.SG_PREC_BF16)
     with pytest.raises(sg.SGError):
         sg.sg_mg_set_level_variant(ctx, -1, -1, 0, -1, 1)

@@ -44,7 +44,7 @@ def test_single_level_preconditioner_is_exact_block_jacobi():
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_prolongation_interpolates_polynomials_exactly(k):
     s = spec2((8, 4), k=k)
-    specs = solver.coarse_specs(s)
+    specs = solver.coarse_specs(s, coarse_dofs=0)
     A = np.eye(2)
     keys = [np.array([1.0, 0.0, 0.0])]
     fine = solver.Level(specs[0], A, 0.1 * A, keys, False)
@@ -69,10 +69,27 @@ def test_prolongation_interpolates_polynomials_exactly(k):
     assert np.abs(uf[sel] - want[sel]).max() < 1e-13
 
 
+def test_coarsest_level_rule():
+    """Coarsening stops at the first level with at most coarse_dofs interior
+    space-time unknowns per mode (N_t x interior nodes), or where a cell
+    count turns odd or reaches 2; coarse_dofs = 0 coarsens to two cells."""
+    cells = lambda specs: [sp_["cells"][0] for sp_ in specs]
+    assert solver.interior_dofs(I.config_2d_q2_64()) == 2 * 127 * 127
+    assert solver.interior_dofs(I.scaled(I.config_3d_q2_32(), (4, 4, 4))) == 2 * 7 ** 3
+    assert cells(solver.coarse_specs(I.config_2d_q2_64())) == [64, 32, 16, 8]          # 8^2: 450 unknowns
+    assert cells(solver.coarse_specs(I.config_2d_q2_64(), coarse_dofs=0)) == [64, 32, 16, 8, 4, 2]
+    assert cells(solver.coarse_specs(I.config_3d_q2_32())) == [32, 16, 8, 4]             # 4^3: 686
+    assert cells(solver.coarse_specs(I.config_3d_q2_32(), coarse_dofs=0)) == [32, 16, 8, 4, 2]
+    assert cells(solver.coarse_specs(I.config_small_2d_q1())) == [8]                    # 98: one level
+    assert cells(solver.coarse_specs(spec2((12, 12), k=2), coarse_dofs=0)) == [12, 6, 3]  # odd count ends it
+    assert cells(solver.coarse_specs(spec2((16, 16), k=2), coarse_dofs=1922)) == [16]   # at the limit: stop
+    assert cells(solver.coarse_specs(spec2((16, 16), k=2), coarse_dofs=1921)) == [16, 8]
+
+
 def test_multigrid_contracts():
     for s in (I.config_small_2d_q1(), spec2((16, 16), k=2), spec2((8, 8), k=2, hi=(1.0, 0.5))):
         p = operator.SGProblem(s)
-        mg = solver.Multigrid(p)
+        mg = solver.Multigrid(p, coarse_dofs=0)
         assert len(mg.levels) >= 3
         b = np.random.default_rng(1).uniform(-1, 1, p.shape)
         b[:, :, p.bmask] = 0.0

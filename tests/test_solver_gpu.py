@@ -58,11 +58,14 @@ def test_vcycle_matches_oracle(cuda, name, prec):
     spec = VCYCLE_CASES[name]
     p = operator.SGProblem(spec)
     # bf16: the oracle's V-cycle with its Vanka inverses rounded the same way
-    mg = solver.Multigrid(p, factor_round=solver.round_bf16 if prec == "bf16" else None)
+    # every level down to two cells (small meshes: the smoothers stay in play)
+    mg = solver.Multigrid(p, factor_round=solver.round_bf16 if prec == "bf16" else None, coarse_dofs=0)
     r = np.random.default_rng(4).uniform(-1, 1, p.shape)
     want = mg.apply(r).reshape(-1)
     ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, MG_PREC[prec][0])
+    assert sg.sg_mg_level_info(ctx, 0)["levels"] == len(mg.levels)
     rd = torch.from_numpy(r.reshape(-1).copy()).cuda()
     zd = torch.full_like(rd, float("nan"))
     sg.sg_vcycle(ctx, rd, zd)
@@ -83,10 +86,11 @@ def test_vcycle_one_smoothing_step_matches_oracle(cuda, name):
     torch = cuda
     spec = VCYCLE_CASES[name]
     p = operator.SGProblem(spec)
-    mg = solver.Multigrid(p, nu=1, omega=0.9)
+    mg = solver.Multigrid(p, nu=1, omega=0.9, coarse_dofs=0)
     r = np.random.default_rng(6).uniform(-1, 1, p.shape)
     want = mg.apply(r).reshape(-1)
     ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, sg.SG_PREC_FP64, 1, 0.9)
     rd = torch.from_numpy(r.reshape(-1).copy()).cuda()
     zd = torch.empty_like(rd)
@@ -95,6 +99,50 @@ def test_vcycle_one_smoothing_step_matches_oracle(cuda, name):
     got = zd.cpu().numpy()
     ctx.destroy()
     assert _rel(got, want) < 1e-10
+
+
+DEFAULT_HIERARCHY_CASES = {
+    "2d-q2-32x32": spec2((32, 32), k=2),                  # 32^2, 16^2, coarse solve on 8^2
+    "2d-q3-dg3-8x8": spec2((8, 8), k=3, r=3),             # 8^2, coarse solve on 4^2 (484 unknowns)
+    "3d-q2-8x8x8": spec3((8, 8, 8), k=2, M=1, P=1),       # 8^3, coarse solve on 4^3 (686)
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(DEFAULT_HIERARCHY_CASES))
+def test_vcycle_default_hierarchy_matches_oracle(cuda, name, prec):
+    """The default coarsest level (the first with at most 1024 interior
+    unknowns per mode, solved densely) on both sides."""
+    torch = cuda
+    spec = DEFAULT_HIERARCHY_CASES[name]
+    p = operator.SGProblem(spec)
+    mg = solver.Multigrid(p)
+    r = np.random.default_rng(9).uniform(-1, 1, p.shape)
+    want = mg.apply(r).reshape(-1)
+    ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_setup(ctx, MG_PREC[prec][0])
+    info = sg.sg_mg_level_info(ctx, 0)
+    assert info["levels"] == len(mg.levels) >= 2
+    last = sg.sg_mg_level_info(ctx, info["levels"] - 1)
+    assert last["coarsest"] == 1 and last["cells"] == mg.levels[-1].mesh.n_cells
+    rd = torch.from_numpy(r.reshape(-1).copy()).cuda()
+    zd = torch.empty_like(rd)
+    sg.sg_vcycle(ctx, rd, zd)
+    torch.cuda.synchronize()
+    got = zd.cpu().numpy()
+    ctx.destroy()
+    assert _rel(got, want) < MG_PREC[prec][1], _rel(got, want)
+
+
+def test_coarse_dofs_argument_errors(cuda):
+    ctx = sg.sg_setup_spec(I.config_small_2d_q1())
+    for bad in (-1, 2049):
+        with pytest.raises(sg.SGError):
+            sg.sg_mg_set_coarse_dofs(ctx, bad)
+    sg.sg_mg_set_coarse_dofs(ctx, 2048)
+    sg.sg_mg_setup(ctx, sg.SG_PREC_FP64)
+    assert sg.sg_mg_level_info(ctx, 0)["levels"] == 1          # 98 unknowns: one dense level
+    ctx.destroy()
 
 
 @pytest.mark.parametrize("prec", list(MG_PREC))
@@ -126,8 +174,9 @@ def test_iterations_match_oracle_fgmres(cuda):
     p = operator.SGProblem(spec)
     b = np.random.default_rng(6).uniform(-1, 1, p.shape)
     b[:, :, p.bmask] = 0.0
-    _, its, _ = solver.fgmres(p, b, solver.Multigrid(p).apply, rtol=1e-10)
+    _, its, _ = solver.fgmres(p, b, solver.Multigrid(p, coarse_dofs=0).apply, rtol=1e-10)
     ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
     sg.sg_mg_setup(ctx, sg.SG_PREC_FP64)
     x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
     st = sg.sg_solve_slab(ctx, 0, torch.from_numpy(b.reshape(-1).copy()).cuda(), x, rtol=1e-10)

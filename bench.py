@@ -317,9 +317,10 @@ def time_applies(sg, torch, ctx, X, Y, steps, warmup, stream, world, sample_cloc
     return elapsed_ms, t_launch, clocks
 
 
-def measure_solve(sg, torch, spec, dev, reps=3, autotune=True):
+def measure_solve(sg, torch, spec, dev, reps=3, autotune=True, profile=None):
     """Time to a 1e-8 relative residual for one slab system, FGMRES(30) from a
-    zero initial guess, for three precision splits."""
+    zero initial guess, for the precision splits.  profile names a split one
+    more solve of which is bracketed by cudaProfilerStart/Stop."""
     from paper_2605_21046_gb300 import inputs
     b = torch.from_numpy(inputs.random_rhs(spec)).to(dev)
     out, ref = {}, None
@@ -341,6 +342,13 @@ def measure_solve(sg, torch, spec, dev, reps=3, autotune=True):
             st = sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-8)
             torch.cuda.synchronize()
             times.append(1e3 * (time.perf_counter() - t0))
+        if profile == name:
+            x.zero_()
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-8)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         if ref is None:
             ref = x.clone()
         err = float((x - ref).abs().max() / ref.abs().max())
@@ -436,7 +444,8 @@ def run_ours(args, world, rank, local):
            "ms_per_step": e_hot / args.steps, "l2": "one x/y pair, L2-resident",
            "fp64_tflops": FLOP_PER_UNKNOWN * n / t_hot / 1e12}
 
-    solve = None if args.no_solve else measure_solve(sg, torch, spec, dev, autotune=not args.no_autotune)
+    solve = None if args.no_solve else measure_solve(sg, torch, spec, dev, autotune=not args.no_autotune,
+                                                     profile=args.profile_solve)
 
     # end to end through the host-buffer entry points, every step copying its
     # x in from pinned host memory and its y back: the pipelined call (two
@@ -944,6 +953,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the slab-solve timing")
     ap.add_argument("--profile-variant", choices=["fp64", "dw"], default="fp64",
                     help="which timed apply loop --profile-range brackets")
+    ap.add_argument("--profile-solve", choices=["fp64", "fp32_mg", "bf16_factors_mg", "fp32_mg_dw_apply"],
+                    default=None, help="bracket one more slab solve of this split with cudaProfilerStart/Stop")
     ap.add_argument("--profile-workload", choices=["3d", "2d"], default="3d",
                     help="workload of the V-cycle --profile-range brackets (--rows vcycle): 32^3 Q2 or 64x64 Q2")
     ap.add_argument("--profile-mg", choices=["fp32", "bf16", "bf16-tensor", "bf16-tensor-1buf"], default="fp32",

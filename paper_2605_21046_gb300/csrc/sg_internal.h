@@ -173,10 +173,15 @@ struct McProblem {
   int aniso;
   double ratio[3];
 };
+// Bytes of y rows one Monte-Carlo apply launch covers (whole sample tiles):
+// preset and then reduced into while they stay in L2.
+constexpr double kMcWaveBytes = 64.0 * 1024 * 1024;
+
 struct McParams {
   McProblem pr[kMcMaxProb];
   int n_prob, n_terms, chunk, mode, mass_only;
   long long units;
+  long long u_lo = 0, u_hi = -1;   // units of this launch (whole sample tiles); u_hi < 0: all of them
   double tb[kMaxNT];
 };
 // Shared memory of the Monte-Carlo apply for a chunk of cells and a sample tile.

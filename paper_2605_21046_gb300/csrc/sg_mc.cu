@@ -436,6 +436,7 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
     int grid = 1;
     auto build_base = [&]() {
       std::memset(&base, 0, sizeof(base));
+      base.u_hi = -1;
       units = 0;
       for (int p = 0; p < P; ++p) {
         McMesh& m = ms[p];
@@ -481,7 +482,21 @@ sg_status mc_solve_meshes(const std::vector<sg_ctx*>& parents, const std::vector
         q.pr[j].amq = transfer ? m.d_amqC : m.d_amqA;
         ++j;
       }
-      return launch_mc_apply(SG_PREC_FP64, h0.dim, h0.k, nt, q, grid, 256, smem, st);
+      // waves of whole sample tiles whose rows of y (preset, then reduced into
+      // by the apply) stay resident in L2 between the two
+      cudaError_t err = cudaSuccess;
+      for (int pi = 0; pi < base.n_prob && err == cudaSuccess; ++pi) {
+        const McProblem& P = base.pr[pi];
+        const double tile_bytes = (double)P.ts * nt * P.n_x * sizeof(double);
+        const int tpw = std::max(1, (int)(kMcWaveBytes / tile_bytes));
+        for (int t0 = 0; t0 < P.tiles && err == cudaSuccess; t0 += tpw) {
+          q.u_lo = P.unit0 + (long long)t0 * P.n_cells;
+          q.u_hi = P.unit0 + (long long)std::min(P.tiles, t0 + tpw) * P.n_cells;
+          const int g = (int)std::max<long long>(1, std::min<long long>((q.u_hi - q.u_lo) / chunk, grid));
+          err = launch_mc_apply(SG_PREC_FP64, h0.dim, h0.k, nt, q, g, 256, smem, st);
+        }
+      }
+      return err;
     };
     auto apply = [&](const double* in, double* out, cudaStream_t st) {
       return mc_launch(in, out, nullptr, kApplyPlain, false, st);

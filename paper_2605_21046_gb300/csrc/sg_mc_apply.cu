@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(256) mc_apply_kernel(const McParams p) {
   T* Tbs = Amq + NQD * NT * NT;                                 // [NT] tau Bhat_ii, converted once
   int* Nd = reinterpret_cast<int*>(Tbs + NT);                   // [C][NKD] node, -1 on the boundary
   if (tid < NT) Tbs[tid] = A::in(p.tb[tid]);
-  const long long u_begin = (long long)blockIdx.x * p.units / gridDim.x;
-  const long long u_end = (long long)(blockIdx.x + 1) * p.units / gridDim.x;
+  const long long u_lo = p.u_lo, u_n = (p.u_hi < 0 ? p.units : p.u_hi) - p.u_lo;
+  const long long u_begin = u_lo + (long long)blockIdx.x * u_n / gridDim.x;
+  const long long u_end = u_lo + (long long)(blockIdx.x + 1) * u_n / gridDim.x;
   int cur_prob = -1, cur_tile = -1;
   for (long long u = u_begin; u < u_end;) {
     int pi = 0;
@@ -255,17 +256,27 @@ cudaError_t launch_mc_apply(int precision, int dim, int k, int n_t, const McPara
   void* f = select_mc(precision, dim, k, n_t);
   if (!f) return cudaErrorInvalidValue;
   // y's start: b (accumulate), b - x on the boundary and b inside (residual),
-  // x on the boundary and 0 inside (overwrite)
+  // x on the boundary and 0 inside (plain), for the sample rows of the tiles
+  // this launch covers (its unit range holds whole tiles)
+  const long long u_lo = p.u_lo, u_hi = p.u_hi < 0 ? p.units : p.u_hi;
   for (int q = 0; q < p.n_prob; ++q) {
     const McProblem& P = p.pr[q];
-    const int V = P.S * n_t;
+    const long long a = std::max(u_lo, P.unit0), z = std::min(u_hi, P.unit0 + (long long)P.tiles * P.n_cells);
+    if (a >= z) continue;
+    const int t_lo = (int)((a - P.unit0) / P.n_cells), t_hi = (int)((z - P.unit0 + P.n_cells - 1) / P.n_cells);
+    const int s_lo = t_lo * P.ts, s_hi = std::min(P.S, t_hi * P.ts);
+    const int V = (s_hi - s_lo) * n_t;
+    const long long off = (long long)s_lo * n_t * P.n_x;
     const int op = p.mode == kApplyResidual ? 1 : (p.mode == kApplyAccumulate ? 3 : 2);
-    if (precision == kPrecF32)
-      launch_vec_start<float>(static_cast<const float*>(P.b), static_cast<const float*>(P.x), static_cast<float*>(P.y),
-                              nullptr, op, V, P.n_x, P.nn, dim, s);
-    else
-      launch_vec_start<double>(static_cast<const double*>(P.b), static_cast<const double*>(P.x),
-                               static_cast<double*>(P.y), nullptr, op, V, P.n_x, P.nn, dim, s);
+    if (precision == kPrecF32) {
+      const float* b = static_cast<const float*>(P.b);
+      launch_vec_start<float>(b ? b + off : nullptr, static_cast<const float*>(P.x) + off,
+                              static_cast<float*>(P.y) + off, nullptr, op, V, P.n_x, P.nn, dim, s);
+    } else {
+      const double* b = static_cast<const double*>(P.b);
+      launch_vec_start<double>(b ? b + off : nullptr, static_cast<const double*>(P.x) + off,
+                               static_cast<double*>(P.y) + off, nullptr, op, V, P.n_x, P.nn, dim, s);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -863,6 +863,7 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
     // apply with per-row weights G_mu[alpha][alpha] (Psi_mu(xi_s) for samples)
     McParams q;
     std::memset(&q, 0, sizeof(q));
+    q.u_hi = -1;                       // every unit in one launch
     q.n_prob = 1;
     McProblem& P = q.pr[0];
     P.x = L.d_x;

@@ -52,6 +52,7 @@
 
 #include "sg_internal.h"
 #include "sg_shape_tables.h"
+#include "sg_vec.cuh"
 
 namespace sg {
 
@@ -59,28 +60,6 @@ void* select_kernel_f64(int dim, int k, int n_t);
 void* select_kernel_dw(int dim, int k, int n_t);
 void* select_kernel_f32(int dim, int k, int n_t);
 
-// Starting value of y before the cell kernel adds: (x on Dirichlet nodes, 0
-// elsewhere) for a plain apply, b minus that for a residual, b for an
-// accumulation (y == b allowed there).
-template <typename IO>
-__global__ void sg_init_y_kernel(const IO* __restrict__ x, IO* y, const IO* b, int mode, int n_x, int nnx,
-                                 int nny, int nnz, int dim) {
-  // blockIdx.y picks the vector; 32-bit node arithmetic within it
-  const long long off = (long long)blockIdx.y * n_x;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_x; m += gridDim.x * blockDim.x) {
-    const long long idx = off + m;
-    if (mode == kApplyAccumulate) {
-      y[idx] = b[idx];
-      continue;
-    }
-    const int ix = m % nnx, r = m / nnx;
-    const int iy = r % nny, iz = r / nny;
-    bool bd = ix == 0 || ix == nnx - 1 || iy == 0 || iy == nny - 1;
-    if (dim == 3) bd = bd || iz == 0 || iz == nnz - 1;
-    const IO v = bd ? x[idx] : IO(0);
-    y[idx] = mode == kApplyResidual ? b[idx] - v : v;
-  }
-}
 
 size_t apply_smem_bytes(int dim, int k, int n_t, int n_xi, int coef_rows, int nnz, int chunk,
                         int value_bytes, bool premul) {
@@ -304,17 +283,17 @@ void fill_apply_params(const HostProblem& hp, const LaunchShape& ls, const void*
 
 cudaError_t launch_apply(const HostProblem& hp, const LaunchShape& ls, const ApplyParams& prm,
                          cudaStream_t stream) {
+  // the start of y before the cell kernel adds into it: x on Dirichlet nodes
+  // and 0 elsewhere (plain), b minus that (residual), b (accumulation; y may
+  // be b) -- one vectorised pass
   const int V = hp.n_xi * hp.n_t;
-  const int ib = 256;
-  const dim3 ig((unsigned)std::max<long long>(1, std::min<long long>((hp.n_x + ib - 1) / ib, 64)), (unsigned)V);
+  const int op = prm.mode == kApplyResidual ? 1 : (prm.mode == kApplyAccumulate ? 3 : 2);
   if (hp.precision == kPrecF32)
-    sg_init_y_kernel<float><<<ig, ib, 0, stream>>>(static_cast<const float*>(prm.x), static_cast<float*>(prm.y),
-                                                   static_cast<const float*>(prm.b), prm.mode, (int)hp.n_x, hp.nn[0],
-                                                   hp.nn[1], hp.nn[2], hp.dim);
+    launch_vec_start<float>(static_cast<const float*>(prm.b), static_cast<const float*>(prm.x),
+                            static_cast<float*>(prm.y), nullptr, op, V, hp.n_x, hp.nn, hp.dim, stream);
   else
-    sg_init_y_kernel<double><<<ig, ib, 0, stream>>>(static_cast<const double*>(prm.x), static_cast<double*>(prm.y),
-                                                    static_cast<const double*>(prm.b), prm.mode, (int)hp.n_x, hp.nn[0],
-                                                    hp.nn[1], hp.nn[2], hp.dim);
+    launch_vec_start<double>(static_cast<const double*>(prm.b), static_cast<const double*>(prm.x),
+                             static_cast<double*>(prm.y), nullptr, op, V, hp.n_x, hp.nn, hp.dim, stream);
   void* f = select_kernel(hp.precision, hp.dim, hp.k, hp.n_t);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<ApplyParams*>(&prm)};

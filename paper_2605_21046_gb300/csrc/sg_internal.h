@@ -228,19 +228,16 @@ struct MGLevel {
   void* d_b = nullptr;
   void* d_r = nullptr;
   // transfer to and from the next coarser level, per direction d: the
-  // interpolation lists per fine node i (pptr[i]..pptr[i+1] entries (coarse
-  // index, weight)) and the restriction lists per coarse node j (rptr[j]..
-  // rptr[j+1] entries (fine index, weight)), weights in the MG precision;
+  // interpolation lists (fine node <- coarse nodes) and the restriction lists
+  // (coarse node <- fine nodes), padded to pmax / rmax entries per output
+  // (weight 0) and stored entry-major, [entry][output]; weights in the MG
+  // precision;
   // d_t1 / d_t2 hold the intermediate arrays of the separable passes
-  int* d_pptr[3] = {nullptr, nullptr, nullptr};
   int* d_pidx[3] = {nullptr, nullptr, nullptr};
   void* d_pwl[3] = {nullptr, nullptr, nullptr};
-  int* d_rptr[3] = {nullptr, nullptr, nullptr};
   int* d_ridx[3] = {nullptr, nullptr, nullptr};
   void* d_rw[3] = {nullptr, nullptr, nullptr};
-  int pnnz[3] = {0, 0, 0};    // entries of the interpolation / restriction lists
-  int rnnz[3] = {0, 0, 0};
-  int pmax[3] = {0, 0, 0};    // the longest list of each
+  int pmax[3] = {0, 0, 0};    // entries per output of the padded lists
   int rmax[3] = {0, 0, 0};
   void* d_t1 = nullptr;
   void* d_t2 = nullptr;

@@ -459,39 +459,22 @@ __global__ void __launch_bounds__(256, 2) mg_vanka(const VankaParams<T> p) {
 
 // One pass of a separable grid transfer: along one axis of a structured
 // array [VA][nin][B] -> [VA][nout][B],
-//     out[va][jo][b] (+)= sum_t w[t] in[va][idx[t]][b],  t in ptr[jo] .. ptr[jo+1],
+//     out[va][jo][b] (+)= sum_k w[k][jo] in[va][idx[k][jo]][b],  k < W,
 // with the 1D restriction lists (coarse node <- fine nodes) or the 1D
-// interpolation lists (fine node <- coarse nodes).  Restriction P^T and
+// interpolation lists (fine node <- coarse nodes) padded to W entries per
+// output (weight 0, index of the output's first entry) and stored entry-major,
+// so the lanes of a warp (consecutive outputs in the x pass, one output in the
+// others) read them coalesced or broadcast from L1.  Restriction P^T and
 // prolongation P are d such passes (x, y, z resp. z, y, x), which read every
-// value a few times instead of (k+1)^d-fold per output.  The lists are staged
-// in shared memory (TAB_SMEM) or read where they are; each thread walks the
+// value a few times instead of (k+1)^d-fold per output.  Each thread walks the
 // flat output index with a fixed stride, carrying (va, jo, b) along instead
 // of dividing for every element.
 constexpr int kAxisMax = 16;  // entries of one output of a 1D transfer list, at most (4k + 1 for k <= 3)
 
-template <typename T, bool TAB_SMEM, int MAXE>
+template <typename T, int W>
 __global__ void __launch_bounds__(256) mg_axis_gather(const T* __restrict__ in, T* __restrict__ out, long long VA,
-                                                      int nin, int nout, int B, const int* __restrict__ ptr,
-                                                      const int* __restrict__ idx, const T* __restrict__ w, int nnz,
-                                                      int accumulate) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const T* tw = w;
-  const int* tidx = idx;
-  const int* tptr = ptr;
-  if constexpr (TAB_SMEM) {
-    T* sw = reinterpret_cast<T*>(sm_raw);
-    int* sidx = reinterpret_cast<int*>(sw + nnz);
-    int* sptr = sidx + nnz;
-    for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
-      sw[i] = w[i];
-      sidx[i] = idx[i];
-    }
-    for (int i = threadIdx.x; i <= nout; i += blockDim.x) sptr[i] = ptr[i];
-    __syncthreads();
-    tw = sw;
-    tidx = sidx;
-    tptr = sptr;
-  }
+                                                      int nin, int nout, int B, const int* __restrict__ idx,
+                                                      const T* __restrict__ w, int accumulate) {
   const long long total = VA * nout * B;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -508,15 +491,10 @@ __global__ void __launch_bounds__(256) mg_axis_gather(const T* __restrict__ in, 
   for (; e < total; e += stride) {
     const T* src = in + va * row_in + b;
     T acc = T(0);
-    const int t0 = tptr[jo], cnt = tptr[jo + 1] - t0;
-    // at most MAXE entries: unrolled, so the loads of one output are in
-    // flight together
 #pragma unroll
-    for (int k = 0; k < MAXE; ++k) {
-      if (k < cnt) {
-        const int si = tidx[t0 + k];
-        if (SG_IN(si, nin, 501)) acc += tw[t0 + k] * src[(long long)si * B];
-      }
+    for (int k = 0; k < W; ++k) {
+      const int si = __ldg(idx + k * nout + jo);
+      if (SG_IN(si, nin, 501)) acc += __ldg(w + k * nout + jo) * src[(long long)si * B];
     }
     if (accumulate) out[e] += acc;
     else out[e] = acc;
@@ -1051,27 +1029,49 @@ bool vk_launch(MG& mg, MGLevel& L, cudaStream_t s) {
   return mg.precision == kPrecF32 ? vanka<float>(mg, L, s, 0) : vanka<double>(mg, L, s, 0);
 }
 
-template <typename T, int MAXE>
-void axis_pass_m(const void* in, void* out, long long VA, int nin, int nout, int B, const int* ptr, const int* idx,
-                 const void* w, int nnz, int accumulate, cudaStream_t s) {
+template <typename T, int W>
+void axis_pass_w(const void* in, void* out, long long VA, int nin, int nout, int B, const int* idx, const void* w,
+                 int accumulate, cudaStream_t s) {
   const long long total = VA * nout * B;
   const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, sg::sm_count() * 8));
-  const size_t tab = (size_t)nnz * (sizeof(T) + sizeof(int)) + (size_t)(nout + 1) * sizeof(int);
-  if (tab <= 32 * 1024)
-    mg_axis_gather<T, true, MAXE><<<grid, 256, tab, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin,
-                                                         nout, B, ptr, idx, static_cast<const T*>(w), nnz, accumulate);
-  else
-    mg_axis_gather<T, false, MAXE><<<grid, 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin,
-                                                        nout, B, ptr, idx, static_cast<const T*>(w), nnz, accumulate);
+  mg_axis_gather<T, W><<<grid, 256, 0, s>>>(static_cast<const T*>(in), static_cast<T*>(out), VA, nin, nout, B, idx,
+                                            static_cast<const T*>(w), accumulate);
 }
 
-// one pass; maxe = the longest list of the pass (at most kAxisMax)
+// one pass with lists padded to width (one of axis_width's values)
 template <typename T>
-void axis_pass(const void* in, void* out, long long VA, int nin, int nout, int B, const int* ptr, const int* idx,
-               const void* w, int nnz, int maxe, int accumulate, cudaStream_t s) {
-  if (maxe <= 4) axis_pass_m<T, 4>(in, out, VA, nin, nout, B, ptr, idx, w, nnz, accumulate, s);
-  else if (maxe <= 8) axis_pass_m<T, 8>(in, out, VA, nin, nout, B, ptr, idx, w, nnz, accumulate, s);
-  else axis_pass_m<T, kAxisMax>(in, out, VA, nin, nout, B, ptr, idx, w, nnz, accumulate, s);
+void axis_pass(const void* in, void* out, long long VA, int nin, int nout, int B, const int* idx, const void* w,
+               int width, int accumulate, cudaStream_t s) {
+  switch (width) {
+    case 2: axis_pass_w<T, 2>(in, out, VA, nin, nout, B, idx, w, accumulate, s); break;
+    case 3: axis_pass_w<T, 3>(in, out, VA, nin, nout, B, idx, w, accumulate, s); break;
+    case 4: axis_pass_w<T, 4>(in, out, VA, nin, nout, B, idx, w, accumulate, s); break;
+    case 5: axis_pass_w<T, 5>(in, out, VA, nin, nout, B, idx, w, accumulate, s); break;
+    case 8: axis_pass_w<T, 8>(in, out, VA, nin, nout, B, idx, w, accumulate, s); break;
+    default: axis_pass_w<T, kAxisMax>(in, out, VA, nin, nout, B, idx, w, accumulate, s); break;
+  }
+}
+
+// the padded width of lists whose longest has n entries
+int axis_width(int n) {
+  for (int w : {2, 3, 4, 5, 8})
+    if (n <= w) return w;
+  return kAxisMax;
+}
+
+// CSR lists (ptr, idx, wt) -> width entries per output, entry-major
+void pad_lists(const std::vector<int>& ptr, const std::vector<int>& idx, const std::vector<double>& wt, int width,
+               std::vector<int>& pidx, std::vector<double>& pw) {
+  const int n = (int)ptr.size() - 1;
+  pidx.assign((size_t)width * n, 0);
+  pw.assign((size_t)width * n, 0.0);
+  for (int o = 0; o < n; ++o) {
+    const int c = ptr[o + 1] - ptr[o];
+    for (int k = 0; k < width; ++k) {
+      pidx[(size_t)k * n + o] = k < c ? idx[ptr[o] + k] : (c > 0 ? idx[ptr[o]] : 0);
+      pw[(size_t)k * n + o] = k < c ? wt[ptr[o] + k] : 0.0;
+    }
+  }
 }
 
 // x_fine += P e_coarse: interpolation along z (3D), y, then x
@@ -1080,7 +1080,7 @@ bool prolong(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
   const int nfx = F.hp.nn[0], nfy = F.hp.nn[1], nfz = F.hp.nn[2];
   const int ncx = C.hp.nn[0], ncy = C.hp.nn[1], ncz = C.hp.nn[2];
   auto pass = [&](const void* in, void* out, long long VA, int nin, int nout, int B, int d, int acc) {
-    axis_pass<T>(in, out, VA, nin, nout, B, F.d_pptr[d], F.d_pidx[d], F.d_pwl[d], F.pnnz[d], F.pmax[d], acc, s);
+    axis_pass<T>(in, out, VA, nin, nout, B, F.d_pidx[d], F.d_pwl[d], F.pmax[d], acc, s);
   };
   if (F.hp.dim == 3) {
     pass(C.d_x, F.d_t2, V, ncz, nfz, ncy * ncx, 2, 0);
@@ -1099,7 +1099,7 @@ void restrict_to(MGLevel& F, MGLevel& C, int V, cudaStream_t s) {
   const int nfx = F.hp.nn[0], nfy = F.hp.nn[1], nfz = F.hp.nn[2];
   const int ncx = C.hp.nn[0], ncy = C.hp.nn[1], ncz = C.hp.nn[2];
   auto pass = [&](const void* in, void* out, long long VA, int nin, int nout, int B, int d) {
-    axis_pass<T>(in, out, VA, nin, nout, B, F.d_rptr[d], F.d_ridx[d], F.d_rw[d], F.rnnz[d], F.rmax[d], 0, s);
+    axis_pass<T>(in, out, VA, nin, nout, B, F.d_ridx[d], F.d_rw[d], F.rmax[d], 0, s);
   };
   if (F.hp.dim == 3) {
     pass(F.d_r, F.d_t1, (long long)V * nfz * nfy, nfx, ncx, 1, 0);
@@ -1365,8 +1365,8 @@ void mg_free(MG& mg) {
     cudaFree(L.d_perm); cudaFree(L.d_inv); cudaFree(L.d_inner); cudaFree(L.d_amq); cudaFree(L.d_amqT);
     cudaFree(L.d_x); cudaFree(L.d_b); cudaFree(L.d_r); cudaFree(L.d_t1); cudaFree(L.d_t2);
     for (int d = 0; d < 3; ++d) {
-      cudaFree(L.d_pptr[d]); cudaFree(L.d_pidx[d]); cudaFree(L.d_pwl[d]);
-      cudaFree(L.d_rptr[d]); cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
+      cudaFree(L.d_pidx[d]); cudaFree(L.d_pwl[d]);
+      cudaFree(L.d_ridx[d]); cudaFree(L.d_rw[d]);
     }
   }
   mg.lv.clear();
@@ -1567,21 +1567,23 @@ sg_status mg_build(const HostProblem& fine, int precision, int nu, double omega,
         std::vector<int> pptr, pidx, rptr, ridx;
         std::vector<double> pwl, rw;
         transfer_1d(F.hp, L.hp, d, pptr, pidx, pwl, rptr, ridx, rw);
-        F.pnnz[d] = (int)pidx.size();
-        F.rnnz[d] = (int)ridx.size();
-        F.pmax[d] = F.rmax[d] = 0;
-        for (size_t i = 0; i + 1 < pptr.size(); ++i) F.pmax[d] = std::max(F.pmax[d], pptr[i + 1] - pptr[i]);
-        for (size_t j = 0; j + 1 < rptr.size(); ++j) F.rmax[d] = std::max(F.rmax[d], rptr[j + 1] - rptr[j]);
-        if (F.pmax[d] > kAxisMax || F.rmax[d] > kAxisMax) {
+        int pm = 0, rm = 0;
+        for (size_t i = 0; i + 1 < pptr.size(); ++i) pm = std::max(pm, pptr[i + 1] - pptr[i]);
+        for (size_t j = 0; j + 1 < rptr.size(); ++j) rm = std::max(rm, rptr[j + 1] - rptr[j]);
+        if (pm > kAxisMax || rm > kAxisMax) {
           e = cudaErrorInvalidValue;
           break;
         }
-        if ((e = upload_vec(&F.d_pptr[d], pptr)) != cudaSuccess) break;
-        if ((e = upload_vec(&F.d_pidx[d], pidx)) != cudaSuccess) break;
-        if ((e = upload_values(&F.d_pwl[d], pwl, precision)) != cudaSuccess) break;
-        if ((e = upload_vec(&F.d_rptr[d], rptr)) != cudaSuccess) break;
-        if ((e = upload_vec(&F.d_ridx[d], ridx)) != cudaSuccess) break;
-        if ((e = upload_values(&F.d_rw[d], rw, precision)) != cudaSuccess) break;
+        F.pmax[d] = axis_width(pm);
+        F.rmax[d] = axis_width(rm);
+        std::vector<int> pi, ri;
+        std::vector<double> pwv, rwv;
+        pad_lists(pptr, pidx, pwl, F.pmax[d], pi, pwv);
+        pad_lists(rptr, ridx, rw, F.rmax[d], ri, rwv);
+        if ((e = upload_vec(&F.d_pidx[d], pi)) != cudaSuccess) break;
+        if ((e = upload_values(&F.d_pwl[d], pwv, precision)) != cudaSuccess) break;
+        if ((e = upload_vec(&F.d_ridx[d], ri)) != cudaSuccess) break;
+        if ((e = upload_values(&F.d_rw[d], rwv, precision)) != cudaSuccess) break;
       }
       if (e != cudaSuccess) break;
       // intermediate arrays of the separable transfers between F and this level

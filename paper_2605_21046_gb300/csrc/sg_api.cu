@@ -514,8 +514,10 @@ sg_status sg_autotune(sg_ctx* ctx, int reps) {
   sg::LaunchShape best = ctx->ls;
   float best_ms = 1e30f;
   const int max1 = sg::max_apply_chunk(ctx->hp, (size_t)optin - 1024);
+  // every chunk size: the cells a CTA takes (cells / CTAs) split into whole
+  // chunks for some sizes only, and a ragged last chunk costs a chunk's time
   std::vector<int> chunks;
-  for (int c = max1; c >= 1; c = c > 1 ? (c + 1) / 2 - (c == 2) : 0) chunks.push_back(c);
+  for (int c = std::min(max1, 16); c >= 1; --c) chunks.push_back(c);
   const int thread_opts[] = {128, 256, 384, 512};
   for (int c : chunks) {
     if (e != cudaSuccess) break;

@@ -182,6 +182,7 @@ struct McParams {
   int n_prob, n_terms, chunk, mode, mass_only;
   long long units;
   long long u_lo = 0, u_hi = -1;   // units of this launch (whole sample tiles); u_hi < 0: all of them
+  int bd_zero = 0;                  // residual whose x equals b on the boundary: its Dirichlet rows are 0
   double tb[kMaxNT];
 };
 // Shared memory of the Monte-Carlo apply for a chunk of cells and a sample tile.

@@ -267,7 +267,7 @@ cudaError_t launch_mc_apply(int precision, int dim, int k, int n_t, const McPara
     const int s_lo = t_lo * P.ts, s_hi = std::min(P.S, t_hi * P.ts);
     const int V = (s_hi - s_lo) * n_t;
     const long long off = (long long)s_lo * n_t * P.n_x;
-    const int op = p.mode == kApplyResidual ? 1 : (p.mode == kApplyAccumulate ? 3 : 2);
+    const int op = p.mode == kApplyResidual ? (p.bd_zero ? 4 : 1) : (p.mode == kApplyAccumulate ? 3 : 2);
     if (precision == kPrecF32) {
       const float* b = static_cast<const float*>(P.b);
       launch_vec_start<float>(b ? b + off : nullptr, static_cast<const float*>(P.x) + off,

@@ -842,6 +842,7 @@ cudaError_t residual(MG& mg, int l, cudaStream_t s, int trans) {
     McParams q;
     std::memset(&q, 0, sizeof(q));
     q.u_hi = -1;                       // every unit in one launch
+    q.bd_zero = 1;                     // x = b on the boundary (start, Vanka and transfers keep it)
     q.n_prob = 1;
     McProblem& P = q.pr[0];
     P.x = L.d_x;

@@ -20,6 +20,9 @@ namespace {
 //   op 1 (residual start):   y = bd ? b - x : b
 //   op 2 (plain apply):      y = bd ? x : 0
 //   op 3 (accumulation):     y = b  (y may be b)
+//   op 4 (residual start where x = b on the boundary, as on every multigrid
+//         level: the Dirichlet rows of the residual are exactly 0):
+//                            y = bd ? 0 : b   (x is not read)
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(256) vec_start(const T* b, const T* __restrict__ x, T* y, T* __restrict__ yz, int op,
                                                  long long n, int nnx, int nny, int nnz) {
@@ -67,6 +70,8 @@ __global__ void __launch_bounds__(256) vec_start(const T* b, const T* __restrict
         out[k] = bd && i + k < n ? bv[k] - x[i + k] : bv[k];
       } else if (op == 2) {
         out[k] = bd && i + k < n ? x[i + k] : T(0);
+      } else if (op == 4) {
+        out[k] = bd ? T(0) : bv[k];
       } else {
         out[k] = bv[k];
       }

@@ -224,6 +224,7 @@ struct MGLevel {
   int vanka_tile = 0;        // modes per Vanka tile on this level (0: the multigrid's tile)
   int vanka_kind = 0;        // Vanka sweep: 0 FFMA kernel, 1 tensor-core kernel (bf16 factors)
   int ffma_chunk = 0, ffma_tile = 0;   // the FFMA sweep's timed choice (kept while the other sweep runs)
+  const void* vanka_r = nullptr;       // residual the next sweep reads when not d_r (the first sweep reads b)
   int* d_inner = nullptr;    // coarsest: dof offset (i * n_x + node) of every interior dof
   void* d_x = nullptr;       // level vectors (N_xi * N_t * n_x values of the MG precision)
   void* d_b = nullptr;

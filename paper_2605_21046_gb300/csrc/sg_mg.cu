@@ -923,7 +923,7 @@ int vanka_chunk(const MGLevel& L, int n_blk, int tile_slots, size_t value_bytes,
 template <typename T, typename W, int DIM, int K, int NT>
 cudaError_t launch_vanka_w(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   VankaParams<T> p;
-  p.r = static_cast<const T*>(L.d_r);
+  p.r = static_cast<const T*>(L.vanka_r ? L.vanka_r : L.d_r);
   p.x = static_cast<T*>(L.d_x);
   p.inv = L.d_inv;
   p.blk_cls = mg.d_blk_cls;
@@ -999,8 +999,9 @@ cudaError_t launch_vanka(MG& mg, MGLevel& L, cudaStream_t s, int trans) {
   if constexpr (std::is_same<T, float>::value) {
     if (mg.bf16 && L.vanka_kind == 1 && !trans) {
       const int tile = L.vanka_tile > 0 ? L.vanka_tile : mg.vanka_tile;
-      return launch_vanka_tc(L.hp, static_cast<const float*>(L.d_r), static_cast<float*>(L.d_x), L.d_inv,
-                             mg.d_blk_alpha, mg.n_blk, L.vanka_chunk, tile, mg.d_status, (float)mg.omega, s);
+      const float* r = static_cast<const float*>(L.vanka_r ? L.vanka_r : L.d_r);
+      return launch_vanka_tc(L.hp, r, static_cast<float*>(L.d_x), L.d_inv, mg.d_blk_alpha, mg.n_blk, L.vanka_chunk,
+                             tile, mg.d_status, (float)mg.omega, s);
     }
     if (mg.bf16) return launch_vanka_w<T, __nv_bfloat16, DIM, K, NT>(mg, L, s, trans);
   }
@@ -1128,12 +1129,16 @@ cudaError_t issue_vcycle(MG& mg, int l, cudaStream_t s, int trans) {
     return cudaGetLastError();
   }
   cudaError_t e;
-  // the start: x = the boundary values of b, r = b on the interior (0 on the boundary)
-  launch_vec_start<T>(static_cast<const T*>(L.d_b), nullptr, static_cast<T*>(L.d_x), static_cast<T*>(L.d_r), 0, V,
-                      L.hp.n_x, L.hp.nn, L.hp.dim, s);
+  // the start: x = the boundary values of b and 0 inside; the first sweep's
+  // residual b - A x is b on the interior, where the sweep reads it
+  launch_vec_start<T>(nullptr, static_cast<const T*>(L.d_b), static_cast<T*>(L.d_x), nullptr, 2, V, L.hp.n_x,
+                      L.hp.nn, L.hp.dim, s);
   for (int it = 0; it < mg.nu; ++it) {
     if (it > 0 && (e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
-    if (!vanka<T>(mg, L, s, trans)) return cudaErrorInvalidValue;
+    L.vanka_r = it == 0 ? L.d_b : nullptr;
+    const bool ok = vanka<T>(mg, L, s, trans);
+    L.vanka_r = nullptr;
+    if (!ok) return cudaErrorInvalidValue;
   }
   if ((e = residual<T>(mg, l, s, trans)) != cudaSuccess) return e;
   MGLevel& C = mg.lv[l + 1];

@@ -2,19 +2,24 @@
 // A^(n) U = rhs (paper, Sec. 3.5: the slab systems are solved by flexible
 // GMRES with the block-Jacobi multigrid preconditioner).
 //
-// Arnoldi uses classical Gram-Schmidt with one reorthogonalisation (CGS2):
-// each pass is one multi-dot kernel (every basis vector against w, per-segment
-// partial sums reduced in a fixed order, so results are deterministic) and one
-// multi-axpy kernel.  The true residual b - A x is recomputed at every restart
-// and at the end; its norm is what is reported and tested against rtol.
+// Arnoldi uses classical Gram-Schmidt with one reorthogonalisation (CGS2) in
+// three streaming kernels per step: the dots V^T w; the update w -= V h fused
+// with the second pass's dots V^T w (each basis value read once while the
+// cycle has at most 12 vectors); the update w -= V h2 fused with ||w||.  Each
+// kernel writes one partial sum per block and its last-arriving block reduces
+// them in a fixed order (results are deterministic, and no block waits for
+// another); the norm kernel's last block also updates the Hessenberg column,
+// the Givens rotations and the residual estimate.  A fourth kernel scales w
+// into the next basis vector.  The true residual b - A x is recomputed at
+// every restart and at the end; its norm is what is reported and tested
+// against rtol.
 //
 // The whole solver state lives on the device and one solve is recorded as a
-// CUDA graph: a conditional WHILE node runs one Arnoldi step per pass (its
-// last kernel updates the Hessenberg column, the Givens rotations and the
-// residual estimate on one thread), and a conditional IF node inside it,
-// taken at the end of a restart cycle, applies the update x += Z y and
-// recomputes the true residual.  A solve is then one graph launch and one
-// read of the final state, with no host round trip per iteration.
+// CUDA graph: a conditional WHILE node runs one Arnoldi step per pass, and a
+// conditional IF node inside it, taken at the end of a restart cycle, applies
+// the update x += Z y, recomputes the true residual and starts the next
+// cycle.  A solve is then one graph launch and one read of the final state,
+// with no host round trip per iteration.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -30,62 +35,26 @@ namespace sg {
 
 namespace {
 
-constexpr int kSeg = 256;      // segments of the multi-dot reduction
-constexpr int kDotThreads = 256;
-
-__global__ void k_multidot(const double* __restrict__ w, const double* __restrict__ V, int nvec, long long N,
-                           double* __restrict__ part) {
-  // blockIdx.y = vector, blockIdx.x = segment
-  __shared__ double red[kDotThreads];
-  const int k = blockIdx.y;
-  const double* v = V + (long long)k * N;
-  double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    s = fma(v[i], w[i], s);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[(long long)k * gridDim.x + blockIdx.x] = red[0];
-}
-
-__global__ void k_reduce_parts(const double* __restrict__ part, int nseg, int nvec, double* __restrict__ out) {
-  const int k = blockIdx.x;
-  __shared__ double red[kDotThreads];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nseg; i += blockDim.x) s += part[(long long)k * nseg + i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[k] = red[0];
-}
-
-
-
-
-__global__ void k_sub_from(const double* __restrict__ b, double* __restrict__ r, long long N) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    r[i] = b[i] - r[i];
-}
-
-int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, sg::sm_count() * 16)); }
+constexpr int kRedThreads = 256;  // threads of the reduction kernels (8 warps)
+constexpr int kKG = 16;           // basis sizes with an element loop of their own; dots a thread accumulates per pass
+constexpr int kMaxVec = 256;      // bound on the basis size m + 1 (restart <= 200)
 
 // Device-resident state of the graph driver (followed in memory by
-// H[(m+1) x m], cs[m], sn[m], g[m+1], y[m]).
+// H[(m+1) x m], cs[m], sn[m], g[m+1], y[m]).  red_count is the arrival
+// counter of the last-block reductions; it is 0 between kernels.
 struct KState {
   double bnorm, beta, rtol, pad0;
   int max_it, m, j, its, restarts, vmult, prec, cycle_end, done, status, nvec, zero_rhs;
+  unsigned red_count, pad1;
 };
 constexpr int kStateDoubles = (int)((sizeof(KState) + 15) / 16 * 2);
 
 struct Ws {
   double *V, *Z, *w, *r, *part, *h, *h2, *nrm, *y, *vj, *zb, *bb, *xx, *st;
 };
+
+// Partial sums: at most kMaxVec rows of kMaxGrid blocks.
+constexpr int kMaxGrid = 2048;
 
 Ws carve(double* base, long long N, int m) {
   Ws ws;
@@ -98,7 +67,7 @@ Ws carve(double* base, long long N, int m) {
   ws.bb = ws.zb + N;
   ws.xx = ws.bb + N;
   ws.part = ws.xx + N;
-  ws.h = ws.part + (long long)(m + 2) * kSeg;
+  ws.h = ws.part + (long long)(m + 2) * kMaxGrid;
   ws.h2 = ws.h + (m + 2);
   ws.nrm = ws.h2 + (m + 2);
   ws.y = ws.nrm + 4;
@@ -106,18 +75,90 @@ Ws carve(double* base, long long N, int m) {
   return ws;
 }
 
-}  // namespace
+__device__ __forceinline__ double* st_H(KState* S) { return reinterpret_cast<double*>(S) + kStateDoubles; }
 
-size_t krylov_bytes(long long N, int m) {
-  const size_t arrays = (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m;
-  return sizeof(double) * ((size_t)(2 * m + 7) * N + (size_t)(m + 2) * kSeg + 3 * (m + 2) + 4 + kStateDoubles +
-                           arrays + 8);
+// Block sums of acc[0..nk) (fixed order: warp shuffles, then the warps in
+// order) into dst[c * dst_stride].
+template <int NA>
+__device__ __forceinline__ void block_sum(const double (&acc)[NA], int nk, double* dst, long long dst_stride) {
+  __shared__ double sred[kKG][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NA; ++c) {
+    if (c < nk) {
+      double v = acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sred[c][wid] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nk) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedThreads / 32; ++w) v += sred[threadIdx.x][w];
+    dst[threadIdx.x * dst_stride] = v;
+  }
+  __syncthreads();
 }
 
-// ------------------------------------------------------------ graph driver
-namespace {
+// This block's sums of acc[0..nk) into part[(k0 + c) * gridDim.x + blockIdx.x].
+template <int NA>
+__device__ __forceinline__ void block_partials(const double (&acc)[NA], int k0, int nk, double* part) {
+  block_sum(acc, nk, part + (long long)k0 * gridDim.x + blockIdx.x, (long long)gridDim.x);
+}
 
-__device__ __forceinline__ double* st_H(KState* S) { return reinterpret_cast<double*>(S) + kStateDoubles; }
+// True in the block that arrives last, once every block has written its
+// partial sums (threadfence reduction: no block waits for another).
+__device__ __forceinline__ bool arrive_last(unsigned* count) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// In the last block: out[k] = sum over blocks of part[k][.] for k < nk (each
+// thread sums a fixed set of blocks for kKG vectors at a time, then the block
+// sum; fixed order), then the counter back to 0.
+__device__ __forceinline__ void reduce_partials(const double* part, int nk, double* out, unsigned* count) {
+  const int G = (int)gridDim.x;
+  for (int k0 = 0; k0 < nk; k0 += kKG) {
+    const int n = min(kKG, nk - k0);
+    double v[kKG] = {};
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < kKG; ++c)
+        if (c < n) v[c] += __ldcg(part + (long long)(k0 + c) * G + b);
+    }
+    block_sum(v, n, out + k0, 1);
+  }
+  if (threadIdx.x == 0) *count = 0u;
+}
+
+// out[idx] = ||v|| (sub = 0) or, with sub = 1, r = b - r and out[idx] = ||r||.
+__global__ void __launch_bounds__(kRedThreads) k_norm(const double* __restrict__ b, double* __restrict__ r, long long N,
+                                                      int sub, double* __restrict__ part, double* __restrict__ out,
+                                                      int idx, unsigned* count) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double v;
+    if (sub) {
+      v = b[i] - r[i];
+      r[i] = v;
+    } else {
+      v = b[i];
+    }
+    acc[0] = fma(v, v, acc[0]);
+  }
+  block_partials(acc, 0, 1, part);
+  if (!arrive_last(count)) return;
+  __shared__ double tot;
+  reduce_partials(part, 1, &tot, count);
+  if (threadIdx.x == 0) out[idx] = sqrt(tot);
+}
 
 // Start of a solve: ||b|| in nrm[0], ||b - A x|| in nrm[1].
 __global__ void k_gm_start(KState* S, const double* nrm, cudaGraphConditionalHandle wh) {
@@ -135,12 +176,17 @@ __global__ void k_gm_start(KState* S, const double* nrm, cudaGraphConditionalHan
   cudaGraphSetConditional(wh, done ? 0u : 1u);
 }
 
-// Start of a restart cycle (j == 0): V_0 = r / beta, g = beta e_0.
-__global__ void k_gm_vstart(KState* S, const double* __restrict__ r, double* __restrict__ V, long long N) {
-  if (S->j != 0) return;
+// Start of a restart cycle: V_0 = vj = r / beta, g = beta e_0 (nothing once
+// the solve is done).
+__global__ void k_gm_vstart(KState* S, const double* __restrict__ r, double* __restrict__ V, double* __restrict__ vj,
+                            long long N) {
+  if (S->done) return;
   const double inv = 1.0 / S->beta;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    V[i] = r[i] * inv;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double v = r[i] * inv;
+    V[i] = v;
+    vj[i] = v;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int m = S->m;
     double* g = st_H(S) + (m + 1) * m + 2 * m;
@@ -149,80 +195,161 @@ __global__ void k_gm_vstart(KState* S, const double* __restrict__ r, double* __r
   }
 }
 
-// dst = src + (j + off) * N (from = 1) or dst + (j + off) * N = src (from = 0).
-__global__ void k_gm_copy(const KState* S, const double* __restrict__ src, double* __restrict__ dst, long long N,
-                          int from) {
-  const long long o = (long long)S->j * N;
-  const double* a = from ? src + o : src;
-  double* b = from ? dst : dst + o;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    b[i] = a[i];
-}
-
-// multi-dot / reduce / multi-axpy over the basis vectors V_0..V_j
-__global__ void k_multidot_st(const KState* S, const double* __restrict__ w, const double* __restrict__ V, long long N,
-                              double* __restrict__ part) {
-  __shared__ double red[kDotThreads];
-  const int k = blockIdx.y;
-  if (k > S->j) return;
-  const double* v = V + (long long)k * N;
-  double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    s = fma(v[i], w[i], s);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[(long long)k * gridDim.x + blockIdx.x] = red[0];
-}
-
-__global__ void k_reduce_parts_st(const KState* S, const double* __restrict__ part, int nseg, double* __restrict__ out) {
-  const int k = blockIdx.x;
-  if (k > S->j) return;
-  __shared__ double red[kDotThreads];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nseg; i += blockDim.x) s += part[(long long)k * nseg + i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[k] = red[0];
-}
-
-__global__ void k_multiaxpy_st(const KState* S, double* __restrict__ w, const double* __restrict__ V,
-                               const double* __restrict__ h, long long N) {
-  const int nvec = S->j + 1;
+// Element loops of the Gram-Schmidt kernels for a basis of NV vectors known
+// at compile time: every basis value of an element is loaded before the
+// arithmetic that uses it (issue is in order: a load followed by its use
+// would hold the next load back).
+template <int NV>
+__device__ __forceinline__ void loop_dot(const double* __restrict__ w, const double* __restrict__ V,
+                                         const double* __restrict__ zb, double* __restrict__ Zj, long long N,
+                                         double (&acc)[kKG]) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double v[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = V[(long long)c * N + i];
+    const double wi = w[i];
+    Zj[i] = zb[i];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] = fma(v[c], wi, acc[c]);
+  }
+}
+template <int NV>
+__device__ __forceinline__ void loop_axpy_dot(double* __restrict__ w, const double* __restrict__ V,
+                                              const double* sh, long long N, double (&acc)[kKG]) {
+  double hc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) hc[c] = sh[c];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double v[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = V[(long long)c * N + i];
     double s = w[i];
-    for (int k = 0; k < nvec; ++k) s = fma(-h[k], V[(long long)k * N + i], s);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) s = fma(-hc[c], v[c], s);
     w[i] = s;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] = fma(v[c], s, acc[c]);
+  }
+}
+template <int NV>
+__device__ __forceinline__ void loop_axpy_norm(double* __restrict__ w, const double* __restrict__ V, const double* sh,
+                                               long long N, double& acc) {
+  double hc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) hc[c] = sh[c];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double v[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = V[(long long)c * N + i];
+    double s = w[i];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) s = fma(-hc[c], v[c], s);
+    w[i] = s;
+    acc = fma(s, s, acc);
+  }
+}
+// Runs CALL(NV) for NV = nvec when nvec <= kKG; false otherwise.
+#define SG_NV_DISPATCH(nvec, CALL)                                                                        \
+  [&]() -> bool {                                                                                         \
+    switch (nvec) {                                                                                       \
+      case 1: CALL(1); return true;   case 2: CALL(2); return true;   case 3: CALL(3); return true;       \
+      case 4: CALL(4); return true;   case 5: CALL(5); return true;   case 6: CALL(6); return true;       \
+      case 7: CALL(7); return true;   case 8: CALL(8); return true;   case 9: CALL(9); return true;       \
+      case 10: CALL(10); return true; case 11: CALL(11); return true; case 12: CALL(12); return true;     \
+      case 13: CALL(13); return true; case 14: CALL(14); return true; case 15: CALL(15); return true;     \
+      case 16: CALL(16); return true;                                                                     \
+      default: return false;                                                                              \
+    }                                                                                                     \
+  }()
+
+// Dots of w with basis vectors g0 .. g0 + nk - 1 (nk <= kKG); the loads of
+// the slots past nk repeat the last vector's address, their products are dropped.
+__device__ __forceinline__ void dots_group(const double* __restrict__ w, const double* __restrict__ V, int g0, int nk,
+                                           long long N, double (&acc)[kKG]) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double v[kKG];
+#pragma unroll
+    for (int c = 0; c < kKG; ++c) v[c] = V[(long long)(g0 + min(c, nk - 1)) * N + i];
+    const double wi = w[i];
+#pragma unroll
+    for (int c = 0; c < kKG; ++c)
+      if (c < nk) acc[c] = fma(v[c], wi, acc[c]);
   }
 }
 
-// V_{j+1} = w / ||w||
-__global__ void k_gm_vnext(const KState* S, const double* __restrict__ w, double* __restrict__ V,
-                           const double* __restrict__ nrm, long long N) {
-  const double inv = 1.0 / nrm[0];
-  double* v = V + (long long)(S->j + 1) * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    v[i] = w[i] * inv;
+// First Gram-Schmidt pass, dots: h[k] = V_k . w for k <= j; also stores the
+// preconditioned vector of this step, Z_j = zb.
+__global__ void __launch_bounds__(kRedThreads, 2) k_cgs_dot(KState* S, const double* __restrict__ w,
+                                                         const double* __restrict__ V, const double* __restrict__ zb,
+                                                         double* __restrict__ Z, long long N, double* __restrict__ part,
+                                                         double* __restrict__ h) {
+  const int nvec = S->j + 1;
+  double* Zj = Z + (long long)S->j * N;
+  double acc[kKG] = {};
+#define SG_CALL(NV) loop_dot<NV>(w, V, zb, Zj, N, acc)
+  if (SG_NV_DISPATCH(nvec, SG_CALL)) {
+    block_partials(acc, 0, nvec, part);
+  } else {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+      Zj[i] = zb[i];
+    for (int g0 = 0; g0 < nvec; g0 += kKG) {
+      const int nk = min(kKG, nvec - g0);
+      double ag[kKG] = {};
+      dots_group(w, V, g0, nk, N, ag);
+      block_partials(ag, g0, nk, part);
+    }
+  }
+#undef SG_CALL
+  if (!arrive_last(&S->red_count)) return;
+  reduce_partials(part, nvec, h, &S->red_count);
+}
+
+// Second pass: w -= sum_k h[k] V_k, then h2[k] = V_k . w.  With at most kKG
+// vectors each V value is read once and used for both; beyond that the dots
+// read V again.
+__global__ void __launch_bounds__(kRedThreads, 2) k_cgs_axpy_dot(KState* S, double* __restrict__ w,
+                                                              const double* __restrict__ V,
+                                                              const double* __restrict__ h, long long N,
+                                                              double* __restrict__ part, double* __restrict__ h2) {
+  const int nvec = S->j + 1;
+  __shared__ double sh[kMaxVec];
+  for (int k = threadIdx.x; k < nvec; k += blockDim.x) sh[k] = h[k];
+  __syncthreads();
+  double acc[kKG] = {};
+#define SG_CALL(NV) loop_axpy_dot<NV>(w, V, sh, N, acc)
+  if (SG_NV_DISPATCH(nvec, SG_CALL)) {
+    block_partials(acc, 0, nvec, part);
+  } else {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+      double s = w[i];
+#pragma unroll 4
+      for (int k = 0; k < nvec; ++k) s = fma(-sh[k], V[(long long)k * N + i], s);
+      w[i] = s;
+    }
+    for (int g0 = 0; g0 < nvec; g0 += kKG) {
+      const int nk = min(kKG, nvec - g0);
+      double ag[kKG] = {};
+      dots_group(w, V, g0, nk, N, ag);
+      block_partials(ag, g0, nk, part);
+    }
+  }
+#undef SG_CALL
+  if (!arrive_last(&S->red_count)) return;
+  reduce_partials(part, nvec, h2, &S->red_count);
 }
 
 // The Hessenberg column of step j, the previous rotations and a new one, the
-// residual estimate |g_{j+1}|; at the end of a cycle y = H^{-1} g.
-__global__ void k_gm_arnoldi(KState* S, const double* __restrict__ h, const double* __restrict__ h2,
-                             const double* __restrict__ nrm, double* __restrict__ y, cudaGraphConditionalHandle ih) {
+// residual estimate |g_{j+1}|; at the end of a cycle y = H^{-1} g.  One thread.
+__device__ void arnoldi_update(KState* S, const double* __restrict__ h, const double* __restrict__ h2, double hn,
+                               double* __restrict__ y, cudaGraphConditionalHandle ih) {
   const int m = S->m, j = S->j;
   double* H = st_H(S);
   double* cs = H + (m + 1) * m;
   double* sn = cs + m;
   double* g = sn + m;
   for (int i = 0; i <= j; ++i) H[i * m + j] = h[i] + h2[i];
-  const double hn = nrm[0];
   H[(j + 1) * m + j] = hn;
   for (int i = 0; i < j; ++i) {
     const double a = H[i * m + j], c = H[(i + 1) * m + j];
@@ -256,6 +383,54 @@ __global__ void k_gm_arnoldi(KState* S, const double* __restrict__ h, const doub
   cudaGraphSetConditional(ih, end ? 1u : 0u);
 }
 
+// Closing pass of the step: w -= sum_k h2[k] V_k, nrm[0] = ||w||, and in the
+// last block the Arnoldi update of step j.
+__global__ void __launch_bounds__(kRedThreads, 3) k_cgs_axpy_norm(KState* S, double* __restrict__ w,
+                                                               const double* __restrict__ V,
+                                                               const double* __restrict__ h,
+                                                               const double* __restrict__ h2, long long N,
+                                                               double* __restrict__ part, double* __restrict__ nrm,
+                                                               double* __restrict__ y, cudaGraphConditionalHandle ih) {
+  const int nvec = S->j + 1;
+  __shared__ double sh[kMaxVec];
+  for (int k = threadIdx.x; k < nvec; k += blockDim.x) sh[k] = h2[k];
+  __syncthreads();
+  double acc[1] = {0.0};
+#define SG_CALL(NV) loop_axpy_norm<NV>(w, V, sh, N, acc[0])
+  if (!SG_NV_DISPATCH(nvec, SG_CALL)) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+      double s = w[i];
+#pragma unroll 4
+      for (int k = 0; k < nvec; ++k) s = fma(-sh[k], V[(long long)k * N + i], s);
+      w[i] = s;
+      acc[0] = fma(s, s, acc[0]);
+    }
+  }
+#undef SG_CALL
+  block_partials(acc, 0, 1, part);
+  if (!arrive_last(&S->red_count)) return;
+  __shared__ double tot;
+  reduce_partials(part, 1, &tot, &S->red_count);
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(tot);
+    nrm[0] = hn;
+    arnoldi_update(S, h, h2, hn, y, ih);
+  }
+}
+
+// V_{j+1} = vj = w / ||w|| (S->j has already advanced to j + 1).
+__global__ void k_gm_vnext(const KState* S, const double* __restrict__ w, double* __restrict__ V,
+                           double* __restrict__ vj, const double* __restrict__ nrm, long long N) {
+  const double inv = 1.0 / nrm[0];
+  double* v = V + (long long)S->j * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double t = w[i] * inv;
+    v[i] = t;
+    vj[i] = t;
+  }
+}
+
 // x += sum_k y[k] Z_k over the cycle's vectors
 __global__ void k_lincomb_st(const KState* S, double* __restrict__ x, const double* __restrict__ Z,
                              const double* __restrict__ y, long long N) {
@@ -282,15 +457,17 @@ __global__ void k_gm_finish(KState* S, const double* nrm, cudaGraphConditionalHa
   cudaGraphSetConditional(wh, done ? 0u : 1u);
 }
 
-__global__ void k_sqrt_at(double* v, int i) { v[i] = sqrt(v[i]); }
+int grid_n(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, sg::sm_count() * 16)); }
 
-// ||v|| into out[i] (two-stage deterministic reduction, then sqrt)
-cudaError_t norm2_at(const double* v, long long N, double* part, double* out, int i, cudaStream_t s) {
-  dim3 grid(kSeg, 1);
-  k_multidot<<<grid, kDotThreads, 0, s>>>(v, v, 1, N, part);
-  k_reduce_parts<<<1, kDotThreads, 0, s>>>(part, kSeg, 1, out + i);
-  k_sqrt_at<<<1, 1, 0, s>>>(out, i);
-  return cudaGetLastError();
+// Grid of a reduction kernel: every block resident at once (the partial sums
+// have one column per block), at most kMaxGrid blocks.
+template <typename K>
+int grid_red(K kern, long long n) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRedThreads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long g = std::min<long long>((long long)per_sm * sg::sm_count(), kMaxGrid);
+  return (int)std::max<long long>(1, std::min<long long>((n + kRedThreads - 1) / kRedThreads, g));
 }
 
 // Appends a conditional node after the current capture dependencies of `cs`,
@@ -320,6 +497,12 @@ cudaError_t add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaG
 }
 
 }  // namespace
+
+size_t krylov_bytes(long long N, int m) {
+  const size_t arrays = (size_t)(m + 1) * m + 2 * (size_t)m + (m + 1) + m;
+  return sizeof(double) * ((size_t)(2 * m + 7) * N + (size_t)(m + 2) * kMaxGrid + 3 * (m + 2) + 4 + kStateDoubles +
+                           arrays + 8);
+}
 
 void krylov_graph_free(KrylovGraph& G) {
   if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -361,51 +544,38 @@ sg_status fgmres_graph(long long N, const double* b, double* x, double rtol, int
     cudaGraphConditionalHandle wh, ih;
     CKG(cudaGraphConditionalHandleCreate(&wh, G.graph, 0, 0));
     const int gn = grid_n(N);
-    // the start: ||b||, r = b - A x, ||r||
+    const int g_norm = grid_red(k_norm, N), g_dot = grid_red(k_cgs_dot, N);
+    const int g_ad = grid_red(k_cgs_axpy_dot, N), g_an = grid_red(k_cgs_axpy_norm, N);
+    unsigned* count = &S->red_count;
+    // the start: ||b||, r = b - A x, ||r||, and V_0 = r / ||r||
     CKG(cudaStreamBeginCaptureToGraph(G.cs, G.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ee = norm2_at(b, N, ws.part, ws.nrm, 0, G.cs);
+    k_norm<<<g_norm, kRedThreads, 0, G.cs>>>(b, nullptr, N, 0, ws.part, ws.nrm, 0, count);
+    cudaError_t ee = cudaGetLastError();
     if (ee == cudaSuccess) ee = apply(x, ws.r, G.cs);
     if (ee == cudaSuccess) {
-      k_sub_from<<<gn, 256, 0, G.cs>>>(b, ws.r, N);
-      ee = norm2_at(ws.r, N, ws.part, ws.nrm, 1, G.cs);
-    }
-    if (ee == cudaSuccess) {
+      k_norm<<<g_norm, kRedThreads, 0, G.cs>>>(b, ws.r, N, 1, ws.part, ws.nrm, 1, count);
       k_gm_start<<<1, 1, 0, G.cs>>>(S, ws.nrm, wh);
+      k_gm_vstart<<<gn, 256, 0, G.cs>>>(S, ws.r, ws.V, ws.vj, N);
       ee = cudaGetLastError();
     }
     cudaGraph_t wbody = nullptr;
     if (ee == cudaSuccess) ee = add_conditional(G.cs, wh, cudaGraphCondTypeWhile, &wbody);
-    // the WHILE body: one Arnoldi step
+    // the WHILE body: one Arnoldi step (z_j = M^-1 v_j, w = A z_j, CGS2, v_{j+1})
     if (ee == cudaSuccess) ee = cudaGraphConditionalHandleCreate(&ih, wbody, 0, 0);
     if (ee == cudaSuccess)
       ee = cudaStreamBeginCaptureToGraph(G.bs, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     bool body_open = ee == cudaSuccess;
-    if (ee == cudaSuccess) {
-      k_gm_vstart<<<gn, 256, 0, G.bs>>>(S, ws.r, ws.V, N);
-      k_gm_copy<<<gn, 256, 0, G.bs>>>(S, ws.V, ws.vj, N, 1);
-      ee = cudaGetLastError();
-    }
     if (ee == cudaSuccess) ee = prec(ws.vj, ws.zb, G.bs);
-    if (ee == cudaSuccess) {
-      k_gm_copy<<<gn, 256, 0, G.bs>>>(S, ws.zb, ws.Z, N, 0);
-      ee = cudaGetLastError();
-    }
     if (ee == cudaSuccess) ee = apply(ws.zb, ws.w, G.bs);
     if (ee == cudaSuccess) {
-      dim3 grid(kSeg, m + 1);
-      for (double* hh : {ws.h, ws.h2}) {
-        k_multidot_st<<<grid, kDotThreads, 0, G.bs>>>(S, ws.w, ws.V, N, ws.part);
-        k_reduce_parts_st<<<m + 1, kDotThreads, 0, G.bs>>>(S, ws.part, kSeg, hh);
-        k_multiaxpy_st<<<gn, 256, 0, G.bs>>>(S, ws.w, ws.V, hh, N);
-      }
-      ee = norm2_at(ws.w, N, ws.part, ws.nrm, 0, G.bs);
-    }
-    if (ee == cudaSuccess) {
-      k_gm_vnext<<<gn, 256, 0, G.bs>>>(S, ws.w, ws.V, ws.nrm, N);
-      k_gm_arnoldi<<<1, 1, 0, G.bs>>>(S, ws.h, ws.h2, ws.nrm, ws.y, ih);
+      k_cgs_dot<<<g_dot, kRedThreads, 0, G.bs>>>(S, ws.w, ws.V, ws.zb, ws.Z, N, ws.part, ws.h);
+      k_cgs_axpy_dot<<<g_ad, kRedThreads, 0, G.bs>>>(S, ws.w, ws.V, ws.h, N, ws.part, ws.h2);
+      k_cgs_axpy_norm<<<g_an, kRedThreads, 0, G.bs>>>(S, ws.w, ws.V, ws.h, ws.h2, N, ws.part, ws.nrm, ws.y, ih);
+      k_gm_vnext<<<gn, 256, 0, G.bs>>>(S, ws.w, ws.V, ws.vj, ws.nrm, N);
       ee = cudaGetLastError();
     }
-    // the IF body: the update and the true residual at the end of a cycle
+    // the IF body: the update, the true residual at the end of a cycle and
+    // the next cycle's V_0
     cudaGraph_t ibody = nullptr;
     if (ee == cudaSuccess) ee = add_conditional(G.bs, ih, cudaGraphCondTypeIf, &ibody);
     if (ee == cudaSuccess)
@@ -417,11 +587,9 @@ sg_status fgmres_graph(long long N, const double* b, double* x, double rtol, int
     }
     if (ee == cudaSuccess) ee = apply(x, ws.r, G.is);
     if (ee == cudaSuccess) {
-      k_sub_from<<<gn, 256, 0, G.is>>>(b, ws.r, N);
-      ee = norm2_at(ws.r, N, ws.part, ws.nrm, 1, G.is);
-    }
-    if (ee == cudaSuccess) {
+      k_norm<<<g_norm, kRedThreads, 0, G.is>>>(b, ws.r, N, 1, ws.part, ws.nrm, 1, count);
       k_gm_finish<<<1, 1, 0, G.is>>>(S, ws.nrm, wh);
+      k_gm_vstart<<<gn, 256, 0, G.is>>>(S, ws.r, ws.V, ws.vj, N);
       ee = cudaGetLastError();
     }
     cudaGraph_t tmp = nullptr;

@@ -184,6 +184,35 @@ def test_iterations_match_oracle_fgmres(cuda):
     assert abs(st["iterations"] - its) <= 1, (st["iterations"], its)
 
 
+@pytest.mark.parametrize("omega,restart", [(0.1, 20), (0.05, 30)])
+def test_long_arnoldi_cycles_match_oracle_fgmres(cuda, omega, restart):
+    """A weakly damped smoother makes the Arnoldi cycles long (up to 29 basis
+    vectors, and a restart with restart = 20): the Gram-Schmidt passes then
+    run past the vectors a thread keeps in registers.  Iteration count and
+    solution against the oracle's FGMRES with the same V-cycle."""
+    torch = cuda
+    spec = I.config_small_2d_q1()
+    p = operator.SGProblem(spec)
+    b = np.random.default_rng(6).uniform(-1, 1, p.shape)
+    b[:, :, p.bmask] = 0.0
+    want, its, _ = solver.fgmres(p, b, solver.Multigrid(p, nu=1, omega=omega, coarse_dofs=0).apply, rtol=1e-10,
+                                 restart=restart)
+    assert its > 20
+    ctx = sg.sg_setup_spec(spec)
+    sg.sg_mg_set_coarse_dofs(ctx, 0)
+    sg.sg_mg_setup(ctx, sg.SG_PREC_FP64, 1, omega)
+    x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+    st = sg.sg_solve_slab(ctx, 0, torch.from_numpy(b.reshape(-1).copy()).cuda(), x, rtol=1e-10, max_it=300,
+                          restart=restart)
+    got = x.cpu().numpy()
+    ctx.destroy()
+    res = np.linalg.norm(b.reshape(-1) - p.apply(got).reshape(-1)) / np.linalg.norm(b)
+    assert st["converged"] == 1 and res <= 1.5e-10, (res, st)
+    assert abs(st["iterations"] - its) <= 1, (st["iterations"], its)
+    assert st["restarts"] == (2 if st["iterations"] > restart else 1), st
+    assert _rel(got, want) < 1e-8
+
+
 @pytest.mark.parametrize("prec", list(MG_PREC))
 def test_solve_at_scale_reaches_tolerance(cuda, prec):
     """64x64 Q2, M=4, P=3 (1.16 M unknowns) to 1e-8; residual checked by the oracle."""

@@ -151,7 +151,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 struct TcUnit {
-  int cx0, cy, cz, nc, b0, nb;
+  int cx0, cy, cz, nc, b0, nb, tile;
   long long cell0;
 };
 
@@ -219,18 +219,44 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
     }
   }
 
+  // unit -> (mode tile, pair): unit = tile * n_pairs + (cz cells[1] + cy) ppr + cx0 / 2
+  auto finish_unit = [&](TcUnit& U) {
+    U.b0 = U.tile * p.tile_blocks;
+    U.nb = min(p.tile_blocks, p.n_blk - U.b0);
+    U.nc = min(2, p.cells[0] - U.cx0);
+    U.cell0 = ((long long)U.cz * p.cells[1] + U.cy) * p.cells[0] + U.cx0;
+  };
   auto decode = [&](unsigned int unit, TcUnit& U) {
     const unsigned int pr = unit % n_pairs;
-    const int tile = (int)(unit / n_pairs);
-    U.b0 = tile * p.tile_blocks;
-    U.nb = min(p.tile_blocks, p.n_blk - U.b0);
+    U.tile = (int)(unit / n_pairs);
     U.cx0 = (int)(pr % ppr) * 2;
     const unsigned int row = pr / ppr;
     U.cy = (int)(row % (unsigned int)p.cells[1]);
     U.cz = (int)(row / (unsigned int)p.cells[1]);
-    U.nc = min(2, p.cells[0] - U.cx0);
-    U.cell0 = ((long long)U.cz * p.cells[1] + U.cy) * p.cells[0] + U.cx0;
+    finish_unit(U);
   };
+  // the unit gridDim.x further on, by a mixed-radix addition of the grid's
+  // stride (each digit carries at most once)
+  const unsigned int g_pairs = gridDim.x % n_pairs, g_rows = g_pairs / ppr;
+  const int st_tile = (int)(gridDim.x / n_pairs), st_px = (int)(g_pairs % ppr);
+  const int st_cy = (int)(g_rows % (unsigned int)p.cells[1]), st_cz = (int)(g_rows / (unsigned int)p.cells[1]);
+  auto advance = [&](const TcUnit& A, TcUnit& U) {
+    int px = (A.cx0 >> 1) + st_px;
+    const int c0 = px >= (int)ppr;
+    px -= c0 * (int)ppr;
+    int cy = A.cy + st_cy + c0;
+    const int c1 = cy >= p.cells[1];
+    cy -= c1 * p.cells[1];
+    int cz = A.cz + st_cz + c1;
+    const int c2 = cz >= p.cells[2];
+    cz -= c2 * p.cells[2];
+    U.tile = A.tile + st_tile + c2;
+    U.cx0 = px * 2;
+    U.cy = cy;
+    U.cz = cz;
+    finish_unit(U);
+  };
+  int so_tile0 = -1, so_tile1 = -1;               // mode tile whose slot offsets each buffer holds
   auto tables = [&](const TcUnit& U, int tb) {
     const int lxn = U.nc * K + 1;
     for (int ln = tid; ln < LN; ln += kTcThreads) {
@@ -246,9 +272,15 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
 #pragma unroll
       for (int i = 0; i < NT; ++i) s_ge[tb][i * LN + ln] = node >= 0 ? (int)(i * p.n_x + node) : -1;
     }
-    for (int sl = tid; sl < SL; sl += kTcThreads) {
-      const int mode = sl < U.nb * kTcVB ? p.blk_alpha[U.b0 * kTcVB + sl] : -1;
-      s_so[tb][sl] = mode >= 0 ? (long long)mode * NT * p.n_x : -1;
+    // slot offsets depend on the mode tile only: rebuilt when the buffer
+    // holds another tile's (the same for all threads)
+    if ((tb ? so_tile1 : so_tile0) != U.b0) {
+      for (int sl = tid; sl < SL; sl += kTcThreads) {
+        const int mode = sl < U.nb * kTcVB ? p.blk_alpha[U.b0 * kTcVB + sl] : -1;
+        s_so[tb][sl] = mode >= 0 ? (long long)mode * NT * p.n_x : -1;
+      }
+      if (tb) so_tile1 = U.b0;
+      else so_tile0 = U.b0;
     }
   };
   // the unit's r values: slot-major, entries (time node, pair node)
@@ -293,9 +325,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
     }
   };
   // B: eight K values (patch columns 8 kc ..) of slot s of cell c, kTcTerms terms
+  // a thread's items (slot s, K chunk ck of either cell) step by kTcThreads:
+  // (s, ck) advances by (kTcThreads % SL, kTcThreads / SL) with one carry
+  const int bb_ds = kTcThreads % SL, bb_dck = kTcThreads / SL;
+  const int bb_s0 = tid % SL, bb_ck0 = tid / SL;
   auto build_b = [&](const float* Rl) {
-    for (int idx = tid; idx < 2 * KC * SL; idx += kTcThreads) {
-      const int s = idx % SL, ck = idx / SL;
+    for (int s = bb_s0, ck = bb_ck0; ck < 2 * KC;) {
       const int c = ck / KC, kc = ck - c * KC;
       const float* src = Rl + s * EP + c * K;
       float v[8];
@@ -319,6 +354,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
         const int n = t * SLP + s;
         *reinterpret_cast<uint4*>(dst + (n >> 3) * 128 + (n & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
       }
+      s += bb_ds;
+      ck += bb_dck;
+      if (s >= SL) {
+        s -= SL;
+        ++ck;
+      }
     }
   };
   // wait (bounded) for the MMAs committed to the barrier
@@ -331,17 +372,27 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
     phase ^= 1u;
   };
   // D into x: lane row = 64 c + patch row
+  // this thread's accumulator row (lane row = 64 c + patch row): its entry
+  // in the unit tables and its multiplicity weight, the same in every unit
+  const int rb_c = (warp * 32 + lane) >> 6;
+  int rb_entry = -1;
+  float rb_sc = 0.0f;
+  {
+    const int rho = (warp * 32 + lane) & 63;
+    if (rho < NP) {
+      const int i = rho / NKD, a = rho - i * NKD;
+      const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
+      rb_entry = i * LN + rb_c * K + ax + LX * (ay + N * az);
+      const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
+      rb_sc = p.omega / (float)mult;
+    }
+  }
   auto read_back = [&](const TcUnit& U, int tb, uint32_t tmem) {
     const int failed = __shfl_sync(0xffffffffu, s_fail, 0);   // warp-uniform: tcgen05.ld is .sync.aligned
     if (failed) return;
-    const int row = warp * 32 + lane, c = row >> 6, rho = row & 63;
-    const int i = rho / NKD, a = rho - i * NKD;
-    const int ax = a % N, ay = (a / N) % N, az = DIM == 3 ? a / (N * N) : 0;
-    const int lna = c * K + ax + LX * (ay + N * az);
-    const int ge = rho < NP ? s_ge[tb][i * LN + lna] : -1;
-    const bool live = rho < NP && c < U.nc && ge >= 0;
-    const int mult = (ax % K == 0 ? 2 : 1) * (ay % K == 0 ? 2 : 1) * (DIM == 3 && az % K == 0 ? 2 : 1);
-    const float sc = p.omega / (float)mult;
+    const int ge = rb_entry >= 0 ? s_ge[tb][rb_entry] : -1;
+    const bool live = rb_c < U.nc && ge >= 0;
+    const float sc = rb_sc;
     const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
     for (int s0 = 0; s0 < SL; s0 += 16) {
       float d0[16], d1[16];
@@ -381,7 +432,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) mg_vanka_tc(const TcParams p) {
     const unsigned int un = u + gridDim.x;
     const bool has_next = un < n_units;
     if (has_next) {
-      decode(un, nxt);
+      advance(cur, nxt);
       tables(nxt, tb ^ 1);
     }
     cp_wait0_tc();

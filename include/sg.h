@@ -376,8 +376,7 @@ sg_status sg_adjoint_gradient(sg_ctx* ctx, double rtol, int max_it, int checkpoi
  * routine).  Its first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, and looks it up again when
  * the device's CUDA context has been replaced since (after cudaDeviceReset,
- * for instance): make that first call before any stream capture.  The
- * context's device must be current.  Every call uses the same array, which
+ * for instance).  The context's device must be current.  Every call uses the same array, which
  * keeps the last call's contents (each call overwrites what it reads); calls
  * that overlap on the GPU, from several threads or contexts, race on it.
  * Synchronous: it copies with cudaMemcpy and launches on the legacy default

@@ -277,7 +277,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": spec["name"], "unknowns": n, "mesh": "64x64 Q2",
+            "data": "synthetic", "config": {"workload": spec["name"], "unknowns": n, "mesh": "64x64 Q2 unit square",
                                             "time": "dG(1)", "M": 4, "P": 3, "chaos_modes": 35},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

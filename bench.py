@@ -903,6 +903,70 @@ def next_vcycle(sg, torch, inputs, profile_range=False, profile_mg="fp32", profi
     return {"row": "V-cycle", "unit": "ms per V-cycle", "workloads": out}
 
 
+def next_krylov(sg, torch, inputs):
+    """Cost of one FGMRES iteration outside the preconditioner and the operator:
+    slab solves cut off after 1, 3, 5, 7 and 9 iterations (restart 30, a
+    tolerance they cannot reach), device time per solve (median of CUDA-event
+    times, host set-up of the call included), a straight-line fit over the
+    iteration count; the slope minus one V-cycle and one FP64 apply, each timed
+    alone, is the Arnoldi step's own part (Gram-Schmidt passes, next basis
+    vector, Hessenberg update).  64x64 Q2 P=3 with the FP32 V-cycle and 32^3 Q2
+    P=3 with bf16 factors, as in the solve and mixed-precision rows."""
+    import numpy as np
+    out = {}
+    for wname, maker, prec, reps in (("2d-q2-64x64-M4P3", inputs.config_2d_q2_64, sg.SG_PREC_FP32, 10),
+                                     ("3d-q2-32x32x32-M3P3", inputs.config_3d_q2_32, sg.SG_PREC_BF16, 3)):
+        ctx = sg.sg_setup_spec(maker())
+        sg.sg_mg_setup(ctx, prec, MG_NU, MG_OMEGA)
+        n = ctx.info["n_unknowns"]
+        gen = torch.Generator(device="cpu").manual_seed(3)
+        b = torch.rand(n, dtype=torch.float64, generator=gen).cuda()
+        x = torch.zeros_like(b)
+        for _ in range(2):
+            x.zero_()
+            sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-14, max_it=9, restart=30, check=False)
+        torch.cuda.synchronize()
+        pts = []
+        for mi in (1, 3, 5, 7, 9):
+            ts = []
+            for _ in range(reps):
+                x.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = sg.sg_solve_slab(ctx, 0, b, x, rtol=1e-14, max_it=mi, restart=30, check=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            pts.append((st["iterations"], statistics.median(ts)))
+        its = np.array([q[0] for q in pts], dtype=np.float64)
+        slope, icpt = np.polyfit(its, np.array([q[1] for q in pts]), 1)
+        z = torch.empty_like(b)
+        y = torch.empty_like(b)
+        for _ in range(3):
+            sg.sg_vcycle(ctx, b, z)
+            ctx.apply(b, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            sg.sg_vcycle(ctx, b, z)
+        e1.record()
+        torch.cuda.synchronize()
+        vc = e0.elapsed_time(e1) / 10
+        e0.record()
+        for _ in range(10):
+            ctx.apply(b, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ap = e0.elapsed_time(e1) / 10
+        out[wname] = {"unknowns": n, "mg": "fp32" if prec == sg.SG_PREC_FP32 else "bf16 factors",
+                      "iterations_ms": [[int(i), round(t, 4)] for i, t in pts],
+                      "slope_ms_per_iteration": float(slope), "intercept_ms": float(icpt),
+                      "vcycle_ms": vc, "apply_ms": ap, "arnoldi_step_ms": float(slope) - vc - ap}
+        ctx.destroy()
+    return {"row": "FGMRES iteration", "unit": "ms", "workloads": out}
+
+
 def run_next(args, world, rank, local):
     import torch
     import paper_2605_21046_gb300 as sg
@@ -928,6 +992,8 @@ def run_next(args, world, rank, local):
                 out = next_applies(sg, torch, inputs)
             elif row == "paper":
                 out = next_paper(sg, torch, inputs)
+            elif row == "krylov":
+                out = next_krylov(sg, torch, inputs)
             else:
                 raise ValueError(row)
         except sg.SGError as ex:
@@ -967,7 +1033,7 @@ def main():
     ap.add_argument("--suite", choices=["apply", "next"], default="apply",
                     help="apply: the headline line; next: one line per solver-side row")
     ap.add_argument("--rows", default="mixed,mc,adjoint", help="rows of --suite next "
-                    "(mixed, mc, adjoint, vcycle, applies, paper)")
+                    "(mixed, mc, adjoint, vcycle, applies, paper, krylov)")
     ap.add_argument("--mc-samples", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
